@@ -1,0 +1,199 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) 3D Gaussian Splatting forward rasterizer with
+ * FlashGS's opacity-aware exact intersection (arXiv 2408.07967).
+ *
+ * Pipeline (Section 2.2 and Fig. "FlashGS Overview"; Algorithm 4):
+ *   gs_preprocess  per-Gaussian cull, projection, EWA conic, Eq. 3 threshold, tight box,
+ *                  exact ellipse/tile test (Algorithm 3, Eq. 9) and (tile, depth) key
+ *                  emission, SH colour, all in one kernel;
+ *   gs_sort        stable radix sort of the 64-bit (tile, depth) keys with Gaussian ids;
+ *   gs_ranges      [start, end) of every tile in the sorted list;
+ *   gs_blend       per-16x16-tile front-to-back alpha blending with early stop.
+ *   gs_render      the four stages in order (replayed from a CUDA graph when enabled).
+ *
+ * Conventions used by every call:
+ *   - Pointers named *_dev are device pointers; others are host pointers.  The caller owns
+ *     every buffer it passes in; the library owns contexts, scenes and frames and the device
+ *     memory inside them, which it allocates once at creation (Section 5.3.1: no per-frame
+ *     allocation) and frees at destruction.
+ *   - Calls taking a gs_stream (a cudaStream_t; NULL is the legacy default stream) only
+ *     enqueue work on it and return without synchronising, unless documented otherwise.
+ *   - Errors are returned as negative gs_status codes; gs_last_error() gives a message for
+ *     the calling thread.  No call aborts the process.  Errors found on the device (pair
+ *     buffer overflow, a bounded wait that gave up) are recorded in the frame and reported by
+ *     gs_frame_get_stats().
+ *   - Cameras are pinholes: x_cam = R x_world + t (R row-major), the camera looks down +z with
+ *     x right and y down; pixel (i, j) covers [i, i+1) x [j, j+1) and is sampled at its centre;
+ *     u = fx x/z + cx, v = fy y/z + cy.
+ *   - Gaussians are given as canonical arrays of float32: means [P,3], scales [P,3] (or
+ *     log-scales), quaternions [P,4] as (w, x, y, z) (normalised internally), opacities [P]
+ *     (or logits), SH coefficients [P,16,3] (coefficient-major, RGB-minor; degree <= 3).
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gs_status;
+#define GS_OK 0
+#define GS_ERR_INVALID_ARG (-1)
+#define GS_ERR_OOM (-2)
+#define GS_ERR_PAIR_OVERFLOW (-3)
+#define GS_ERR_CUDA (-4)
+#define GS_ERR_DEVICE_TIMEOUT (-5)
+#define GS_ERR_BUSY (-6)
+#define GS_ERR_CAPACITY (-7)
+#define GS_ERR_NO_DEVICE (-8)
+
+typedef struct gs_context gs_context;
+typedef struct gs_scene gs_scene;
+typedef struct gs_frame gs_frame;
+typedef void *gs_stream; /* cudaStream_t */
+
+typedef struct {
+    float R[9];      /* world -> camera rotation, row-major */
+    float t[3];      /* world -> camera translation */
+    float fx, fy;    /* focal lengths in pixels */
+    float cx, cy;    /* principal point in pixel-area coordinates */
+    int32_t width, height;
+    float near_z;    /* near plane; Algorithm 4 culls z <= 0.2 */
+} gs_camera;
+
+typedef struct {
+    const float *means;    /* [P,3] device */
+    const float *scales;   /* [P,3] device: scales, or log-scales when activated == 0 */
+    const float *quats;    /* [P,4] device: (w,x,y,z) */
+    const float *opacity;  /* [P] device: opacity, or logits when activated == 0 */
+    const float *sh;       /* [P,16,3] device */
+    int64_t P;
+    int32_t sh_degree;     /* 0..3 */
+    int32_t activated;     /* 1: scales/opacities as given; 0: exp / sigmoid applied on device */
+} gs_gaussians;
+
+typedef struct {
+    float bg[3];        /* background colour added with the final transmittance */
+    float tau;          /* alpha threshold, 1/255 (Section 4.1) */
+    float alpha_max;    /* alpha clamp, 0.99 */
+    float T_min;        /* early-stop transmittance, 1e-4 */
+    float dilation;     /* low-pass added to the 2D covariance diagonal, 0.3 px^2 */
+    int32_t cap_3sigma; /* 0: t = 2 ln(alpha0/tau) (Eq. 3); 1: t = min(9, Eq. 3) (Section 4.1) */
+    int32_t clamp_fov;  /* 1: clamp x/z, y/z to 1.3 tan(half fov) in the EWA Jacobian */
+} gs_render_opts;
+
+typedef struct {
+    int64_t pairs;          /* Gaussian/tile pairs emitted by gs_preprocess (may exceed capacity) */
+    int64_t visible;        /* Gaussians with at least one pair */
+    int64_t pair_capacity;  /* pairs the frame can hold */
+    int32_t status;         /* GS_OK, GS_ERR_PAIR_OVERFLOW or GS_ERR_DEVICE_TIMEOUT */
+    int32_t width, height;
+    int32_t tiles_x, tiles_y;
+    int32_t sort_passes;    /* 8-bit digit passes of the last sort */
+} gs_frame_stats;
+
+/* Message for the last error returned on the calling thread ("" if none). */
+const char *gs_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int32_t gs_version(void);
+
+/* Fills *opts with the defaults above (bg 0, tau 1/255, alpha_max 0.99, T_min 1e-4,
+   dilation 0.3, cap_3sigma 0, clamp_fov 1).  GS_ERR_INVALID_ARG if opts is NULL. */
+gs_status gs_default_opts(gs_render_opts *opts);
+
+/* Creates a context bound to CUDA device `device` (made current on the calling thread).
+   Errors: GS_ERR_NO_DEVICE, GS_ERR_CUDA, GS_ERR_OOM. */
+gs_status gs_context_create(int32_t device, gs_context **out);
+gs_status gs_context_destroy(gs_context *ctx);
+
+/* Device-resident scene: copies the canonical arrays in `g` into the library's internal
+   structure-of-arrays layout (16-byte vectors per Gaussian: position+opacity, scale,
+   quaternion, and twelve SH planes), enqueued on `stream`.  The input arrays may be freed
+   once the stream has passed this call.  Section 5.3.1 (per-scene work done once).
+   Errors: GS_ERR_INVALID_ARG (NULL pointers, P <= 0, P >= 2^31, bad degree), GS_ERR_OOM. */
+gs_status gs_scene_create(gs_context *ctx, const gs_gaussians *g, gs_stream stream, gs_scene **out);
+/* Re-packs new parameter values of the same P into an existing scene (training steps). */
+gs_status gs_scene_update(gs_scene *scene, const gs_gaussians *g, gs_stream stream);
+gs_status gs_scene_destroy(gs_scene *scene);
+int64_t gs_scene_size(const gs_scene *scene);
+
+/* Per-frame state (Table 2 / Section 5.3.1: allocated once, reused every frame): render
+   records for up to max_gaussians, two ping-pong pair buffers of max_pairs (u64 key, u32
+   value), tile ranges for up to max_width x max_height, and the scratch of the scan and the
+   sort.  Errors: GS_ERR_INVALID_ARG, GS_ERR_OOM (nothing is left allocated). */
+gs_status gs_frame_create(gs_context *ctx, int64_t max_gaussians, int64_t max_pairs,
+                          int32_t max_width, int32_t max_height, gs_frame **out);
+gs_status gs_frame_destroy(gs_frame *frame);
+/* Bytes of device memory held by the frame. */
+int64_t gs_frame_bytes(const gs_frame *frame);
+
+/* Stage a (Algorithm 4; Algorithm 3; Eq. 2-3, 9): per Gaussian, cull z <= near_z and
+   alpha0 <= tau, project, build the EWA conic, compute t = 2 ln(alpha0/tau), test every tile
+   of the tight bounding box exactly, and write one (key, Gaussian id) pair per intersecting
+   tile, key = (tile_id << 32) | float_bits(z), tile_id = ty * tiles_x + tx.  Pairs are written
+   in (Gaussian id, tile row-major) order.  Also writes each paired Gaussian's render record
+   (centre, conic, threshold, colour).  Errors: GS_ERR_INVALID_ARG (scene larger than the frame,
+   image larger than the frame, camera with non-positive focal length). */
+gs_status gs_preprocess(gs_frame *frame, const gs_scene *scene, const gs_camera *cam,
+                        const gs_render_opts *opts, gs_stream stream);
+
+/* Stage b (Section 2.2 sort): stable LSD radix sort of the frame's pairs by key, over bits
+   [0, 32 + ceil(log2(tiles))) in 8-bit digits (one histogram pass, then one chained-scan
+   scatter pass per digit).  The pair count is read on the device. */
+gs_status gs_sort(gs_frame *frame, gs_stream stream);
+
+/* Stage c: start of every tile's run in the sorted keys (binary search per tile). */
+gs_status gs_ranges(gs_frame *frame, gs_stream stream);
+
+/* Stage d (Section 2.2 render; Section 5.2): per 16x16 tile, walk the tile's sorted list
+   front to back; per pixel alpha = min(alpha_max, alpha0 exp(-q/2)), skip when
+   alpha < tau, stop before a Gaussian that would take T below T_min, C += rgb alpha T.
+   Writes rgb_dev [3,H,W] = C + T bg, T_dev [H,W] (nullable) and last_dev [H,W] (nullable:
+   1-based position in the tile list of the last contributor, 0 if none). */
+gs_status gs_blend(gs_frame *frame, const gs_render_opts *opts, float *rgb_dev, float *T_dev,
+                   uint32_t *last_dev, gs_stream stream);
+
+/* Stages a-d in order.  When graphs are enabled on the frame (gs_frame_use_graph) the
+   sequence is captured once per (scene, image size) and replayed with updated camera and
+   options.  Errors: as the stages. */
+gs_status gs_render(gs_frame *frame, const gs_scene *scene, const gs_camera *cam,
+                    const gs_render_opts *opts, float *rgb_dev, float *T_dev, uint32_t *last_dev,
+                    gs_stream stream);
+
+/* Enables (1) or disables (0) CUDA-graph replay of gs_render on this frame. */
+gs_status gs_frame_use_graph(gs_frame *frame, int32_t enable);
+
+/* Synchronises `stream` and reads the frame's counters.  status carries device-side errors:
+   GS_ERR_PAIR_OVERFLOW when more pairs were found than max_pairs (outputs are then invalid;
+   pairs holds the number needed), GS_ERR_DEVICE_TIMEOUT when a bounded wait gave up. */
+gs_status gs_frame_get_stats(gs_frame *frame, gs_frame_stats *out, gs_stream stream);
+
+/* Copies min(pairs, capacity, cap) pairs to caller buffers keys_dev / vals_dev (device):
+   which = 0 the emission-order list written by gs_preprocess (valid before gs_sort),
+   which = 1 the sorted list (valid after gs_sort).  *n_out (host) receives the count copied.
+   Synchronises `stream`. */
+gs_status gs_frame_pairs(gs_frame *frame, int32_t which, uint64_t *keys_dev, uint32_t *vals_dev,
+                         int64_t cap, int64_t *n_out, gs_stream stream);
+
+/* Copies the tile starts (tiles + 1 entries of uint32) to starts_dev.  Synchronises. */
+gs_status gs_frame_ranges(gs_frame *frame, uint32_t *starts_dev, int64_t cap, gs_stream stream);
+
+/* Stand-alone stable radix sort of n (u64 key, u32 value) pairs by key bits [0, end_bit)
+   (end_bit <= 64), the primitive behind gs_sort.  keys_dev/vals_dev hold the input; tmp
+   buffers of the same sizes are caller-provided ping-pong storage.  *in_tmp (host) is set to 1
+   when the result ended in the tmp buffers (odd number of passes), else 0.  Scratch for the
+   histograms and the chained scan comes from the context (grown on demand, never freed before
+   gs_context_destroy).  Errors: GS_ERR_INVALID_ARG (n < 0, n >= 2^30, end_bit out of range). */
+gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys_dev, uint32_t *vals_dev, uint64_t *keys_tmp_dev,
+                        uint32_t *vals_tmp_dev, int64_t n, int32_t end_bit, int32_t *in_tmp,
+                        gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

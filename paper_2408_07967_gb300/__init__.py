@@ -1,0 +1,250 @@
+"""GB300 (sm_103a) 3D Gaussian Splatting forward rasterizer with FlashGS's opacity-aware exact
+intersection (arXiv 2408.07967).
+
+Thin Python binding over the C ABI of include/gs.h: the functions carry the C names and only
+marshal arguments (torch CUDA tensors -> device pointers, the current torch stream ->
+cudaStream_t).  Every stage of the rasterizer runs in the library's CUDA kernels; when
+libgs.so is missing the binding raises -- there is no CPU fallback.
+
+Importing this package loads neither torch nor the library; both happen on first use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _native
+
+__all__ = ["GsError", "Context", "Scene", "Frame", "gs_camera_from", "gs_opts", "gs_sort_pairs", "lib"]
+
+GS_OK = 0
+STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_PAIR_OVERFLOW", -4: "GS_ERR_CUDA",
+                -5: "GS_ERR_DEVICE_TIMEOUT", -6: "GS_ERR_BUSY", -7: "GS_ERR_CAPACITY", -8: "GS_ERR_NO_DEVICE"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    return _native.load()
+
+
+def _check(status):
+    if status != GS_OK:
+        raise GsError(status, lib().gs_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "tensors must be contiguous CUDA tensors"
+    return C.c_void_p(t.data_ptr())
+
+
+def gs_camera_from(cam) -> _native.gs_camera:
+    """gs_camera from any object with R, t, fx, fy, cx, cy, width, height (and optional near)."""
+    import numpy as np
+    c = _native.gs_camera()
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    t = np.asarray(cam.t, np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.near_z = float(getattr(cam, "near", 0.2))
+    return c
+
+
+def gs_opts(bg=(0.0, 0.0, 0.0), tau=None, alpha_max=None, T_min=None, dilation=None, cap_3sigma=False,
+            clamp_fov=True) -> _native.gs_render_opts:
+    o = _native.gs_render_opts()
+    _check(lib().gs_default_opts(C.byref(o)))
+    for i in range(3):
+        o.bg[i] = float(bg[i])
+    if tau is not None:
+        o.tau = float(tau)
+    if alpha_max is not None:
+        o.alpha_max = float(alpha_max)
+    if T_min is not None:
+        o.T_min = float(T_min)
+    if dilation is not None:
+        o.dilation = float(dilation)
+    o.cap_3sigma = int(bool(cap_3sigma))
+    o.clamp_fov = int(bool(clamp_fov))
+    return o
+
+
+class Context:
+    """gs_context: one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = C.c_void_p()
+        _check(lib().gs_context_create(self.device, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gs_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """gs_scene: device-resident Gaussians (packed into the library's SoA layout)."""
+
+    def __init__(self, ctx: Context, means, scales, quats, opacity, sh, sh_degree=3, activated=True, stream=None):
+        self.ctx = ctx
+        g = self._struct(means, scales, quats, opacity, sh, sh_degree, activated)
+        h = C.c_void_p()
+        _check(lib().gs_scene_create(ctx.h, C.byref(g), _stream(stream), C.byref(h)))
+        self.h = h
+        self.P = int(g.P)
+
+    @staticmethod
+    def _struct(means, scales, quats, opacity, sh, sh_degree, activated):
+        g = _native.gs_gaussians()
+        g.means, g.scales, g.quats, g.opacity, g.sh = (_ptr(x) for x in (means, scales, quats, opacity, sh))
+        g.P = int(means.shape[0])
+        g.sh_degree = int(sh_degree)
+        g.activated = int(bool(activated))
+        for x, k in ((means, 3), (scales, 3), (quats, 4), (sh, 48)):
+            assert x.numel() == g.P * k, "array size does not match P"
+        assert opacity.numel() == g.P
+        return g
+
+    def gs_scene_update(self, means, scales, quats, opacity, sh, sh_degree=3, activated=True, stream=None):
+        g = self._struct(means, scales, quats, opacity, sh, sh_degree, activated)
+        _check(lib().gs_scene_update(self.h, C.byref(g), _stream(stream)))
+
+    @classmethod
+    def from_numpy(cls, ctx, scene, device="cuda", stream=None):
+        """Upload a synth.Scene-like object (numpy float32 arrays) and build the device scene."""
+        import torch
+        arrs = [torch.from_numpy(a.reshape(a.shape[0], -1) if a.ndim > 1 else a).to(device).contiguous()
+                for a in (scene.means, scene.scales, scene.quats, scene.opacity, scene.sh)]
+        s = cls(ctx, *arrs, sh_degree=3, activated=scene.activated, stream=stream)
+        s._inputs = arrs          # kept alive until the pack kernel has run
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gs_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Frame:
+    """gs_frame: per-frame device state allocated once."""
+
+    def __init__(self, ctx: Context, max_gaussians: int, max_pairs: int, max_width: int, max_height: int):
+        self.ctx = ctx
+        h = C.c_void_p()
+        _check(lib().gs_frame_create(ctx.h, int(max_gaussians), int(max_pairs), int(max_width), int(max_height),
+                                     C.byref(h)))
+        self.h = h
+        self.max_pairs = int(max_pairs)
+
+    # ---- stages (C names)
+    def gs_preprocess(self, scene: Scene, cam, opts=None, stream=None):
+        o = opts or gs_opts()
+        _check(lib().gs_preprocess(self.h, scene.h, C.byref(gs_camera_from(cam)), C.byref(o), _stream(stream)))
+
+    def gs_sort(self, stream=None):
+        _check(lib().gs_sort(self.h, _stream(stream)))
+
+    def gs_ranges(self, stream=None):
+        _check(lib().gs_ranges(self.h, _stream(stream)))
+
+    def gs_blend(self, rgb, T=None, last=None, opts=None, stream=None):
+        o = opts or gs_opts()
+        _check(lib().gs_blend(self.h, C.byref(o), _ptr(rgb), _ptr(T), _ptr(last), _stream(stream)))
+
+    def gs_render(self, scene: Scene, cam, rgb, T=None, last=None, opts=None, stream=None):
+        o = opts or gs_opts()
+        _check(lib().gs_render(self.h, scene.h, C.byref(gs_camera_from(cam)), C.byref(o), _ptr(rgb), _ptr(T),
+                               _ptr(last), _stream(stream)))
+
+    def gs_frame_use_graph(self, enable: bool):
+        _check(lib().gs_frame_use_graph(self.h, int(bool(enable))))
+
+    # ---- conveniences
+    def render(self, scene: Scene, cam, opts=None, stream=None, want_T=True, want_last=True):
+        import torch
+        H, W = int(cam.height), int(cam.width)
+        rgb = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
+        T = torch.empty((H, W), dtype=torch.float32, device="cuda") if want_T else None
+        last = torch.empty((H, W), dtype=torch.int32, device="cuda") if want_last else None
+        self.gs_render(scene, cam, rgb, T, last, opts, stream)
+        return rgb, T, last
+
+    def stats(self, stream=None) -> dict:
+        s = _native.gs_frame_stats()
+        _check(lib().gs_frame_get_stats(self.h, C.byref(s), _stream(stream)))
+        return {k: getattr(s, k) for k, _ in _native.gs_frame_stats._fields_}
+
+    def pairs(self, which: int = 1, stream=None):
+        """(keys uint64 as int64 tensor, values int32 tensor) of the emission-order (0) or sorted (1) list."""
+        import torch
+        n_total = self.stats(stream)["pairs"]
+        cap = max(1, min(n_total, self.max_pairs))
+        keys = torch.empty(cap, dtype=torch.int64, device="cuda")
+        vals = torch.empty(cap, dtype=torch.int32, device="cuda")
+        n = C.c_int64()
+        _check(lib().gs_frame_pairs(self.h, int(which), _ptr(keys), _ptr(vals), cap, C.byref(n), _stream(stream)))
+        return keys[: n.value], vals[: n.value]
+
+    def starts(self, stream=None):
+        import torch
+        st = self.stats(stream)
+        n = st["tiles_x"] * st["tiles_y"] + 1
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        _check(lib().gs_frame_ranges(self.h, _ptr(out), n, _stream(stream)))
+        return out
+
+    def nbytes(self) -> int:
+        return int(lib().gs_frame_bytes(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gs_frame_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gs_sort_pairs(ctx: Context, keys, vals, end_bit: int = 64, stream=None):
+    """Stable radix sort of (int64-viewed uint64 keys, int32 values) by key bits [0, end_bit).
+    Returns the sorted (keys, vals) tensors (inputs are used as ping-pong storage)."""
+    import torch
+    n = int(keys.numel())
+    kt = torch.empty_like(keys)
+    vt = torch.empty_like(vals)
+    in_tmp = C.c_int32()
+    _check(lib().gs_sort_pairs(ctx.h, _ptr(keys), _ptr(vals), _ptr(kt), _ptr(vt), n, int(end_bit), C.byref(in_tmp),
+                               _stream(stream)))
+    return (kt, vt) if in_tmp.value else (keys, vals)

@@ -1,0 +1,82 @@
+"""ctypes declarations of the C ABI in include/gs.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_lock = threading.Lock()
+_lib = None
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libgs.so")
+
+
+class gs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_z", C.c_float)]
+
+
+class gs_gaussians(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacity", C.c_void_p),
+                ("sh", C.c_void_p), ("P", C.c_int64), ("sh_degree", C.c_int32), ("activated", C.c_int32)]
+
+
+class gs_render_opts(C.Structure):
+    _fields_ = [("bg", C.c_float * 3), ("tau", C.c_float), ("alpha_max", C.c_float), ("T_min", C.c_float),
+                ("dilation", C.c_float), ("cap_3sigma", C.c_int32), ("clamp_fov", C.c_int32)]
+
+
+class gs_frame_stats(C.Structure):
+    _fields_ = [("pairs", C.c_int64), ("visible", C.c_int64), ("pair_capacity", C.c_int64), ("status", C.c_int32),
+                ("width", C.c_int32), ("height", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
+                ("sort_passes", C.c_int32)]
+
+
+_vp = C.c_void_p
+_pp = C.POINTER(C.c_void_p)
+_st = C.c_int32
+
+# name -> (restype, argtypes); every symbol declared in include/gs.h
+PROTOTYPES = {
+    "gs_last_error": (C.c_char_p, []),
+    "gs_version": (C.c_int32, []),
+    "gs_default_opts": (_st, [C.POINTER(gs_render_opts)]),
+    "gs_context_create": (_st, [C.c_int32, _pp]),
+    "gs_context_destroy": (_st, [_vp]),
+    "gs_scene_create": (_st, [_vp, C.POINTER(gs_gaussians), _vp, _pp]),
+    "gs_scene_update": (_st, [_vp, C.POINTER(gs_gaussians), _vp]),
+    "gs_scene_destroy": (_st, [_vp]),
+    "gs_scene_size": (C.c_int64, [_vp]),
+    "gs_frame_create": (_st, [_vp, C.c_int64, C.c_int64, C.c_int32, C.c_int32, _pp]),
+    "gs_frame_destroy": (_st, [_vp]),
+    "gs_frame_bytes": (C.c_int64, [_vp]),
+    "gs_preprocess": (_st, [_vp, _vp, C.POINTER(gs_camera), C.POINTER(gs_render_opts), _vp]),
+    "gs_sort": (_st, [_vp, _vp]),
+    "gs_ranges": (_st, [_vp, _vp]),
+    "gs_blend": (_st, [_vp, C.POINTER(gs_render_opts), _vp, _vp, _vp, _vp]),
+    "gs_render": (_st, [_vp, _vp, C.POINTER(gs_camera), C.POINTER(gs_render_opts), _vp, _vp, _vp, _vp]),
+    "gs_frame_use_graph": (_st, [_vp, C.c_int32]),
+    "gs_frame_get_stats": (_st, [_vp, C.POINTER(gs_frame_stats), _vp]),
+    "gs_frame_pairs": (_st, [_vp, C.c_int32, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
+    "gs_frame_ranges": (_st, [_vp, _vp, C.c_int64, _vp]),
+    "gs_sort_pairs": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _vp]),
+}
+
+
+def load(path: str | None = None):
+    """Load libgs.so and attach the prototypes.  Raises if the library is missing: there is no
+    fallback implementation."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libgs.so not built ({p}); run paper_2408_07967_gb300.build.build()")
+            L = C.CDLL(p)
+            for name, (res, args) in PROTOTYPES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib

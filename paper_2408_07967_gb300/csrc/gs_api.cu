@@ -1,0 +1,543 @@
+// gs_api.cu -- the C ABI (include/gs.h): contexts, device-resident scenes, per-frame state
+// allocated once (Section 5.3.1 "we reduce the dynamic memory allocation"), the four stages and
+// their CUDA-graph replay, statistics and debug copies.
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "gs_internal.cuh"
+
+using namespace gs;
+
+namespace {
+
+thread_local std::string g_err;
+
+gs_status fail(gs_status code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+gs_status fail(gs_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+gs_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GS_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves aligned slices out of one device allocation.
+struct Carver {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count) {
+        size_t o = align_up(off, 256);
+        off = o + count * sizeof(T);
+        return o;
+    }
+};
+
+int ceil_log2(long long x) {
+    int b = 0;
+    while ((1ll << b) < x) ++b;
+    return b;
+}
+
+Opts make_opts(const gs_render_opts *o) {
+    gs_render_opts d;
+    gs_default_opts(&d);
+    if (!o) o = &d;
+    Opts r;
+    for (int i = 0; i < 3; ++i) r.bg[i] = o->bg[i];
+    r.tau = o->tau;
+    r.alpha_max = o->alpha_max;
+    r.T_min = o->T_min;
+    r.dilation = o->dilation;
+    r.cap_3sigma = o->cap_3sigma;
+    r.clamp_fov = o->clamp_fov;
+    return r;
+}
+
+}  // namespace
+
+struct gs_context {
+    int device = 0;
+    int sm_count = 0;
+    FrameCounters *ctr = nullptr;     // counters of the stand-alone sort
+    SortScratch sort{};
+    void *sort_mem = nullptr;
+};
+
+struct gs_scene {
+    gs_context *ctx = nullptr;
+    long long P = 0;
+    int sh_degree = 3;
+    int activated = 1;
+    void *mem = nullptr;
+    float4 *pos_opa = nullptr, *scale = nullptr, *quat = nullptr, *sh = nullptr;
+};
+
+struct gs_frame {
+    gs_context *ctx = nullptr;
+    long long max_g = 0, max_pairs = 0;
+    int max_w = 0, max_h = 0;
+    long long max_tiles = 0, max_chunks = 0;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    Rec *recs = nullptr;
+    unsigned long long *keys[2] = {nullptr, nullptr};
+    unsigned *vals[2] = {nullptr, nullptr};
+    unsigned *starts = nullptr;
+    unsigned long long *scan_desc = nullptr;
+    SortScratch sort{};
+    FrameCounters *ctr = nullptr;
+    // state of the last call
+    int W = 0, H = 0, tiles_x = 0, tiles_y = 0;
+    int sorted_buf = 0, passes = 0;
+    // graph replay
+    int use_graph = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+const char *gs_last_error(void) { return g_err.c_str(); }
+
+int32_t gs_version(void) { return 100; }
+
+gs_status gs_default_opts(gs_render_opts *o) {
+    if (!o) return fail(GS_ERR_INVALID_ARG, "opts is NULL");
+    o->bg[0] = o->bg[1] = o->bg[2] = 0.0f;
+    o->tau = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->T_min = 1e-4f;
+    o->dilation = 0.3f;
+    o->cap_3sigma = 0;
+    o->clamp_fov = 1;
+    return GS_OK;
+}
+
+gs_status gs_context_create(int32_t device, gs_context **out) {
+    if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return fail(GS_ERR_NO_DEVICE, "no CUDA device");
+    }
+    if (device < 0 || device >= n) return fail(GS_ERR_INVALID_ARG, "device %d out of range [0,%d)", device, n);
+    GS_CUDA(cudaSetDevice(device));
+    gs_context *c = new (std::nothrow) gs_context();
+    if (!c) return fail(GS_ERR_OOM, "host allocation failed");
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaMalloc(&c->ctr, sizeof(FrameCounters));
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaMalloc(counters)");
+    }
+    cudaMemset(c->ctr, 0, sizeof(FrameCounters));
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(c->ctr);
+        delete c;
+        return cuda_fail(e, "context init");
+    }
+    *out = c;
+    return GS_OK;
+}
+
+gs_status gs_context_destroy(gs_context *c) {
+    if (!c) return GS_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    cudaFree(c->ctr);
+    cudaFree(c->sort_mem);
+    delete c;
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------------------------------ scenes
+static gs_status check_gaussians(const gs_gaussians *g) {
+    if (!g) return fail(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->P <= 0 || g->P >= (1ll << 31)) return fail(GS_ERR_INVALID_ARG, "P = %lld out of range", (long long)g->P);
+    if (!g->means || !g->scales || !g->quats || !g->opacity || !g->sh)
+        return fail(GS_ERR_INVALID_ARG, "a Gaussian array pointer is NULL");
+    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(GS_ERR_INVALID_ARG, "sh_degree %d not in 0..3", g->sh_degree);
+    return GS_OK;
+}
+
+gs_status gs_scene_create(gs_context *ctx, const gs_gaussians *g, gs_stream stream, gs_scene **out) {
+    if (!ctx || !out) return fail(GS_ERR_INVALID_ARG, "NULL context or out");
+    *out = nullptr;
+    gs_status st = check_gaussians(g);
+    if (st) return st;
+    GS_CUDA(cudaSetDevice(ctx->device));
+    gs_scene *s = new (std::nothrow) gs_scene();
+    if (!s) return fail(GS_ERR_OOM, "host allocation failed");
+    s->ctx = ctx;
+    s->P = g->P;
+    size_t planes = 3 + kShPlanes;
+    cudaError_t e = cudaMalloc(&s->mem, planes * (size_t)g->P * sizeof(float4));
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "cudaMalloc(scene)");
+    }
+    float4 *base = (float4 *)s->mem;
+    s->pos_opa = base;
+    s->scale = base + g->P;
+    s->quat = base + 2 * g->P;
+    s->sh = base + 3 * g->P;
+    st = gs_scene_update(s, g, stream);
+    if (st) {
+        cudaFree(s->mem);
+        delete s;
+        return st;
+    }
+    *out = s;
+    return GS_OK;
+}
+
+gs_status gs_scene_update(gs_scene *s, const gs_gaussians *g, gs_stream stream) {
+    if (!s) return fail(GS_ERR_INVALID_ARG, "scene is NULL");
+    gs_status st = check_gaussians(g);
+    if (st) return st;
+    if (g->P != s->P) return fail(GS_ERR_INVALID_ARG, "P changed (%lld != %lld)", (long long)g->P, s->P);
+    s->sh_degree = g->sh_degree;
+    s->activated = g->activated ? 1 : 0;
+    launch_pack_scene(*g, s->pos_opa, s->scale, s->quat, s->sh, (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status gs_scene_destroy(gs_scene *s) {
+    if (!s) return GS_OK;
+    cudaSetDevice(s->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(s->mem);
+    delete s;
+    return GS_OK;
+}
+
+int64_t gs_scene_size(const gs_scene *s) { return s ? s->P : 0; }
+
+// ------------------------------------------------------------------------------------------ frames
+gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int32_t max_w, int32_t max_h,
+                          gs_frame **out) {
+    if (!ctx || !out) return fail(GS_ERR_INVALID_ARG, "NULL context or out");
+    *out = nullptr;
+    if (max_g <= 0 || max_g >= (1ll << 31)) return fail(GS_ERR_INVALID_ARG, "max_gaussians out of range");
+    if (max_pairs <= 0 || max_pairs >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "max_pairs must be in (0, 2^30)");
+    if (max_w <= 0 || max_h <= 0 || max_w > 65536 || max_h > 65536) return fail(GS_ERR_INVALID_ARG, "bad image size");
+    long long tiles = (long long)((max_w + kTile - 1) / kTile) * ((max_h + kTile - 1) / kTile);
+    if (tiles >= (1ll << 31)) return fail(GS_ERR_INVALID_ARG, "too many tiles");
+    GS_CUDA(cudaSetDevice(ctx->device));
+    gs_frame *f = new (std::nothrow) gs_frame();
+    if (!f) return fail(GS_ERR_OOM, "host allocation failed");
+    f->ctx = ctx;
+    f->max_g = max_g;
+    f->max_pairs = max_pairs;
+    f->max_w = max_w;
+    f->max_h = max_h;
+    f->max_tiles = tiles;
+    f->max_chunks = (max_g + preprocess_chunk() - 1) / preprocess_chunk();
+    f->sort.max_tiles = sort_max_tiles_for(max_pairs);
+    Carver cv;
+    size_t o_recs = cv.take<Rec>(max_g);
+    size_t o_k0 = cv.take<unsigned long long>(max_pairs), o_k1 = cv.take<unsigned long long>(max_pairs);
+    size_t o_v0 = cv.take<unsigned>(max_pairs), o_v1 = cv.take<unsigned>(max_pairs);
+    size_t o_starts = cv.take<unsigned>(tiles + 1);
+    size_t o_scan = cv.take<unsigned long long>(f->max_chunks);
+    size_t o_hist = cv.take<unsigned>(8 * 256), o_offs = cv.take<unsigned>(8 * 256);
+    size_t o_desc = cv.take<unsigned long long>(f->sort.max_tiles * 256);
+    size_t o_ctr = cv.take<FrameCounters>(1);
+    f->bytes = align_up(cv.off, 256);
+    cudaError_t e = cudaMalloc(&f->mem, f->bytes);
+    if (e != cudaSuccess) {
+        delete f;
+        cudaGetLastError();
+        return fail(GS_ERR_OOM, "cudaMalloc(frame, %zu bytes): %s", f->bytes, cudaGetErrorString(e));
+    }
+    char *b = (char *)f->mem;
+    f->recs = (Rec *)(b + o_recs);
+    f->keys[0] = (unsigned long long *)(b + o_k0);
+    f->keys[1] = (unsigned long long *)(b + o_k1);
+    f->vals[0] = (unsigned *)(b + o_v0);
+    f->vals[1] = (unsigned *)(b + o_v1);
+    f->starts = (unsigned *)(b + o_starts);
+    f->scan_desc = (unsigned long long *)(b + o_scan);
+    f->sort.hist = (unsigned *)(b + o_hist);
+    f->sort.offs = (unsigned *)(b + o_offs);
+    f->sort.desc = (unsigned long long *)(b + o_desc);
+    f->ctr = (FrameCounters *)(b + o_ctr);
+    // zero scratch that must start cleared (histograms, descriptors, counters, tile starts)
+    cudaMemset(b + o_starts, 0, f->bytes - o_starts);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(f->mem);
+        delete f;
+        return cuda_fail(e, "frame init");
+    }
+    *out = f;
+    return GS_OK;
+}
+
+gs_status gs_frame_destroy(gs_frame *f) {
+    if (!f) return GS_OK;
+    cudaSetDevice(f->ctx->device);
+    cudaDeviceSynchronize();
+    if (f->exec) cudaGraphExecDestroy(f->exec);
+    cudaFree(f->mem);
+    delete f;
+    return GS_OK;
+}
+
+int64_t gs_frame_bytes(const gs_frame *f) { return f ? (int64_t)f->bytes : 0; }
+
+gs_status gs_frame_use_graph(gs_frame *f, int32_t enable) {
+    if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
+    f->use_graph = enable ? 1 : 0;
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------------------------------ stages
+gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, const gs_render_opts *opts,
+                        gs_stream stream) {
+    if (!f || !s || !cam) return fail(GS_ERR_INVALID_ARG, "NULL frame, scene or camera");
+    if (s->P > f->max_g) return fail(GS_ERR_INVALID_ARG, "scene has %lld Gaussians, frame holds %lld", s->P, f->max_g);
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > f->max_w || cam->height > f->max_h)
+        return fail(GS_ERR_INVALID_ARG, "image %dx%d outside the frame's %dx%d", cam->width, cam->height, f->max_w,
+                    f->max_h);
+    if (!(cam->fx > 0.0f) || !(cam->fy > 0.0f)) return fail(GS_ERR_INVALID_ARG, "focal lengths must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    PreprocessArgs a;
+    a.scene.pos_opa = s->pos_opa;
+    a.scene.scale = s->scale;
+    a.scene.quat = s->quat;
+    a.scene.sh = s->sh;
+    a.scene.P = s->P;
+    a.scene.sh_degree = s->sh_degree;
+    a.scene.activated = s->activated;
+    Cam &c = a.cam;
+    for (int i = 0; i < 9; ++i) c.R[i] = cam->R[i];
+    for (int i = 0; i < 3; ++i) c.t[i] = cam->t[i];
+    c.fx = cam->fx;
+    c.fy = cam->fy;
+    c.cx = cam->cx;
+    c.cy = cam->cy;
+    c.near_z = cam->near_z;
+    c.W = cam->width;
+    c.H = cam->height;
+    c.tiles_x = (cam->width + kTile - 1) / kTile;
+    c.tiles_y = (cam->height + kTile - 1) / kTile;
+    // clamp bounds, binary32 as in the Jacobian definition: 1.3 * ((W/2) / fx)
+    volatile float hw = 0.5f * (float)cam->width, hh = 0.5f * (float)cam->height;
+    volatile float qx = hw / cam->fx, qy = hh / cam->fy;
+    c.limx = 1.3f * qx;
+    c.limy = 1.3f * qy;
+    for (int i = 0; i < 3; ++i)
+        c.campos[i] = -(cam->R[i] * cam->t[0] + cam->R[3 + i] * cam->t[1] + cam->R[6 + i] * cam->t[2]);
+    a.opt = make_opts(opts);
+    a.recs = f->recs;
+    a.keys = f->keys[0];
+    a.vals = f->vals[0];
+    a.scan_desc = f->scan_desc;
+    a.ctr = f->ctr;
+    a.pair_cap = f->max_pairs;
+    a.n_chunks = (int)((s->P + preprocess_chunk() - 1) / preprocess_chunk());
+    GS_CUDA(cudaMemsetAsync(f->ctr, 0, offsetof(FrameCounters, sort_epoch), st));
+    GS_CUDA(cudaMemsetAsync(f->scan_desc, 0, sizeof(unsigned long long) * (size_t)a.n_chunks, st));
+    launch_preprocess(a, st);
+    GS_CUDA(cudaGetLastError());
+    f->W = c.W;
+    f->H = c.H;
+    f->tiles_x = c.tiles_x;
+    f->tiles_y = c.tiles_y;
+    f->sorted_buf = 0;
+    return GS_OK;
+}
+
+gs_status gs_sort(gs_frame *f, gs_stream stream) {
+    if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
+    if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_sort before gs_preprocess");
+    const int end_bit = 32 + ceil_log2((long long)f->tiles_x * f->tiles_y);
+    f->passes = launch_sort(f->keys[0], f->vals[0], f->keys[1], f->vals[1], &f->ctr->n_pairs, 0, f->max_pairs,
+                            end_bit, f->sort, f->ctr, (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    f->sorted_buf = f->passes & 1;
+    return GS_OK;
+}
+
+gs_status gs_ranges(gs_frame *f, gs_stream stream) {
+    if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
+    if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_ranges before gs_preprocess");
+    launch_ranges(f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs, f->tiles_x * f->tiles_y, f->starts,
+                  (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status gs_blend(gs_frame *f, const gs_render_opts *opts, float *rgb, float *T, uint32_t *last,
+                   gs_stream stream) {
+    if (!f || !rgb) return fail(GS_ERR_INVALID_ARG, "NULL frame or rgb");
+    if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_blend before gs_preprocess");
+    BlendArgs a;
+    a.recs = f->recs;
+    a.vals = f->vals[f->sorted_buf];
+    a.starts = f->starts;
+    a.n_dev = &f->ctr->n_pairs;
+    a.cap = f->max_pairs;
+    a.opt = make_opts(opts);
+    a.W = f->W;
+    a.H = f->H;
+    a.tiles_x = f->tiles_x;
+    a.tiles_y = f->tiles_y;
+    a.rgb = rgb;
+    a.T = T;
+    a.last = last;
+    launch_blend(a, (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+static gs_status enqueue_all(gs_frame *f, const gs_scene *s, const gs_camera *cam, const gs_render_opts *opts,
+                             float *rgb, float *T, uint32_t *last, gs_stream stream) {
+    gs_status st = gs_preprocess(f, s, cam, opts, stream);
+    if (st) return st;
+    if ((st = gs_sort(f, stream))) return st;
+    if ((st = gs_ranges(f, stream))) return st;
+    return gs_blend(f, opts, rgb, T, last, stream);
+}
+
+gs_status gs_render(gs_frame *f, const gs_scene *s, const gs_camera *cam, const gs_render_opts *opts, float *rgb,
+                    float *T, uint32_t *last, gs_stream stream) {
+    if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
+    if (!f->use_graph) return enqueue_all(f, s, cam, opts, rgb, T, last, stream);
+    if (!stream) return fail(GS_ERR_INVALID_ARG, "graph replay needs a non-default stream");
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    gs_status r = enqueue_all(f, s, cam, opts, rgb, T, last, stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (r) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    if (f->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(f->exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(f->exec);
+            f->exec = nullptr;
+        }
+    }
+    if (!f->exec) {
+        e = cudaGraphInstantiate(&f->exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            f->exec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+    }
+    cudaGraphDestroy(g);
+    GS_CUDA(cudaGraphLaunch(f->exec, st));
+    return GS_OK;
+}
+
+gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream) {
+    if (!f || !out) return fail(GS_ERR_INVALID_ARG, "NULL frame or out");
+    GS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    FrameCounters c;
+    GS_CUDA(cudaMemcpy(&c, f->ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    memset(out, 0, sizeof(*out));
+    out->pairs = (int64_t)c.n_pairs;
+    out->visible = c.n_visible;
+    out->pair_capacity = f->max_pairs;
+    out->status = (c.status & kStTimeout) ? GS_ERR_DEVICE_TIMEOUT
+                  : (c.status & kStPairOverflow) ? GS_ERR_PAIR_OVERFLOW
+                                                 : GS_OK;
+    out->width = f->W;
+    out->height = f->H;
+    out->tiles_x = f->tiles_x;
+    out->tiles_y = f->tiles_y;
+    out->sort_passes = f->passes;
+    return GS_OK;
+}
+
+gs_status gs_frame_pairs(gs_frame *f, int32_t which, uint64_t *keys, uint32_t *vals, int64_t cap, int64_t *n_out,
+                         gs_stream stream) {
+    if (!f || !n_out) return fail(GS_ERR_INVALID_ARG, "NULL frame or n_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA(cudaStreamSynchronize(st));
+    unsigned long long n = 0;
+    GS_CUDA(cudaMemcpy(&n, &f->ctr->n_pairs, sizeof(n), cudaMemcpyDeviceToHost));
+    long long m = (long long)n;
+    if (m > f->max_pairs) m = f->max_pairs;
+    if (m > cap) m = cap;
+    const int b = which ? f->sorted_buf : 0;
+    if (m > 0) {
+        if (keys) GS_CUDA(cudaMemcpyAsync(keys, f->keys[b], (size_t)m * 8, cudaMemcpyDeviceToDevice, st));
+        if (vals) GS_CUDA(cudaMemcpyAsync(vals, f->vals[b], (size_t)m * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    GS_CUDA(cudaStreamSynchronize(st));
+    *n_out = m;
+    return GS_OK;
+}
+
+gs_status gs_frame_ranges(gs_frame *f, uint32_t *starts, int64_t cap, gs_stream stream) {
+    if (!f || !starts) return fail(GS_ERR_INVALID_ARG, "NULL frame or starts");
+    const long long n = (long long)f->tiles_x * f->tiles_y + 1;
+    if (cap < n) return fail(GS_ERR_CAPACITY, "need %lld entries", n);
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA(cudaMemcpyAsync(starts, f->starts, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
+gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp, uint32_t *vals_tmp,
+                        int64_t n, int32_t end_bit, int32_t *in_tmp, gs_stream stream) {
+    if (!ctx || !in_tmp) return fail(GS_ERR_INVALID_ARG, "NULL context or in_tmp");
+    if (n < 0 || n >= (1ll << 30)) return fail(GS_ERR_INVALID_ARG, "n = %lld out of range", (long long)n);
+    if (end_bit < 1 || end_bit > 64) return fail(GS_ERR_INVALID_ARG, "end_bit %d not in 1..64", end_bit);
+    if (n > 0 && (!keys || !vals || !keys_tmp || !vals_tmp)) return fail(GS_ERR_INVALID_ARG, "NULL buffer");
+    GS_CUDA(cudaSetDevice(ctx->device));
+    const long long tiles = sort_max_tiles_for(n > 0 ? n : 1);
+    if (tiles > ctx->sort.max_tiles) {
+        GS_CUDA(cudaDeviceSynchronize());
+        cudaFree(ctx->sort_mem);
+        ctx->sort_mem = nullptr;
+        ctx->sort.max_tiles = 0;
+        Carver cv;
+        size_t oh = cv.take<unsigned>(8 * 256), oo = cv.take<unsigned>(8 * 256);
+        size_t od = cv.take<unsigned long long>(tiles * 256);
+        GS_CUDA(cudaMalloc(&ctx->sort_mem, cv.off));
+        GS_CUDA(cudaMemset(ctx->sort_mem, 0, cv.off));
+        char *b = (char *)ctx->sort_mem;
+        ctx->sort.hist = (unsigned *)(b + oh);
+        ctx->sort.offs = (unsigned *)(b + oo);
+        ctx->sort.desc = (unsigned long long *)(b + od);
+        ctx->sort.max_tiles = tiles;
+    }
+    const int passes = launch_sort((unsigned long long *)keys, vals, (unsigned long long *)keys_tmp, vals_tmp, nullptr,
+                                   n, n, end_bit, ctx->sort, ctx->ctr, (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    *in_tmp = passes & 1;
+    return GS_OK;
+}
+
+}  // extern "C"

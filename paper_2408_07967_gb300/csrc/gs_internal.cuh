@@ -1,0 +1,248 @@
+// gs_internal.cuh -- device-side structures and helpers shared by the sm_103a kernels.
+//
+// Decision arithmetic.  Every quantity that decides an integer outcome (cull, candidate
+// tiles, the exact tile test, key bits, the per-pixel alpha >= tau skip) is computed with
+// explicitly rounded binary32 intrinsics (__fadd_rn, __fmul_rn, __fdiv_rn, __fsqrt_rn and,
+// where the definition fuses, __fmaf_rn), so the compiler can neither contract nor reorder
+// it.  The rest (SH colour, blending values) uses ordinary float arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int kTile = 16;            // 16x16-pixel tiles (Section 2.2)
+constexpr int kShPlanes = 12;        // 48 SH floats as twelve float4 planes
+
+// device-side status bits, collected in FrameCounters::status
+enum : unsigned { kStPairOverflow = 1u, kStTimeout = 2u };
+
+// Bounded waits: a spin gives up after this many polls and sets kStTimeout.
+constexpr unsigned kSpinLimit = 1u << 22;
+
+struct Cam {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float near_z;
+    float limx, limy;      // 1.3 tan(half fov) bounds of x/z, y/z for the Jacobian
+    float campos[3];       // camera centre in world space (for SH directions)
+    int W, H;
+    int tiles_x, tiles_y;
+};
+
+struct Opts {
+    float bg[3];
+    float tau, alpha_max, T_min, dilation;
+    int cap_3sigma, clamp_fov;
+};
+
+// Internal structure-of-arrays scene, one 16-byte vector per Gaussian per plane.
+struct SceneView {
+    const float4 *pos_opa;   // (x, y, z, opacity or logit)
+    const float4 *scale;     // (sx, sy, sz, 0) or log-scales
+    const float4 *quat;      // (w, x, y, z)
+    const float4 *sh;        // kShPlanes planes of P float4: plane k = SH floats 4k .. 4k+3
+    int64_t P;
+    int sh_degree;
+    int activated;
+};
+
+// Render record of a paired Gaussian (48 bytes, three float4):
+//   r0 = (u, v, a, b2)   centre and conic, b2 = 2 b
+//   r1 = (c, t, G, red)  t = pixel threshold on q; G = log2(alpha0) = log2(tau) + t_full log2(e)/2
+//   r2 = (green, blue, z, alpha0)
+struct Rec {
+    float4 r0, r1, r2;
+};
+
+// Device counters of one frame.
+struct FrameCounters {
+    unsigned long long n_pairs;      // pairs found by preprocess (may exceed capacity)
+    unsigned int n_visible;          // Gaussians with >= 1 pair
+    unsigned int status;             // kSt* bits
+    unsigned int chunk_ticket;       // preprocess chunk ticket
+    unsigned int pad0;
+    unsigned int sort_ticket[8];     // scatter-pass tickets
+    unsigned int sort_epoch;         // bumped once per sort; tags look-back descriptors
+    unsigned int pad1[7];
+};
+
+// ----------------------------------------------------------------------------------------------
+// explicit IEEE binary32 operations (never contracted)
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// ln(x) for positive normal x: x = m 2^e with m in [sqrt(1/2), sqrt(2)); ln m = 2 atanh(s),
+// s = (m - 1)/(m + 1), by the odd Taylor series of atanh through s^11 in Horner form; e ln 2
+// added with a two-part constant whose high part has 16 significant bits.
+__device__ __forceinline__ float log_rn(float x) {
+    unsigned bits = __float_as_uint(x);
+    int e = (int)((bits >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);
+    if (m > 1.41421353816986083984375f) {
+        m = fmul(m, 0.5f);
+        e += 1;
+    }
+    const float k3 = 0.3333333432674407958984375f;    // 1/3 rounded
+    const float k5 = 0.20000000298023223876953125f;   // 1/5
+    const float k7 = 0.14285714924335479736328125f;   // 1/7
+    const float k9 = 0.111111111938953399658203125f;  // 1/9
+    const float k11 = 0.0909090936183929443359375f;   // 1/11
+    float s = fdiv(fsub(m, 1.0f), fadd(m, 1.0f));
+    float s2 = fmul(s, s);
+    float p = fmul(k11, s2);
+    p = fmul(fadd(p, k9), s2);
+    p = fmul(fadd(p, k7), s2);
+    p = fmul(fadd(p, k5), s2);
+    p = fmul(fadd(p, k3), s2);
+    float s_2 = fadd(s, s);
+    float lnm = fadd(s_2, fmul(s_2, p));
+    float ef = (float)e;
+    const float ln2_hi = 0.693145751953125f;
+    const float ln2_lo = 1.428606765330187045037746429443359375e-06f;
+    return fadd(fmul(ef, ln2_hi), fadd(fmul(ef, ln2_lo), lnm));
+}
+
+// e^x: x = k ln 2 + r with k = floor(x log2 e + 1/2), r reduced with the same two-part ln 2;
+// e^r by its Taylor polynomial through r^8/8! (Horner); scaled by 2^k as two exact factors.
+__device__ __forceinline__ float exp_rn(float x) {
+    if (!(x == x)) return x;
+    if (x < -87.0f) return 0.0f;
+    if (x > 88.0f) return __uint_as_float(0x7f800000u);
+    const float log2e = 1.44269502162933349609375f;
+    const float ln2_hi = 0.693145751953125f;
+    const float ln2_lo = 1.428606765330187045037746429443359375e-06f;
+    float kf = floorf(fadd(fmul(x, log2e), 0.5f));
+    float r = fsub(x, fmul(kf, ln2_hi));
+    r = fsub(r, fmul(kf, ln2_lo));
+    const float c2 = 0.5f;
+    const float c3 = 0.16666667163372039794921875f;      // 1/3!
+    const float c4 = 0.0416666679084300994873046875f;    // 1/4!
+    const float c5 = 0.008333333767950534820556640625f;  // 1/5!
+    const float c6 = 0.001388888922519981861114501953125f;       // 1/6!
+    const float c7 = 0.0001984127011382952332496643066406f;      // 1/7!
+    const float c8 = 2.48015876422868669033050537109375e-05f;    // 1/8!
+    float p = fmul(c8, r);
+    p = fmul(fadd(p, c7), r);
+    p = fmul(fadd(p, c6), r);
+    p = fmul(fadd(p, c5), r);
+    p = fmul(fadd(p, c4), r);
+    p = fmul(fadd(p, c3), r);
+    p = fmul(fadd(p, c2), r);
+    p = fmul(fadd(p, 1.0f), r);
+    p = fadd(p, 1.0f);
+    int k = (int)kf;
+    int k1 = k / 2, k2 = k - k1;
+    float s1 = __uint_as_float((unsigned)(k1 + 127) << 23);
+    float s2 = __uint_as_float((unsigned)(k2 + 127) << 23);
+    return fmul(fmul(p, s1), s2);
+}
+
+// Exact ellipse/tile test (Algorithm 3, Eq. 9 with the linear coefficient halved): the tile
+// [x0,x1] x [y0,y1] meets {a X^2 + 2 b X Y + c Y^2 <= t} about (u, v) iff the centre is inside,
+// or some edge line's chord (roots of A s^2 + 2 B s + C) overlaps the edge.
+__device__ __forceinline__ bool chord_hits(float A, float B, float C, float lo, float hi) {
+    float D = fsub(fmul(B, B), fmul(A, C));
+    if (!(D >= 0.0f)) return false;
+    float e1 = fadd(fmul(A, lo), B);
+    float e2 = fadd(fmul(A, hi), B);
+    bool left = (e1 <= 0.0f) || (fmul(e1, e1) <= D);
+    bool right = (e2 >= 0.0f) || (fmul(e2, e2) <= D);
+    return left && right;
+}
+
+__device__ __forceinline__ bool tile_hits(float u, float v, float a, float b, float c, float t,
+                                          float x0, float x1, float y0, float y1) {
+    if (x0 <= u && u <= x1 && y0 <= v && v <= y1) return true;
+    float lo = fsub(x0, u), hi = fsub(x1, u);
+    float dy = fsub(y0, v);
+    if (chord_hits(a, fmul(b, dy), fsub(fmul(fmul(c, dy), dy), t), lo, hi)) return true;
+    dy = fsub(y1, v);
+    if (chord_hits(a, fmul(b, dy), fsub(fmul(fmul(c, dy), dy), t), lo, hi)) return true;
+    lo = fsub(y0, v);
+    hi = fsub(y1, v);
+    float dx = fsub(x0, u);
+    if (chord_hits(c, fmul(b, dx), fsub(fmul(fmul(a, dx), dx), t), lo, hi)) return true;
+    dx = fsub(x1, u);
+    if (chord_hits(c, fmul(b, dx), fsub(fmul(fmul(a, dx), dx), t), lo, hi)) return true;
+    return false;
+}
+
+// Pixel-area rectangle of tile (tx, ty), clipped to the image.
+__device__ __forceinline__ void tile_rect(const Cam &cam, int tx, int ty, float &x0, float &x1,
+                                          float &y0, float &y1) {
+    int xe = min(kTile * tx + kTile, cam.W), ye = min(kTile * ty + kTile, cam.H);
+    x0 = (float)(kTile * tx);
+    x1 = (float)xe;
+    y0 = (float)(kTile * ty);
+    y1 = (float)ye;
+}
+
+// Per-pixel skip decision: q = fma(fma(a, dx, b2 dy), dx, (c dy) dy) at the pixel sample,
+// skipped when !(q <= t).
+__device__ __forceinline__ float pixel_q(float a, float b2, float c, float dx, float dy) {
+    float By = fmul(b2, dy);
+    float Cy = fmul(fmul(c, dy), dy);
+    return ffma(ffma(a, dx, By), dx, Cy);
+}
+
+// ----------------------------------------------------------------------------------------------
+// host-side launchers (defined in the .cu files)
+struct PreprocessArgs {
+    SceneView scene;
+    Cam cam;
+    Opts opt;
+    Rec *recs;
+    unsigned long long *keys;
+    unsigned *vals;
+    unsigned long long *scan_desc;   // one per chunk of the chained scan
+    FrameCounters *ctr;
+    long long pair_cap;
+    int n_chunks;
+};
+
+void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *scale, float4 *quat, float4 *sh,
+                       cudaStream_t s);
+void launch_preprocess(const PreprocessArgs &a, cudaStream_t s);
+int preprocess_chunk();
+
+struct SortScratch {
+    unsigned *hist;                  // [8][256] digit counts
+    unsigned *offs;                  // [8][256] exclusive digit offsets
+    unsigned long long *desc;        // [max_tiles * 256] epoch-tagged look-back descriptors
+    long long max_tiles;
+};
+
+int sort_tile_items();
+long long sort_max_tiles_for(long long n);
+// Sorts by key bits [0, end_bit).  n_dev: device pointer to the pair count (clamped to cap);
+// returns the number of passes (result in the tmp buffers when odd).
+int launch_sort(unsigned long long *keys, unsigned *vals, unsigned long long *keys_tmp, unsigned *vals_tmp,
+                const unsigned long long *n_dev, long long n_host, long long cap, int end_bit,
+                const SortScratch &scr, FrameCounters *ctr, cudaStream_t s);
+void launch_ranges(const unsigned long long *keys, const unsigned long long *n_dev, long long cap, int ntiles,
+                   unsigned *starts, cudaStream_t s);
+
+struct BlendArgs {
+    const Rec *recs;
+    const unsigned *vals;
+    const unsigned *starts;
+    const unsigned long long *n_dev;
+    long long cap;
+    Opts opt;
+    int W, H, tiles_x, tiles_y;
+    float *rgb;
+    float *T;
+    unsigned *last;
+};
+void launch_blend(const BlendArgs &a, cudaStream_t s);
+
+}  // namespace gs

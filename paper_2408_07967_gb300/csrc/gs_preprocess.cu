@@ -1,0 +1,473 @@
+// gs_preprocess.cu -- scene packing and the fused preprocess / exact-intersection / key-emission
+// kernel (Algorithm 4 of FlashGS, with the exact tile test of Algorithm 3 and Eq. 9, the
+// opacity-aware threshold of Eq. 2-3 and the tight bounding box of Section 4.1).
+//
+// One CTA handles a chunk of 256 consecutive Gaussians:
+//   1. each thread culls and projects its Gaussian and finds its candidate tiles;
+//   2. exact tile tests: a one-tile Gaussian stays on its thread, a multi-tile Gaussian is
+//      tested by the whole warp, 32 candidate tiles per step (Section 5.1.2); the warp's
+//      ballot gives the hit mask;
+//   3. a block scan of the per-Gaussian pair counts and a decoupled look-back across chunks
+//      (chunk order fixed by an atomic ticket, waits bounded) give every Gaussian its output
+//      offset, so pairs land in (Gaussian id, tile row-major) order -- deterministic, unlike
+//      the paper's atomicAdd slots;
+//   4. keys/values are written; the SH colour is evaluated and the render record stored only
+//      for Gaussians with at least one pair (Algorithm 4, last step).
+#include "gs_internal.cuh"
+
+namespace gs {
+
+constexpr int kPreBlock = 256;
+constexpr int kPackBlock = 128;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+
+int preprocess_chunk() { return kPreBlock; }
+
+// ------------------------------------------------------------------------------------------ pack
+// Canonical AoS arrays -> internal SoA float4 planes.  The SH block of a CTA is staged through
+// shared memory so that both the AoS reads and the plane writes are coalesced.
+__global__ void __launch_bounds__(kPackBlock) k_pack_scene(gs_gaussians g, float4 *pos_opa, float4 *scale,
+                                                           float4 *quat, float4 *sh) {
+    __shared__ float s_sh[kPackBlock * 48];
+    const long long base = (long long)blockIdx.x * kPackBlock;
+    const int n = (int)min((long long)kPackBlock, g.P - base);
+    const float *src = g.sh + base * 48;
+    for (int k = threadIdx.x; k < n * 48; k += kPackBlock) s_sh[k] = src[k];
+    __syncthreads();
+    const long long i = base + threadIdx.x;
+    if (threadIdx.x < n) {
+        const float *m = g.means + 3 * i;
+        const float *s = g.scales + 3 * i;
+        const float *q = g.quats + 4 * i;
+        pos_opa[i] = make_float4(m[0], m[1], m[2], g.opacity[i]);
+        scale[i] = make_float4(s[0], s[1], s[2], 0.0f);
+        quat[i] = make_float4(q[0], q[1], q[2], q[3]);
+        const float *c = s_sh + threadIdx.x * 48;
+#pragma unroll
+        for (int k = 0; k < kShPlanes; ++k)
+            sh[(long long)k * g.P + i] = make_float4(c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
+    }
+}
+
+void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *scale, float4 *quat, float4 *sh,
+                       cudaStream_t s) {
+    long long blocks = (g.P + kPackBlock - 1) / kPackBlock;
+    k_pack_scene<<<(unsigned)blocks, kPackBlock, 0, s>>>(g, pos_opa, scale, quat, sh);
+}
+
+// ------------------------------------------------------------------------------------------ SH
+// Real SH basis through degree 3 (3DGS sign/order convention), constants are the closed forms
+// 1/(2 sqrt pi), sqrt(3/(4 pi)), sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4, sqrt(35/(2 pi))/4,
+// sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4 evaluated to float.
+__device__ __forceinline__ void sh_colour(const SceneView &S, long long gid, const Cam &cam, float mx, float my,
+                                          float mz, float rgb[3]) {
+    const float K0 = 0.28209479177387814f;
+    const float K1 = 0.48860251190291992f;
+    const float K2a = 1.0925484305920792f, K2b = 0.31539156525252005f, K2c = 0.54627421529603959f;
+    const float K3a = 0.59004358992664352f, K3b = 2.8906114426405538f, K3c = 0.45704579946446572f;
+    const float K3d = 0.3731763325901154f, K3e = 1.4453057213202769f;
+    float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float x = dx * inv, y = dy * inv, z = dz * inv;
+    float Y[16];
+    Y[0] = K0;
+    Y[1] = -K1 * y;
+    Y[2] = K1 * z;
+    Y[3] = -K1 * x;
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = K2a * x * y;
+    Y[5] = -K2a * y * z;
+    Y[6] = K2b * (2.0f * zz - xx - yy);
+    Y[7] = -K2a * x * z;
+    Y[8] = K2c * (xx - yy);
+    Y[9] = -K3a * y * (3.0f * xx - yy);
+    Y[10] = K3b * x * y * z;
+    Y[11] = -K3c * y * (4.0f * zz - xx - yy);
+    Y[12] = K3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -K3c * x * (4.0f * zz - xx - yy);
+    Y[14] = K3e * z * (xx - yy);
+    Y[15] = -K3a * x * (xx - 3.0f * yy);
+    const int deg = S.sh_degree;
+    const int ncoef = (deg + 1) * (deg + 1);
+    float f[48];
+    const int nplanes = (3 * ncoef + 3) / 4;
+#pragma unroll
+    for (int k = 0; k < kShPlanes; ++k) {
+        float4 v = k < nplanes ? __ldg(S.sh + (long long)k * S.P + gid) : make_float4(0.f, 0.f, 0.f, 0.f);
+        f[4 * k] = v.x;
+        f[4 * k + 1] = v.y;
+        f[4 * k + 2] = v.z;
+        f[4 * k + 3] = v.w;
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc += (i < ncoef ? Y[i] : 0.0f) * f[3 * i + ch];
+        rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
+    }
+}
+
+// ------------------------------------------------------------------------------------------ geometry
+struct Geom {
+    float u, v, a, b, c, t, t_full, z, alpha0;
+    int tx0, tx1, ty0, ty1;
+};
+
+// Cull, project and build the conic of one Gaussian; false if it is culled or has no
+// candidate tile.  Binary32 evaluation order of the definition (see the header).
+__device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long gid, const Cam &cam,
+                                                  const Opts &o, Geom &G) {
+    const float4 po = __ldg(S.pos_opa + gid);
+    const float *R = cam.R;
+    float p[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float s = fmul(R[3 * i], po.x);
+        s = fadd(s, fmul(R[3 * i + 1], po.y));
+        s = fadd(s, fmul(R[3 * i + 2], po.z));
+        p[i] = fadd(s, cam.t[i]);
+    }
+    float alpha0 = S.activated ? po.w : fdiv(1.0f, fadd(1.0f, exp_rn(-po.w)));
+    if (!(p[2] > cam.near_z)) return false;
+    if (!(alpha0 > o.tau)) return false;
+    // Eq. 3: alpha0 exp(-q/2) >= tau  <=>  q <= 2 ln(alpha0 / tau)
+    const float t_full = fmul(2.0f, log_rn(fdiv(alpha0, o.tau)));
+    float t = t_full;
+    if (o.cap_3sigma && t > 9.0f) t = 9.0f;
+    // Sigma = R_q diag(s^2) R_q^T
+    const float4 sc = __ldg(S.scale + gid);
+    float s0 = sc.x, s1 = sc.y, s2 = sc.z;
+    if (!S.activated) {
+        s0 = exp_rn(s0);
+        s1 = exp_rn(s1);
+        s2 = exp_rn(s2);
+    }
+    const float4 q4 = __ldg(S.quat + gid);
+    float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+    float n2 = fmul(qw, qw);
+    n2 = fadd(n2, fmul(qx, qx));
+    n2 = fadd(n2, fmul(qy, qy));
+    n2 = fadd(n2, fmul(qz, qz));
+    if (!(n2 > 0.0f)) return false;
+    const float qn = fsqrt(n2);
+    qw = fdiv(qw, qn);
+    qx = fdiv(qx, qn);
+    qy = fdiv(qy, qn);
+    qz = fdiv(qz, qn);
+    const float yy = fmul(qy, qy), zz = fmul(qz, qz), xx = fmul(qx, qx);
+    const float xy = fmul(qx, qy), xz = fmul(qx, qz), yz = fmul(qy, qz);
+    const float wx = fmul(qw, qx), wy = fmul(qw, qy), wz = fmul(qw, qz);
+    float r[9];
+    r[0] = fsub(1.0f, fmul(2.0f, fadd(yy, zz)));
+    r[1] = fmul(2.0f, fsub(xy, wz));
+    r[2] = fmul(2.0f, fadd(xz, wy));
+    r[3] = fmul(2.0f, fadd(xy, wz));
+    r[4] = fsub(1.0f, fmul(2.0f, fadd(xx, zz)));
+    r[5] = fmul(2.0f, fsub(yz, wx));
+    r[6] = fmul(2.0f, fsub(xz, wy));
+    r[7] = fmul(2.0f, fadd(yz, wx));
+    r[8] = fsub(1.0f, fmul(2.0f, fadd(xx, yy)));
+    const float d0 = fmul(s0, s0), d1 = fmul(s1, s1), d2 = fmul(s2, s2);
+    float Sg[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            float acc = fmul(fmul(r[3 * i], d0), r[3 * j]);
+            acc = fadd(acc, fmul(fmul(r[3 * i + 1], d1), r[3 * j + 1]));
+            acc = fadd(acc, fmul(fmul(r[3 * i + 2], d2), r[3 * j + 2]));
+            Sg[3 * i + j] = acc;
+            Sg[3 * j + i] = acc;
+        }
+    // projection to pixel-area coordinates
+    const float u = fadd(fdiv(fmul(cam.fx, p[0]), p[2]), cam.cx);
+    const float v = fadd(fdiv(fmul(cam.fy, p[1]), p[2]), cam.cy);
+    // EWA Jacobian of the perspective map, with the 1.3 tan(half fov) clamp
+    float tx = p[0], ty = p[1];
+    if (o.clamp_fov) {
+        float txz = fdiv(p[0], p[2]), tyz = fdiv(p[1], p[2]);
+        txz = txz < -cam.limx ? -cam.limx : (txz > cam.limx ? cam.limx : txz);
+        tyz = tyz < -cam.limy ? -cam.limy : (tyz > cam.limy ? cam.limy : tyz);
+        tx = fmul(txz, p[2]);
+        ty = fmul(tyz, p[2]);
+    }
+    const float zsq = fmul(p[2], p[2]);
+    const float j00 = fdiv(cam.fx, p[2]);
+    const float j02 = -fdiv(fmul(cam.fx, tx), zsq);
+    const float j11 = fdiv(cam.fy, p[2]);
+    const float j12 = -fdiv(fmul(cam.fy, ty), zsq);
+    float M[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        M[k] = fadd(fmul(j00, R[k]), fmul(j02, R[6 + k]));
+        M[3 + k] = fadd(fmul(j11, R[3 + k]), fmul(j12, R[6 + k]));
+    }
+    float N[6];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float acc = fmul(M[3 * i], Sg[k]);
+            acc = fadd(acc, fmul(M[3 * i + 1], Sg[3 + k]));
+            acc = fadd(acc, fmul(M[3 * i + 2], Sg[6 + k]));
+            N[3 * i + k] = acc;
+        }
+    float s00 = fmul(N[0], M[0]);
+    s00 = fadd(s00, fmul(N[1], M[1]));
+    s00 = fadd(s00, fmul(N[2], M[2]));
+    s00 = fadd(s00, o.dilation);
+    float s01 = fmul(N[0], M[3]);
+    s01 = fadd(s01, fmul(N[1], M[4]));
+    s01 = fadd(s01, fmul(N[2], M[5]));
+    float s11 = fmul(N[3], M[3]);
+    s11 = fadd(s11, fmul(N[4], M[4]));
+    s11 = fadd(s11, fmul(N[5], M[5]));
+    s11 = fadd(s11, o.dilation);
+    const float det = fsub(fmul(s00, s11), fmul(s01, s01));
+    if (!(det > 0.0f)) return false;
+    G.a = fdiv(s11, det);
+    G.b = fdiv(-s01, det);
+    G.c = fdiv(s00, det);
+    // tight box of {q <= t}: half extents sqrt(t Sigma'00), sqrt(t Sigma'11), padded by 1 px
+    const float hx = fsqrt(fmul(t, s00));
+    const float hy = fsqrt(fmul(t, s11));
+    const float fx0 = floorf(fmul(fsub(fsub(u, hx), 1.0f), 0.0625f));
+    const float fx1 = floorf(fmul(fadd(fadd(u, hx), 1.0f), 0.0625f));
+    const float fy0 = floorf(fmul(fsub(fsub(v, hy), 1.0f), 0.0625f));
+    const float fy1 = floorf(fmul(fadd(fadd(v, hy), 1.0f), 0.0625f));
+    const float mxx = (float)(cam.tiles_x - 1), mxy = (float)(cam.tiles_y - 1);
+    if (!(fx1 >= 0.0f) || !(fy1 >= 0.0f) || !(fx0 <= mxx) || !(fy0 <= mxy)) return false;
+    G.tx0 = fx0 < 0.0f ? 0 : (int)fx0;
+    G.tx1 = fx1 > mxx ? cam.tiles_x - 1 : (int)fx1;
+    G.ty0 = fy0 < 0.0f ? 0 : (int)fy0;
+    G.ty1 = fy1 > mxy ? cam.tiles_y - 1 : (int)fy1;
+    G.u = u;
+    G.v = v;
+    G.t = t;
+    G.t_full = t_full;
+    G.z = p[2];
+    G.alpha0 = alpha0;
+    return true;
+}
+
+__device__ __forceinline__ bool test_tile(const Cam &cam, float u, float v, float a, float b, float c, float t,
+                                          int tx, int ty) {
+    float x0, x1, y0, y1;
+    tile_rect(cam, tx, ty, x0, x1, y0, y1);
+    return tile_hits(u, v, a, b, c, t, x0, x1, y0, y1);
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+    return *(const volatile unsigned long long *)p;
+}
+
+__device__ __forceinline__ void st_volatile_u64(unsigned long long *p, unsigned long long v) {
+    *(volatile unsigned long long *)p = v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Decoupled look-back over chunk descriptors (warp 0 of the CTA); returns the exclusive prefix.
+__device__ unsigned long long chunk_lookback(unsigned long long *desc, long long chunk, FrameCounters *ctr) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long excl = 0;
+    long long j = chunk - 1;
+    unsigned spins = 0;
+    bool timed_out = false;
+    while (true) {
+        const long long idx = j - lane;
+        unsigned long long d = idx >= 0 ? ld_volatile_u64(desc + idx) : kFlagPrefix;
+        while (__any_sync(0xffffffffu, (d >> 62) == 0)) {
+            if ((d >> 62) == 0) d = ld_volatile_u64(desc + idx);
+            if (++spins > kSpinLimit) {
+                timed_out = true;
+                break;
+            }
+            __nanosleep(32);
+        }
+        if (timed_out) {
+            if (lane == 0) atomicOr(&ctr->status, kStTimeout);
+            return excl;
+        }
+        const unsigned pm = __ballot_sync(0xffffffffu, (d >> 62) == 2);
+        unsigned long long val = d & kValMask;
+        if (pm) {
+            const int first = __ffs(pm) - 1;
+            excl += warp_sum_u64(lane <= first ? val : 0ull);
+            return excl;
+        }
+        excl += warp_sum_u64(val);
+        j -= 32;
+    }
+}
+
+// ------------------------------------------------------------------------------------------ kernel
+__global__ void __launch_bounds__(kPreBlock) k_preprocess(const __grid_constant__ PreprocessArgs A) {
+    __shared__ unsigned s_chunk;
+    __shared__ unsigned s_warp[kPreBlock / 32];
+    __shared__ unsigned s_vis[kPreBlock / 32];
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned FULL = 0xffffffffu;
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&A.ctr->chunk_ticket, 1u);
+    __syncthreads();
+    const long long chunk = s_chunk;
+    const long long gid = chunk * kPreBlock + threadIdx.x;
+    const Cam &cam = A.cam;
+
+    Geom G;
+    bool valid = false;
+    if (gid < A.scene.P) valid = gaussian_geometry(A.scene, gid, cam, A.opt, G);
+    const int w = valid ? G.tx1 - G.tx0 + 1 : 0;
+    const int ncand = valid ? w * (G.ty1 - G.ty0 + 1) : 0;
+
+    // ---- exact tests: count hits
+    unsigned count = 0, mask = 0;
+    if (ncand == 1) {
+        mask = test_tile(cam, G.u, G.v, G.a, G.b, G.c, G.t, G.tx0, G.ty0) ? 1u : 0u;
+        count = mask;
+    }
+    unsigned multi = __ballot_sync(FULL, ncand > 1);
+    while (multi) {
+        const int src = __ffs(multi) - 1;
+        multi &= multi - 1;
+        const float su = __shfl_sync(FULL, G.u, src), sv = __shfl_sync(FULL, G.v, src);
+        const float sa = __shfl_sync(FULL, G.a, src), sb = __shfl_sync(FULL, G.b, src);
+        const float scc = __shfl_sync(FULL, G.c, src), st = __shfl_sync(FULL, G.t, src);
+        const int stx0 = __shfl_sync(FULL, G.tx0, src), sty0 = __shfl_sync(FULL, G.ty0, src);
+        const int sw = __shfl_sync(FULL, w, src), sn = __shfl_sync(FULL, ncand, src);
+        unsigned total = 0;
+        for (int base = 0; base < sn; base += 32) {
+            const int k = base + lane;
+            bool hit = false;
+            if (k < sn) hit = test_tile(cam, su, sv, sa, sb, scc, st, stx0 + k % sw, sty0 + k / sw);
+            const unsigned bal = __ballot_sync(FULL, hit);
+            total += __popc(bal);
+            if (base == 0 && lane == src) mask = bal;
+        }
+        if (lane == src) count = total;
+    }
+
+    // ---- block scan of counts
+    unsigned incl = count;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned vis = __popc(__ballot_sync(FULL, count > 0));
+    if (lane == 31) s_warp[warp] = incl;
+    if (lane == 0) s_vis[warp] = vis;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned wt = lane < kPreBlock / 32 ? s_warp[lane] : 0u;
+        unsigned vt = lane < kPreBlock / 32 ? s_vis[lane] : 0u;
+        unsigned wi = wt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += y;
+            vt += __shfl_xor_sync(FULL, vt, o);
+        }
+        const unsigned long long block_total = __shfl_sync(FULL, wi, 31);
+        if (lane < kPreBlock / 32) s_warp[lane] = wi - wt;   // exclusive warp offsets
+        if (lane == 0) {
+            if (vt) atomicAdd(&A.ctr->n_visible, vt);
+            __threadfence();
+            st_volatile_u64(A.scan_desc + chunk, (chunk == 0 ? kFlagPrefix : kFlagAgg) | block_total);
+        }
+        unsigned long long excl = 0;
+        if (chunk > 0) excl = chunk_lookback(A.scan_desc, chunk, A.ctr);
+        if (lane == 0) {
+            if (chunk > 0) st_volatile_u64(A.scan_desc + chunk, kFlagPrefix | (excl + block_total));
+            s_base = excl;
+            if (chunk == A.n_chunks - 1) {
+                const unsigned long long n = excl + block_total;
+                A.ctr->n_pairs = n;
+                if ((long long)n > A.pair_cap) atomicOr(&A.ctr->status, kStPairOverflow);
+            }
+        }
+    }
+    __syncthreads();
+    const unsigned long long off = s_base + s_warp[warp] + (incl - count);
+    const long long cap = A.pair_cap;
+
+    // ---- emission
+    const unsigned long long zbits = valid ? (unsigned long long)__float_as_uint(G.z) : 0ull;
+    if (ncand == 1 && count) {
+        if ((long long)off < cap) {
+            A.keys[off] = ((unsigned long long)(G.ty0 * cam.tiles_x + G.tx0) << 32) | zbits;
+            A.vals[off] = (unsigned)gid;
+        }
+    }
+    multi = __ballot_sync(FULL, ncand > 1 && count > 0);
+    while (multi) {
+        const int src = __ffs(multi) - 1;
+        multi &= multi - 1;
+        const int sn = __shfl_sync(FULL, ncand, src);
+        const int sw = __shfl_sync(FULL, w, src);
+        const int stx0 = __shfl_sync(FULL, G.tx0, src), sty0 = __shfl_sync(FULL, G.ty0, src);
+        const unsigned long long soff = __shfl_sync(FULL, off, src);
+        const unsigned long long sz = __shfl_sync(FULL, zbits, src);
+        const unsigned sgid = (unsigned)(chunk * kPreBlock + warp * 32 + src);
+        if (sn <= 32) {
+            const unsigned smask = __shfl_sync(FULL, mask, src);
+            if ((smask >> lane) & 1u) {
+                const unsigned long long pos = soff + __popc(smask & ((1u << lane) - 1u));
+                const int tx = stx0 + lane % sw, ty = sty0 + lane / sw;
+                if ((long long)pos < cap) {
+                    A.keys[pos] = ((unsigned long long)(ty * cam.tiles_x + tx) << 32) | sz;
+                    A.vals[pos] = sgid;
+                }
+            }
+        } else {
+            const float su = __shfl_sync(FULL, G.u, src), sv = __shfl_sync(FULL, G.v, src);
+            const float sa = __shfl_sync(FULL, G.a, src), sb = __shfl_sync(FULL, G.b, src);
+            const float scc = __shfl_sync(FULL, G.c, src), st = __shfl_sync(FULL, G.t, src);
+            unsigned long long run = soff;
+            for (int base = 0; base < sn; base += 32) {
+                const int k = base + lane;
+                bool hit = false;
+                const int tx = k < sn ? stx0 + k % sw : 0, ty = k < sn ? sty0 + k / sw : 0;
+                if (k < sn) hit = test_tile(cam, su, sv, sa, sb, scc, st, tx, ty);
+                const unsigned bal = __ballot_sync(FULL, hit);
+                if (hit) {
+                    const unsigned long long pos = run + __popc(bal & ((1u << lane) - 1u));
+                    if ((long long)pos < cap) {
+                        A.keys[pos] = ((unsigned long long)(ty * cam.tiles_x + tx) << 32) | sz;
+                        A.vals[pos] = sgid;
+                    }
+                }
+                run += __popc(bal);
+            }
+        }
+    }
+
+    // ---- render record of paired Gaussians
+    if (count > 0) {
+        const float4 po = __ldg(A.scene.pos_opa + gid);
+        float rgb[3];
+        sh_colour(A.scene, gid, cam, po.x, po.y, po.z, rgb);
+        const float LOG2E = 1.4426950408889634f;
+        const float Gl = log_rn(G.alpha0) * LOG2E;
+        Rec rc;
+        rc.r0 = make_float4(G.u, G.v, G.a, G.b + G.b);
+        rc.r1 = make_float4(G.c, G.t, Gl, rgb[0]);
+        rc.r2 = make_float4(rgb[1], rgb[2], G.z, G.alpha0);
+        A.recs[gid] = rc;
+    }
+}
+
+void launch_preprocess(const PreprocessArgs &a, cudaStream_t s) {
+    if (a.n_chunks <= 0) return;
+    k_preprocess<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+}
+
+}  // namespace gs
