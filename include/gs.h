@@ -93,6 +93,10 @@ typedef struct {
     int32_t width, height;
     int32_t tiles_x, tiles_y;
     int32_t sort_passes;    /* 8-bit digit passes of the last sort */
+    int64_t culled_in;      /* Gaussians passing the near-plane and opacity cull */
+    int64_t evaluations;    /* (pixel, list entry) evaluations of the last gs_blend */
+    int32_t kernels;        /* kernels one gs_render launches */
+    int32_t pad;
 } gs_frame_stats;
 
 /* Message for the last error returned on the calling thread ("" if none). */
@@ -166,6 +170,35 @@ gs_status gs_render(gs_frame *frame, const gs_scene *scene, const gs_camera *cam
 
 /* Enables (1) or disables (0) CUDA-graph replay of gs_render on this frame. */
 gs_status gs_frame_use_graph(gs_frame *frame, int32_t enable);
+
+/* Launch-shape choices of a frame (picked by the autotuner in the Python package):
+   blend_variant 0..5 = (pixels per thread, records per staged batch) of (1, 256), (2, 128),
+   (4, 128), (2, 256), (4, 64), (4, 256); 256 / pixels-per-thread threads per 16x16 tile.
+   Results are bit-identical across variants.  GS_ERR_INVALID_ARG for out-of-range values. */
+typedef struct {
+    int32_t blend_variant;
+    int32_t reserved[7];
+} gs_tuning;
+gs_status gs_frame_set_tuning(gs_frame *frame, const gs_tuning *tuning);
+gs_status gs_frame_get_tuning(const gs_frame *frame, gs_tuning *tuning);
+
+/* Enables (1) or disables (0) CUDA events around the four stages of gs_render (recorded inside
+   the graph when graphs are enabled). */
+gs_status gs_frame_enable_timing(gs_frame *frame, int32_t enable);
+
+/* Waits for the last timed gs_render and writes the device time of its stages in milliseconds:
+   ms[0] preprocess, ms[1] sort, ms[2] ranges, ms[3] blend.  GS_ERR_INVALID_ARG when timing is
+   off or nothing was timed yet. */
+gs_status gs_frame_stage_ms(gs_frame *frame, float ms[4]);
+
+/* gs_render into buffers owned by the frame, then copies the result to HOST memory: rgb_host
+   [3,H,W] float, T_host [H,W] float (nullable), last_host [H,W] uint32 (nullable); `cam` and
+   `opts` are host structs passed by value to the kernels.  The copies are enqueued on `stream`
+   (asynchronous when the host buffers are page-locked); the call returns without waiting --
+   synchronise `stream` before reading the host buffers.  Errors: as gs_render. */
+gs_status gs_render_host(gs_frame *frame, const gs_scene *scene, const gs_camera *cam,
+                         const gs_render_opts *opts, float *rgb_host, float *T_host, uint32_t *last_host,
+                         gs_stream stream);
 
 /* Synchronises `stream` and reads the frame's counters.  status carries device-side errors:
    GS_ERR_PAIR_OVERFLOW when more pairs were found than max_pairs (outputs are then invalid;

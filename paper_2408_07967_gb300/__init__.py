@@ -188,6 +188,31 @@ class Frame:
     def gs_frame_use_graph(self, enable: bool):
         _check(lib().gs_frame_use_graph(self.h, int(bool(enable))))
 
+    def gs_frame_set_tuning(self, blend_variant: int):
+        t = _native.gs_tuning()
+        t.blend_variant = int(blend_variant)
+        _check(lib().gs_frame_set_tuning(self.h, C.byref(t)))
+
+    def gs_frame_get_tuning(self) -> dict:
+        t = _native.gs_tuning()
+        _check(lib().gs_frame_get_tuning(self.h, C.byref(t)))
+        return {"blend_variant": t.blend_variant}
+
+    def gs_frame_enable_timing(self, enable: bool):
+        _check(lib().gs_frame_enable_timing(self.h, int(bool(enable))))
+
+    def gs_frame_stage_ms(self):
+        ms = (C.c_float * 4)()
+        _check(lib().gs_frame_stage_ms(self.h, ms))
+        return list(ms)
+
+    def gs_render_host(self, scene: Scene, cam, rgb_host, T_host=None, last_host=None, opts=None, stream=None):
+        """Render and copy into host tensors (page-locked for asynchronous copies)."""
+        o = opts or gs_opts()
+        hp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        _check(lib().gs_render_host(self.h, scene.h, C.byref(gs_camera_from(cam)), C.byref(o), hp(rgb_host),
+                                    hp(T_host), hp(last_host), _stream(stream)))
+
     # ---- conveniences
     def render(self, scene: Scene, cam, opts=None, stream=None, want_T=True, want_last=True):
         import torch

@@ -111,6 +111,12 @@ struct gs_frame {
     // graph replay
     int use_graph = 0;
     cudaGraphExec_t exec = nullptr;
+    // stage timing
+    int timing = 0, timed = 0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // frame-owned outputs for gs_render_host (allocated on first use)
+    void *out_mem = nullptr;
+    gs_tuning tuning{2, {0, 0, 0, 0, 0, 0, 0}};
 };
 
 extern "C" {
@@ -301,6 +307,9 @@ gs_status gs_frame_destroy(gs_frame *f) {
     cudaSetDevice(f->ctx->device);
     cudaDeviceSynchronize();
     if (f->exec) cudaGraphExecDestroy(f->exec);
+    for (int i = 0; i < 5; ++i)
+        if (f->ev[i]) cudaEventDestroy(f->ev[i]);
+    cudaFree(f->out_mem);
     cudaFree(f->mem);
     delete f;
     return GS_OK;
@@ -311,6 +320,47 @@ int64_t gs_frame_bytes(const gs_frame *f) { return f ? (int64_t)f->bytes : 0; }
 gs_status gs_frame_use_graph(gs_frame *f, int32_t enable) {
     if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
     f->use_graph = enable ? 1 : 0;
+    return GS_OK;
+}
+
+gs_status gs_frame_set_tuning(gs_frame *f, const gs_tuning *t) {
+    if (!f || !t) return fail(GS_ERR_INVALID_ARG, "NULL frame or tuning");
+    if (t->blend_variant < 0 || t->blend_variant >= blend_variant_count())
+        return fail(GS_ERR_INVALID_ARG, "blend_variant %d out of range", t->blend_variant);
+    if (t->blend_variant != f->tuning.blend_variant && f->exec) {
+        cudaGraphExecDestroy(f->exec);
+        f->exec = nullptr;
+    }
+    f->tuning = *t;
+    return GS_OK;
+}
+
+gs_status gs_frame_get_tuning(const gs_frame *f, gs_tuning *t) {
+    if (!f || !t) return fail(GS_ERR_INVALID_ARG, "NULL frame or tuning");
+    *t = f->tuning;
+    return GS_OK;
+}
+
+gs_status gs_frame_enable_timing(gs_frame *f, int32_t enable) {
+    if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
+    if (enable && !f->ev[0]) {
+        GS_CUDA(cudaSetDevice(f->ctx->device));
+        for (int i = 0; i < 5; ++i) GS_CUDA(cudaEventCreate(&f->ev[i]));
+    }
+    if (f->timing != (enable ? 1 : 0) && f->exec) {   // topology changes: re-instantiate the graph
+        cudaGraphExecDestroy(f->exec);
+        f->exec = nullptr;
+    }
+    f->timing = enable ? 1 : 0;
+    f->timed = 0;
+    return GS_OK;
+}
+
+gs_status gs_frame_stage_ms(gs_frame *f, float ms[4]) {
+    if (!f || !ms) return fail(GS_ERR_INVALID_ARG, "NULL frame or ms");
+    if (!f->timing || !f->timed) return fail(GS_ERR_INVALID_ARG, "no timed render on this frame");
+    GS_CUDA(cudaEventSynchronize(f->ev[4]));
+    for (int i = 0; i < 4; ++i) GS_CUDA(cudaEventElapsedTime(&ms[i], f->ev[i], f->ev[i + 1]));
     return GS_OK;
 }
 
@@ -409,18 +459,44 @@ gs_status gs_blend(gs_frame *f, const gs_render_opts *opts, float *rgb, float *T
     a.rgb = rgb;
     a.T = T;
     a.last = last;
+    a.evals = &f->ctr->evals;
+    a.variant = f->tuning.blend_variant;
+    GS_CUDA(cudaMemsetAsync(&f->ctr->evals, 0, sizeof(unsigned long long), (cudaStream_t)stream));
     launch_blend(a, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
+// Records stage event i; inside a stream capture the record must become an event node of the
+// graph (cudaEventRecordExternal), otherwise the event is only a capture dependency.
+static gs_status record_stage(gs_frame *f, int i, cudaStream_t cs) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GS_CUDA(cudaStreamIsCapturing(cs, &cap));
+    if (cap == cudaStreamCaptureStatusActive)
+        GS_CUDA(cudaEventRecordWithFlags(f->ev[i], cs, cudaEventRecordExternal));
+    else
+        GS_CUDA(cudaEventRecord(f->ev[i], cs));
+    return GS_OK;
+}
+
 static gs_status enqueue_all(gs_frame *f, const gs_scene *s, const gs_camera *cam, const gs_render_opts *opts,
                              float *rgb, float *T, uint32_t *last, gs_stream stream) {
-    gs_status st = gs_preprocess(f, s, cam, opts, stream);
-    if (st) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const bool tm = f->timing != 0;
+    gs_status st;
+    if (tm && (st = record_stage(f, 0, cs))) return st;
+    if ((st = gs_preprocess(f, s, cam, opts, stream))) return st;
+    if (tm && (st = record_stage(f, 1, cs))) return st;
     if ((st = gs_sort(f, stream))) return st;
+    if (tm && (st = record_stage(f, 2, cs))) return st;
     if ((st = gs_ranges(f, stream))) return st;
-    return gs_blend(f, opts, rgb, T, last, stream);
+    if (tm && (st = record_stage(f, 3, cs))) return st;
+    if ((st = gs_blend(f, opts, rgb, T, last, stream))) return st;
+    if (tm) {
+        if ((st = record_stage(f, 4, cs))) return st;
+        f->timed = 1;
+    }
+    return GS_OK;
 }
 
 gs_status gs_render(gs_frame *f, const gs_scene *s, const gs_camera *cam, const gs_render_opts *opts, float *rgb,
@@ -476,6 +552,30 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     out->tiles_x = f->tiles_x;
     out->tiles_y = f->tiles_y;
     out->sort_passes = f->passes;
+    out->culled_in = c.n_culled_in;
+    out->evaluations = (int64_t)c.evals;
+    out->kernels = 5 + f->passes;
+    return GS_OK;
+}
+
+gs_status gs_render_host(gs_frame *f, const gs_scene *s, const gs_camera *cam, const gs_render_opts *opts,
+                         float *rgb_host, float *T_host, uint32_t *last_host, gs_stream stream) {
+    if (!f || !cam || !rgb_host) return fail(GS_ERR_INVALID_ARG, "NULL frame, camera or rgb_host");
+    const size_t npx = (size_t)f->max_w * (size_t)f->max_h;
+    if (!f->out_mem) {
+        GS_CUDA(cudaSetDevice(f->ctx->device));
+        GS_CUDA(cudaMalloc(&f->out_mem, npx * 5 * sizeof(float)));
+    }
+    float *rgb = (float *)f->out_mem;
+    float *T = rgb + 3 * npx;
+    uint32_t *last = (uint32_t *)(T + npx);
+    gs_status st = gs_render(f, s, cam, opts, rgb, T_host ? T : nullptr, last_host ? last : nullptr, stream);
+    if (st) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const size_t n = (size_t)cam->width * (size_t)cam->height;
+    GS_CUDA(cudaMemcpyAsync(rgb_host, rgb, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, cs));
+    if (T_host) GS_CUDA(cudaMemcpyAsync(T_host, T, n * sizeof(float), cudaMemcpyDeviceToHost, cs));
+    if (last_host) GS_CUDA(cudaMemcpyAsync(last_host, last, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
     return GS_OK;
 }
 

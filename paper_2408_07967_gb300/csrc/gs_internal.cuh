@@ -59,13 +59,15 @@ struct Rec {
     float4 r0, r1, r2;
 };
 
-// Device counters of one frame.
+// Device counters of one frame.  Everything before sort_epoch is cleared at the start of every
+// frame; sort_epoch only grows (it tags the sort's look-back descriptors).
 struct FrameCounters {
     unsigned long long n_pairs;      // pairs found by preprocess (may exceed capacity)
+    unsigned long long evals;        // (pixel, entry) evaluations of the last blend
     unsigned int n_visible;          // Gaussians with >= 1 pair
+    unsigned int n_culled_in;        // Gaussians passing the near-plane / opacity cull
     unsigned int status;             // kSt* bits
     unsigned int chunk_ticket;       // preprocess chunk ticket
-    unsigned int pad0;
     unsigned int sort_ticket[8];     // scatter-pass tickets
     unsigned int sort_epoch;         // bumped once per sort; tags look-back descriptors
     unsigned int pad1[7];
@@ -242,7 +244,10 @@ struct BlendArgs {
     float *rgb;
     float *T;
     unsigned *last;
+    unsigned long long *evals;
+    int variant;                     // launch shape, see launch_blend
 };
 void launch_blend(const BlendArgs &a, cudaStream_t s);
+int blend_variant_count();
 
 }  // namespace gs

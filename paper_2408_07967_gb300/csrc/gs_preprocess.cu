@@ -3,16 +3,19 @@
 // opacity-aware threshold of Eq. 2-3 and the tight bounding box of Section 4.1).
 //
 // One CTA handles a chunk of 256 consecutive Gaussians:
-//   1. each thread culls and projects its Gaussian and finds its candidate tiles;
-//   2. exact tile tests: a one-tile Gaussian stays on its thread, a multi-tile Gaussian is
-//      tested by the whole warp, 32 candidate tiles per step (Section 5.1.2); the warp's
-//      ballot gives the hit mask;
-//   3. a block scan of the per-Gaussian pair counts and a decoupled look-back across chunks
-//      (chunk order fixed by an atomic ticket, waits bounded) give every Gaussian its output
-//      offset, so pairs land in (Gaussian id, tile row-major) order -- deterministic, unlike
-//      the paper's atomicAdd slots;
-//   4. keys/values are written; the SH colour is evaluated and the render record stored only
-//      for Gaussians with at least one pair (Algorithm 4, last step).
+//   1. each thread culls and projects its Gaussian and finds its candidate tiles (tight box);
+//   2. exact tile tests, load-balanced over the whole CTA: a block scan of the candidate counts
+//      numbers every (Gaussian, candidate tile) slot, and each step the 256 threads test 256
+//      consecutive slots, whatever Gaussians they belong to.  This generalises the paper's
+//      size-aware remapping of a large ellipse onto a warp (Section 5.1.2) to any mix of sizes,
+//      so one Gaussian covering thousands of tiles no longer serialises a warp;
+//   3. the CTA's hit count goes through a decoupled look-back across chunks (chunk order fixed
+//      by an atomic ticket, waits bounded) to give the CTA its output offset;
+//   4. the tests are repeated and every hit is written at offset + its rank in slot order,
+//      i.e. pairs land in (Gaussian id, tile row-major) order -- deterministic, unlike the
+//      paper's atomicAdd slots;
+//   5. the SH colour is evaluated and the render record stored only for Gaussians with at
+//      least one pair (Algorithm 4, last step).
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -119,7 +122,7 @@ struct Geom {
 // Cull, project and build the conic of one Gaussian; false if it is culled or has no
 // candidate tile.  Binary32 evaluation order of the definition (see the header).
 __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long gid, const Cam &cam,
-                                                  const Opts &o, Geom &G) {
+                                                  const Opts &o, Geom &G, bool &passed_cull) {
     const float4 po = __ldg(S.pos_opa + gid);
     const float *R = cam.R;
     float p[3];
@@ -133,6 +136,7 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
     float alpha0 = S.activated ? po.w : fdiv(1.0f, fadd(1.0f, exp_rn(-po.w)));
     if (!(p[2] > cam.near_z)) return false;
     if (!(alpha0 > o.tau)) return false;
+    passed_cull = true;
     // Eq. 3: alpha0 exp(-q/2) >= tau  <=>  q <= 2 ln(alpha0 / tau)
     const float t_full = fmul(2.0f, log_rn(fdiv(alpha0, o.tau)));
     float t = t_full;
@@ -309,77 +313,108 @@ __device__ unsigned long long chunk_lookback(unsigned long long *desc, long long
 }
 
 // ------------------------------------------------------------------------------------------ kernel
-__global__ void __launch_bounds__(kPreBlock) k_preprocess(const __grid_constant__ PreprocessArgs A) {
-    __shared__ unsigned s_chunk;
-    __shared__ unsigned s_warp[kPreBlock / 32];
-    __shared__ unsigned s_vis[kPreBlock / 32];
-    __shared__ unsigned long long s_base;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+struct PreSmem {
+    float u[kPreBlock], v[kPreBlock], a[kPreBlock], b[kPreBlock], c[kPreBlock], t[kPreBlock];
+    unsigned zb[kPreBlock];
+    int tx0[kPreBlock], ty0[kPreBlock], w[kPreBlock];
+    int cstart[kPreBlock + 1];        // exclusive scan of candidate-tile counts
+    unsigned char any[kPreBlock];     // Gaussian has at least one pair
+    unsigned wsum[kPreBlock / 32];
+    unsigned long long base;
+    unsigned chunk;
+};
+
+// Candidate slot -> (Gaussian g of the CTA, tile); slot s belongs to the last g with
+// cstart[g] <= s, and is its k-th candidate tile in row-major order.
+__device__ __forceinline__ bool slot_test(const PreSmem &S, const Cam &cam, int slot, int &g_out, int &tile) {
+    int lo = 0, hi = kPreBlock - 1;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.cstart[mid] <= slot)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int g = lo;
+    const int k = slot - S.cstart[g];
+    const int w = S.w[g];
+    const int dy = k / w;
+    const int tx = S.tx0[g] + (k - dy * w), ty = S.ty0[g] + dy;
+    g_out = g;
+    tile = ty * cam.tiles_x + tx;
+    return test_tile(cam, S.u[g], S.v[g], S.a[g], S.b[g], S.c[g], S.t[g], tx, ty);
+}
+
+__global__ void __launch_bounds__(kPreBlock, 3) k_preprocess(const __grid_constant__ PreprocessArgs A) {
+    __shared__ PreSmem S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
-    if (threadIdx.x == 0) s_chunk = atomicAdd(&A.ctr->chunk_ticket, 1u);
+    if (tid == 0) S.chunk = atomicAdd(&A.ctr->chunk_ticket, 1u);
     __syncthreads();
-    const long long chunk = s_chunk;
-    const long long gid = chunk * kPreBlock + threadIdx.x;
+    const long long chunk = S.chunk;
+    const long long gid = chunk * kPreBlock + tid;
     const Cam &cam = A.cam;
 
+    // ---- per-Gaussian geometry (one Gaussian per thread)
     Geom G;
-    bool valid = false;
-    if (gid < A.scene.P) valid = gaussian_geometry(A.scene, gid, cam, A.opt, G);
+    bool valid = false, passed_cull = false;
+    if (gid < A.scene.P) valid = gaussian_geometry(A.scene, gid, cam, A.opt, G, passed_cull);
+    const unsigned n_in = __popc(__ballot_sync(FULL, passed_cull));
+    if (lane == 0 && n_in) atomicAdd(&A.ctr->n_culled_in, n_in);
     const int w = valid ? G.tx1 - G.tx0 + 1 : 0;
     const int ncand = valid ? w * (G.ty1 - G.ty0 + 1) : 0;
-
-    // ---- exact tests: count hits
-    unsigned count = 0, mask = 0;
-    if (ncand == 1) {
-        mask = test_tile(cam, G.u, G.v, G.a, G.b, G.c, G.t, G.tx0, G.ty0) ? 1u : 0u;
-        count = mask;
+    if (valid) {
+        S.u[tid] = G.u;
+        S.v[tid] = G.v;
+        S.a[tid] = G.a;
+        S.b[tid] = G.b;
+        S.c[tid] = G.c;
+        S.t[tid] = G.t;
+        S.zb[tid] = __float_as_uint(G.z);
+        S.tx0[tid] = G.tx0;
+        S.ty0[tid] = G.ty0;
     }
-    unsigned multi = __ballot_sync(FULL, ncand > 1);
-    while (multi) {
-        const int src = __ffs(multi) - 1;
-        multi &= multi - 1;
-        const float su = __shfl_sync(FULL, G.u, src), sv = __shfl_sync(FULL, G.v, src);
-        const float sa = __shfl_sync(FULL, G.a, src), sb = __shfl_sync(FULL, G.b, src);
-        const float scc = __shfl_sync(FULL, G.c, src), st = __shfl_sync(FULL, G.t, src);
-        const int stx0 = __shfl_sync(FULL, G.tx0, src), sty0 = __shfl_sync(FULL, G.ty0, src);
-        const int sw = __shfl_sync(FULL, w, src), sn = __shfl_sync(FULL, ncand, src);
-        unsigned total = 0;
-        for (int base = 0; base < sn; base += 32) {
-            const int k = base + lane;
-            bool hit = false;
-            if (k < sn) hit = test_tile(cam, su, sv, sa, sb, scc, st, stx0 + k % sw, sty0 + k / sw);
-            const unsigned bal = __ballot_sync(FULL, hit);
-            total += __popc(bal);
-            if (base == 0 && lane == src) mask = bal;
-        }
-        if (lane == src) count = total;
-    }
+    S.w[tid] = w > 0 ? w : 1;
+    S.any[tid] = 0;
 
-    // ---- block scan of counts
-    unsigned incl = count;
+    // ---- block exclusive scan of candidate counts
+    int incl = ncand;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(FULL, incl, o);
+        const int y = __shfl_up_sync(FULL, incl, o);
         if (lane >= o) incl += y;
     }
-    const unsigned vis = __popc(__ballot_sync(FULL, count > 0));
-    if (lane == 31) s_warp[warp] = incl;
-    if (lane == 0) s_vis[warp] = vis;
+    if (lane == 31) S.wsum[warp] = (unsigned)incl;
     __syncthreads();
-    if (warp == 0) {
-        unsigned wt = lane < kPreBlock / 32 ? s_warp[lane] : 0u;
-        unsigned vt = lane < kPreBlock / 32 ? s_vis[lane] : 0u;
-        unsigned wi = wt;
+    int wex = 0, ctotal = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(FULL, wi, o);
-            if (lane >= o) wi += y;
-            vt += __shfl_xor_sync(FULL, vt, o);
+    for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
+        const int x = (int)S.wsum[w2];
+        wex += w2 < warp ? x : 0;
+        ctotal += x;
+    }
+    S.cstart[tid] = wex + incl - ncand;
+    if (tid == 0) S.cstart[kPreBlock] = ctotal;
+    __syncthreads();
+
+    // ---- exact tests, load-balanced over all candidate tiles of the CTA: count hits
+    unsigned hits = 0;
+    for (int base = 0; base < ctotal; base += kPreBlock) {
+        const int slot = base + tid;
+        bool hit = false;
+        if (slot < ctotal) {
+            int g, tile;
+            hit = slot_test(S, cam, slot, g, tile);
+            if (hit) S.any[g] = 1;
         }
-        const unsigned long long block_total = __shfl_sync(FULL, wi, 31);
-        if (lane < kPreBlock / 32) s_warp[lane] = wi - wt;   // exclusive warp offsets
+        hits += (unsigned)__syncthreads_count(hit);
+    }
+
+    // ---- chained scan across CTAs (decoupled look-back, warp 0)
+    if (warp == 0) {
+        const unsigned long long block_total = hits;
         if (lane == 0) {
-            if (vt) atomicAdd(&A.ctr->n_visible, vt);
             __threadfence();
             st_volatile_u64(A.scan_desc + chunk, (chunk == 0 ? kFlagPrefix : kFlagAgg) | block_total);
         }
@@ -387,7 +422,7 @@ __global__ void __launch_bounds__(kPreBlock) k_preprocess(const __grid_constant_
         if (chunk > 0) excl = chunk_lookback(A.scan_desc, chunk, A.ctr);
         if (lane == 0) {
             if (chunk > 0) st_volatile_u64(A.scan_desc + chunk, kFlagPrefix | (excl + block_total));
-            s_base = excl;
+            S.base = excl;
             if (chunk == A.n_chunks - 1) {
                 const unsigned long long n = excl + block_total;
                 A.ctr->n_pairs = n;
@@ -396,62 +431,42 @@ __global__ void __launch_bounds__(kPreBlock) k_preprocess(const __grid_constant_
         }
     }
     __syncthreads();
-    const unsigned long long off = s_base + s_warp[warp] + (incl - count);
-    const long long cap = A.pair_cap;
 
-    // ---- emission
-    const unsigned long long zbits = valid ? (unsigned long long)__float_as_uint(G.z) : 0ull;
-    if (ncand == 1 && count) {
-        if ((long long)off < cap) {
-            A.keys[off] = ((unsigned long long)(G.ty0 * cam.tiles_x + G.tx0) << 32) | zbits;
-            A.vals[off] = (unsigned)gid;
+    // ---- emission: the CTA's pairs are [base, base + hits) in slot order
+    const long long cap = A.pair_cap;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long run = S.base;
+    for (int base = 0; base < ctotal; base += kPreBlock) {
+        const int slot = base + tid;
+        bool hit = false;
+        int g = 0, tile = 0;
+        if (slot < ctotal) hit = slot_test(S, cam, slot, g, tile);
+        const unsigned bal = __ballot_sync(FULL, hit);
+        if (lane == 0) S.wsum[warp] = __popc(bal);
+        __syncthreads();
+        unsigned wpre = 0, tot = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
+            const unsigned x = S.wsum[w2];
+            wpre += w2 < warp ? x : 0u;
+            tot += x;
         }
-    }
-    multi = __ballot_sync(FULL, ncand > 1 && count > 0);
-    while (multi) {
-        const int src = __ffs(multi) - 1;
-        multi &= multi - 1;
-        const int sn = __shfl_sync(FULL, ncand, src);
-        const int sw = __shfl_sync(FULL, w, src);
-        const int stx0 = __shfl_sync(FULL, G.tx0, src), sty0 = __shfl_sync(FULL, G.ty0, src);
-        const unsigned long long soff = __shfl_sync(FULL, off, src);
-        const unsigned long long sz = __shfl_sync(FULL, zbits, src);
-        const unsigned sgid = (unsigned)(chunk * kPreBlock + warp * 32 + src);
-        if (sn <= 32) {
-            const unsigned smask = __shfl_sync(FULL, mask, src);
-            if ((smask >> lane) & 1u) {
-                const unsigned long long pos = soff + __popc(smask & ((1u << lane) - 1u));
-                const int tx = stx0 + lane % sw, ty = sty0 + lane / sw;
-                if ((long long)pos < cap) {
-                    A.keys[pos] = ((unsigned long long)(ty * cam.tiles_x + tx) << 32) | sz;
-                    A.vals[pos] = sgid;
-                }
-            }
-        } else {
-            const float su = __shfl_sync(FULL, G.u, src), sv = __shfl_sync(FULL, G.v, src);
-            const float sa = __shfl_sync(FULL, G.a, src), sb = __shfl_sync(FULL, G.b, src);
-            const float scc = __shfl_sync(FULL, G.c, src), st = __shfl_sync(FULL, G.t, src);
-            unsigned long long run = soff;
-            for (int base = 0; base < sn; base += 32) {
-                const int k = base + lane;
-                bool hit = false;
-                const int tx = k < sn ? stx0 + k % sw : 0, ty = k < sn ? sty0 + k / sw : 0;
-                if (k < sn) hit = test_tile(cam, su, sv, sa, sb, scc, st, tx, ty);
-                const unsigned bal = __ballot_sync(FULL, hit);
-                if (hit) {
-                    const unsigned long long pos = run + __popc(bal & ((1u << lane) - 1u));
-                    if ((long long)pos < cap) {
-                        A.keys[pos] = ((unsigned long long)(ty * cam.tiles_x + tx) << 32) | sz;
-                        A.vals[pos] = sgid;
-                    }
-                }
-                run += __popc(bal);
+        if (hit) {
+            const unsigned long long pos = run + wpre + __popc(bal & lt);
+            if ((long long)pos < cap) {
+                A.keys[pos] = ((unsigned long long)(unsigned)tile << 32) | S.zb[g];
+                A.vals[pos] = (unsigned)(chunk * kPreBlock + g);
             }
         }
+        run += tot;
+        __syncthreads();
     }
 
     // ---- render record of paired Gaussians
-    if (count > 0) {
+    const bool vis = S.any[tid] != 0;
+    const unsigned nvis = __popc(__ballot_sync(FULL, vis));
+    if (lane == 0 && nvis) atomicAdd(&A.ctr->n_visible, nvis);
+    if (vis) {
         const float4 po = __ldg(A.scene.pos_opa + gid);
         float rgb[3];
         sh_colour(A.scene, gid, cam, po.x, po.y, po.z, rgb);

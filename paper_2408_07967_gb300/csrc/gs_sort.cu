@@ -85,7 +85,7 @@ struct ScatterSmem {
     unsigned tile;
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const unsigned long long *__restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const unsigned long long *__restrict__ kin,
                                                                const unsigned *__restrict__ vin,
                                                                unsigned long long *__restrict__ kout,
                                                                unsigned *__restrict__ vout,

@@ -29,9 +29,11 @@ def ctx():
     return gs.Context(0)
 
 
-def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False):
+def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False, variant=None):
     sc = gs.Scene.from_numpy(ctx, scene)
     fr = gs.Frame(ctx, scene.P, max_pairs, cam.width, cam.height)
+    if variant is not None:
+        fr.gs_frame_set_tuning(variant)
     o = gs.gs_opts(**(opts_kw or {}))
     H, W = cam.height, cam.width
     rgb = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
@@ -162,6 +164,18 @@ def test_deterministic_and_graph_replay(ctx):
     for k in ("rgb", "T", "last", "keys", "vals", "starts"):
         assert np.array_equal(a[k], b[k]), k
         assert np.array_equal(a[k], c[k]), k
+
+
+@pytest.mark.parametrize("variant", range(6))
+def test_blend_variants_bit_identical(ctx, variant):
+    """Every launch shape evaluates each pixel's list identically: outputs equal bit for bit,
+    and match the oracle."""
+    scene, cam = synth.random_small_scene(5000, 23, 200, 150, log_scale_mu=-2.6, log_scale_sigma=1.0)
+    base = run_gpu(ctx, scene, cam, variant=2)
+    res = run_gpu(ctx, scene, cam, variant=variant)
+    for k in ("rgb", "T", "last"):
+        assert np.array_equal(base[k], res[k]), k
+    check(res, oracle.Frame(scene, cam, mode=64))
 
 
 def test_graph_replay_many_cameras(ctx):
