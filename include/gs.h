@@ -225,6 +225,25 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys_dev, uint32_t *vals_dev,
                         uint32_t *vals_tmp_dev, int64_t n, int32_t end_bit, int32_t *in_tmp,
                         gs_stream stream);
 
+/* gs_sort_pairs without any allocation.  The paper has no counterpart: this entry point exists
+   for callers that must not allocate device memory -- code handed its buffers by a host
+   application that owns the device-memory budget (an embedded renderer, a plugin, a real-time
+   loop), where cudaMalloc/cudaFree could synchronise the device or fail because the host
+   application has reserved all memory for its own pool.
+   Same sort and arguments as gs_sort_pairs (the caller passes the key/value buffers and the
+   ping-pong buffers), but the histograms, digit offsets, look-back descriptors and tickets live
+   in one fixed array inside the library's device image (about 2 MiB, held by every GPU that loads
+   the library until the process exits).  n may be at most 2,097,152 pairs; larger n returns
+   GS_ERR_CAPACITY with a message in gs_last_error().  The first call on a device looks up the
+   array's device address with that device current; make that first call before any stream
+   capture.  Every call on a device shares the array and it keeps the last call's contents (the
+   call clears what must start at zero), so calls whose work overlaps on the GPU -- e.g. on two
+   streams without an ordering between them -- race and must not be issued.  Calls no cudaMalloc,
+   cudaFree or allocating library routine. */
+gs_status gs_sort_pairs_noalloc(uint64_t *keys_dev, uint32_t *vals_dev, uint64_t *keys_tmp_dev,
+                                uint32_t *vals_tmp_dev, int64_t n, int32_t end_bit, int32_t *in_tmp,
+                                gs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,7 @@ PROTOTYPES = {
     "gs_frame_pairs": (_st, [_vp, C.c_int32, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
     "gs_frame_ranges": (_st, [_vp, _vp, C.c_int64, _vp]),
     "gs_sort_pairs": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _vp]),
+    "gs_sort_pairs_noalloc": (_st, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _vp]),
 }
 
 

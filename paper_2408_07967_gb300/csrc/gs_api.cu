@@ -17,6 +17,14 @@ namespace {
 
 thread_local std::string g_err;
 
+}  // namespace
+
+namespace gs {
+void set_error_message(const char *msg) { g_err = msg ? msg : ""; }
+}  // namespace gs
+
+namespace {
+
 gs_status fail(gs_status code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 gs_status fail(gs_status code, const char *fmt, ...) {
     char buf[512];
