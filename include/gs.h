@@ -94,7 +94,8 @@ typedef struct {
     int32_t tiles_x, tiles_y;
     int32_t sort_passes;    /* 8-bit digit passes of the last sort */
     int64_t culled_in;      /* Gaussians passing the near-plane and opacity cull */
-    int64_t evaluations;    /* (pixel, list entry) evaluations of the last gs_blend */
+    int64_t evaluations;    /* counting mode: (pixel, list entry) pairs walked by the last gs_blend */
+    int64_t contributions;  /* counting mode: of those, entries with q <= t (alpha >= tau) */
     int32_t kernels;        /* kernels one gs_render launches */
     int32_t pad;
 } gs_frame_stats;
@@ -181,6 +182,22 @@ typedef struct {
 } gs_tuning;
 gs_status gs_frame_set_tuning(gs_frame *frame, const gs_tuning *tuning);
 gs_status gs_frame_get_tuning(const gs_frame *frame, gs_tuning *tuning);
+
+/* Autotuner: picks the frame's launch shape (gs_tuning) for rendering `scene` at the size of
+   cams[0].  With cache_path non-NULL, a line "gs-autotune-v1 <device> <P> <W> <H> <variant>"
+   matching this device, scene size and image size is reused when present; otherwise every
+   blend_variant is timed over the ncams cameras (one warm-up render, then CUDA-event stage
+   times of the blend, summed) and the fastest is kept and appended to the cache file.  The frame
+   is left with the chosen tuning, which is also written to *out (nullable).  Synchronises
+   `stream`; renders into frame-owned buffers.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA; an
+   unreadable or unwritable cache file is ignored. */
+gs_status gs_autotune(gs_frame *frame, const gs_scene *scene, const gs_camera *cams, int32_t ncams,
+                      const gs_render_opts *opts, const char *cache_path, gs_tuning *out, gs_stream stream);
+
+/* Enables (1) or disables (0) the instrumented blend that counts, per frame, the (pixel, entry)
+   pairs walked before early stop and those passing q <= t (gs_frame_stats.evaluations /
+   .contributions).  Same outputs; slower; meant for measurement, not for timed runs. */
+gs_status gs_frame_set_counting(gs_frame *frame, int32_t enable);
 
 /* Enables (1) or disables (0) CUDA events around the four stages of gs_render (recorded inside
    the graph when graphs are enabled). */

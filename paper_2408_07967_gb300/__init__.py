@@ -198,6 +198,18 @@ class Frame:
         _check(lib().gs_frame_get_tuning(self.h, C.byref(t)))
         return {"blend_variant": t.blend_variant}
 
+    def gs_autotune(self, scene: Scene, cams, opts=None, cache_path=None, stream=None) -> dict:
+        """Pick the fastest launch shape for this scene and image size (cached per device, P, W, H)."""
+        arr = (_native.gs_camera * len(cams))(*[gs_camera_from(c) for c in cams])
+        o = opts or gs_opts()
+        t = _native.gs_tuning()
+        path = None if cache_path is None else str(cache_path).encode()
+        _check(lib().gs_autotune(self.h, scene.h, arr, len(cams), C.byref(o), path, C.byref(t), _stream(stream)))
+        return {"blend_variant": t.blend_variant}
+
+    def gs_frame_set_counting(self, enable: bool):
+        _check(lib().gs_frame_set_counting(self.h, int(bool(enable))))
+
     def gs_frame_enable_timing(self, enable: bool):
         _check(lib().gs_frame_enable_timing(self.h, int(bool(enable))))
 

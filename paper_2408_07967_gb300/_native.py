@@ -31,7 +31,7 @@ class gs_frame_stats(C.Structure):
     _fields_ = [("pairs", C.c_int64), ("visible", C.c_int64), ("pair_capacity", C.c_int64), ("status", C.c_int32),
                 ("width", C.c_int32), ("height", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
                 ("sort_passes", C.c_int32), ("culled_in", C.c_int64), ("evaluations", C.c_int64),
-                ("kernels", C.c_int32), ("pad", C.c_int32)]
+                ("contributions", C.c_int64), ("kernels", C.c_int32), ("pad", C.c_int32)]
 
 
 class gs_tuning(C.Structure):
@@ -65,6 +65,9 @@ PROTOTYPES = {
     "gs_frame_enable_timing": (_st, [_vp, C.c_int32]),
     "gs_frame_set_tuning": (_st, [_vp, C.POINTER(gs_tuning)]),
     "gs_frame_get_tuning": (_st, [_vp, C.POINTER(gs_tuning)]),
+    "gs_frame_set_counting": (_st, [_vp, C.c_int32]),
+    "gs_autotune": (_st, [_vp, _vp, _vp, C.c_int32, C.POINTER(gs_render_opts), C.c_char_p, C.POINTER(gs_tuning),
+                          _vp]),
     "gs_frame_stage_ms": (_st, [_vp, C.POINTER(C.c_float)]),
     "gs_render_host": (_st, [_vp, _vp, C.POINTER(gs_camera), C.POINTER(gs_render_opts), _vp, _vp, _vp, _vp]),
     "gs_frame_get_stats": (_st, [_vp, C.POINTER(gs_frame_stats), _vp]),

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gs_internal.cuh"
 
@@ -110,7 +111,10 @@ struct gs_frame {
     unsigned long long *keys[2] = {nullptr, nullptr};
     unsigned *vals[2] = {nullptr, nullptr};
     unsigned *starts = nullptr;
-    unsigned long long *scan_desc = nullptr;
+    unsigned long long *chunk_base = nullptr;
+    unsigned *chunk_hits = nullptr;
+    float4 *geo0 = nullptr, *geo1 = nullptr;
+    int4 *geo2 = nullptr;
     SortScratch sort{};
     FrameCounters *ctr = nullptr;
     // state of the last call
@@ -125,6 +129,7 @@ struct gs_frame {
     // frame-owned outputs for gs_render_host (allocated on first use)
     void *out_mem = nullptr;
     gs_tuning tuning{2, {0, 0, 0, 0, 0, 0, 0}};
+    int counting = 0;
 };
 
 extern "C" {
@@ -275,7 +280,9 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     size_t o_k0 = cv.take<unsigned long long>(max_pairs), o_k1 = cv.take<unsigned long long>(max_pairs);
     size_t o_v0 = cv.take<unsigned>(max_pairs), o_v1 = cv.take<unsigned>(max_pairs);
     size_t o_starts = cv.take<unsigned>(tiles + 1);
-    size_t o_scan = cv.take<unsigned long long>(f->max_chunks);
+    size_t o_cbase = cv.take<unsigned long long>(f->max_chunks);
+    size_t o_chits = cv.take<unsigned>(f->max_chunks);
+    size_t o_geo0 = cv.take<float4>(max_g), o_geo1 = cv.take<float4>(max_g), o_geo2 = cv.take<int4>(max_g);
     size_t o_hist = cv.take<unsigned>(8 * 256), o_offs = cv.take<unsigned>(8 * 256);
     size_t o_desc = cv.take<unsigned long long>(f->sort.max_tiles * 256);
     size_t o_ctr = cv.take<FrameCounters>(1);
@@ -293,7 +300,11 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     f->vals[0] = (unsigned *)(b + o_v0);
     f->vals[1] = (unsigned *)(b + o_v1);
     f->starts = (unsigned *)(b + o_starts);
-    f->scan_desc = (unsigned long long *)(b + o_scan);
+    f->chunk_base = (unsigned long long *)(b + o_cbase);
+    f->chunk_hits = (unsigned *)(b + o_chits);
+    f->geo0 = (float4 *)(b + o_geo0);
+    f->geo1 = (float4 *)(b + o_geo1);
+    f->geo2 = (int4 *)(b + o_geo2);
     f->sort.hist = (unsigned *)(b + o_hist);
     f->sort.offs = (unsigned *)(b + o_offs);
     f->sort.desc = (unsigned long long *)(b + o_desc);
@@ -340,6 +351,16 @@ gs_status gs_frame_set_tuning(gs_frame *f, const gs_tuning *t) {
         f->exec = nullptr;
     }
     f->tuning = *t;
+    return GS_OK;
+}
+
+gs_status gs_frame_set_counting(gs_frame *f, int32_t enable) {
+    if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
+    if (f->counting != (enable ? 1 : 0) && f->exec) {
+        cudaGraphExecDestroy(f->exec);
+        f->exec = nullptr;
+    }
+    f->counting = enable ? 1 : 0;
     return GS_OK;
 }
 
@@ -413,12 +434,15 @@ gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, co
     a.recs = f->recs;
     a.keys = f->keys[0];
     a.vals = f->vals[0];
-    a.scan_desc = f->scan_desc;
+    a.geo0 = f->geo0;
+    a.geo1 = f->geo1;
+    a.geo2 = f->geo2;
+    a.chunk_hits = f->chunk_hits;
+    a.chunk_base = f->chunk_base;
     a.ctr = f->ctr;
     a.pair_cap = f->max_pairs;
     a.n_chunks = (int)((s->P + preprocess_chunk() - 1) / preprocess_chunk());
     GS_CUDA(cudaMemsetAsync(f->ctr, 0, offsetof(FrameCounters, sort_epoch), st));
-    GS_CUDA(cudaMemsetAsync(f->scan_desc, 0, sizeof(unsigned long long) * (size_t)a.n_chunks, st));
     launch_preprocess(a, st);
     GS_CUDA(cudaGetLastError());
     f->W = c.W;
@@ -467,9 +491,10 @@ gs_status gs_blend(gs_frame *f, const gs_render_opts *opts, float *rgb, float *T
     a.rgb = rgb;
     a.T = T;
     a.last = last;
-    a.evals = &f->ctr->evals;
+    a.evals = f->ctr->evals;
     a.variant = f->tuning.blend_variant;
-    GS_CUDA(cudaMemsetAsync(&f->ctr->evals, 0, sizeof(unsigned long long), (cudaStream_t)stream));
+    a.count = f->counting;
+    if (f->counting) GS_CUDA(cudaMemsetAsync(f->ctr->evals, 0, sizeof(f->ctr->evals), (cudaStream_t)stream));
     launch_blend(a, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
@@ -561,8 +586,9 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     out->tiles_y = f->tiles_y;
     out->sort_passes = f->passes;
     out->culled_in = c.n_culled_in;
-    out->evaluations = (int64_t)c.evals;
-    out->kernels = 5 + f->passes;
+    out->evaluations = (int64_t)c.evals[0];
+    out->contributions = (int64_t)c.evals[1];
+    out->kernels = 7 + f->passes;
     return GS_OK;
 }
 
@@ -649,3 +675,88 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *vals, uint64_
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------ autotune
+static gs_status frame_outputs(gs_frame *f, float **rgb, float **T, uint32_t **last) {
+    const size_t npx = (size_t)f->max_w * (size_t)f->max_h;
+    if (!f->out_mem) {
+        GS_CUDA(cudaSetDevice(f->ctx->device));
+        GS_CUDA(cudaMalloc(&f->out_mem, npx * 5 * sizeof(float)));
+    }
+    *rgb = (float *)f->out_mem;
+    *T = *rgb + 3 * npx;
+    *last = (uint32_t *)(*T + npx);
+    return GS_OK;
+}
+
+extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera *cams, int32_t ncams,
+                                 const gs_render_opts *opts, const char *cache_path, gs_tuning *out,
+                                 gs_stream stream) {
+    if (!f || !s || !cams || ncams <= 0) return fail(GS_ERR_INVALID_ARG, "NULL frame/scene/cameras or ncams <= 0");
+    cudaDeviceProp prop;
+    GS_CUDA(cudaGetDeviceProperties(&prop, f->ctx->device));
+    std::string dev = prop.name;
+    for (char &ch : dev)
+        if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+    char key[256];
+    snprintf(key, sizeof(key), "gs-autotune-v1 %s %lld %d %d", dev.c_str(), s->P, cams[0].width, cams[0].height);
+    if (cache_path) {
+        FILE *fp = fopen(cache_path, "r");
+        if (fp) {
+            char line[512];
+            int found = -1;
+            const size_t kl = strlen(key);
+            while (fgets(line, sizeof(line), fp))
+                if (strncmp(line, key, kl) == 0 && line[kl] == ' ') found = atoi(line + kl + 1);
+            fclose(fp);
+            if (found >= 0 && found < blend_variant_count()) {
+                gs_tuning t = f->tuning;
+                t.blend_variant = found;
+                gs_status st = gs_frame_set_tuning(f, &t);
+                if (st) return st;
+                if (out) *out = f->tuning;
+                return GS_OK;
+            }
+        }
+    }
+    float *rgb, *T;
+    uint32_t *last;
+    gs_status st = frame_outputs(f, &rgb, &T, &last);
+    if (st) return st;
+    const int timing_before = f->timing;
+    if ((st = gs_frame_enable_timing(f, 1))) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    int best = f->tuning.blend_variant;
+    float best_ms = 1e30f;
+    for (int v = 0; v < blend_variant_count(); ++v) {
+        gs_tuning t = f->tuning;
+        t.blend_variant = v;
+        if ((st = gs_frame_set_tuning(f, &t))) return st;
+        if ((st = gs_render(f, s, &cams[0], opts, rgb, T, last, stream))) return st;
+        float total = 0.0f;
+        for (int c = 0; c < ncams; ++c) {
+            if ((st = gs_render(f, s, &cams[c], opts, rgb, T, last, stream))) return st;
+            float ms[4];
+            if ((st = gs_frame_stage_ms(f, ms))) return st;
+            total += ms[3];
+        }
+        if (total < best_ms) {
+            best_ms = total;
+            best = v;
+        }
+    }
+    GS_CUDA(cudaStreamSynchronize(cs));
+    gs_tuning t = f->tuning;
+    t.blend_variant = best;
+    if ((st = gs_frame_set_tuning(f, &t))) return st;
+    if ((st = gs_frame_enable_timing(f, timing_before))) return st;
+    if (cache_path) {
+        FILE *fp = fopen(cache_path, "a");
+        if (fp) {
+            fprintf(fp, "%s %d\n", key, best);
+            fclose(fp);
+        }
+    }
+    if (out) *out = f->tuning;
+    return GS_OK;
+}

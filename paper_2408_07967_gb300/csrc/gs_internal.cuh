@@ -54,7 +54,7 @@ struct SceneView {
 // Render record of a paired Gaussian (48 bytes, three float4):
 //   r0 = (u, v, a, b2)   centre and conic, b2 = 2 b
 //   r1 = (c, t, G, red)  t = pixel threshold on q; G = log2(alpha0) = log2(tau) + t_full log2(e)/2
-//   r2 = (green, blue, z, alpha0)
+//   r2 = (green, blue, hx + 1, hy + 1)  half extents of the {q <= t} box plus one pixel
 struct Rec {
     float4 r0, r1, r2;
 };
@@ -63,7 +63,7 @@ struct Rec {
 // frame; sort_epoch only grows (it tags the sort's look-back descriptors).
 struct FrameCounters {
     unsigned long long n_pairs;      // pairs found by preprocess (may exceed capacity)
-    unsigned long long evals;        // (pixel, entry) evaluations of the last blend
+    unsigned long long evals[2];     // counted blend: entries walked, entries passing q <= t
     unsigned int n_visible;          // Gaussians with >= 1 pair
     unsigned int n_culled_in;        // Gaussians passing the near-plane / opacity cull
     unsigned int status;             // kSt* bits
@@ -205,7 +205,10 @@ struct PreprocessArgs {
     Rec *recs;
     unsigned long long *keys;
     unsigned *vals;
-    unsigned long long *scan_desc;   // one per chunk of the chained scan
+    float4 *geo0, *geo1;             // per Gaussian: (u, v, a, b), (c, t, z bits, -)
+    int4 *geo2;                      // per Gaussian: (tx0, ty0, w, h) of the candidate box, 0 if unpaired
+    unsigned *chunk_hits;            // pairs per 256-Gaussian chunk
+    unsigned long long *chunk_base;  // exclusive scan of chunk_hits
     FrameCounters *ctr;
     long long pair_cap;
     int n_chunks;
@@ -244,8 +247,9 @@ struct BlendArgs {
     float *rgb;
     float *T;
     unsigned *last;
-    unsigned long long *evals;
+    unsigned long long *evals;       // [2]: entries walked, entries passing q <= t (count mode)
     int variant;                     // launch shape, see launch_blend
+    int count;                       // 1: instrumented variant filling evals
 };
 void launch_blend(const BlendArgs &a, cudaStream_t s);
 int blend_variant_count();

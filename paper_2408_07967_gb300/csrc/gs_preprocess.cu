@@ -1,30 +1,27 @@
-// gs_preprocess.cu -- scene packing and the fused preprocess / exact-intersection / key-emission
-// kernel (Algorithm 4 of FlashGS, with the exact tile test of Algorithm 3 and Eq. 9, the
-// opacity-aware threshold of Eq. 2-3 and the tight bounding box of Section 4.1).
+// gs_preprocess.cu -- scene packing and the preprocess / exact-intersection / key-emission stage
+// (Algorithm 4 of FlashGS, with the exact tile test of Algorithm 3 and Eq. 9, the opacity-aware
+// threshold of Eq. 2-3 and the tight bounding box of Section 4.1).
 //
-// One CTA handles a chunk of 256 consecutive Gaussians:
-//   1. each thread culls and projects its Gaussian and finds its candidate tiles (tight box);
-//   2. exact tile tests, load-balanced over the whole CTA: a block scan of the candidate counts
-//      numbers every (Gaussian, candidate tile) slot, and each step the 256 threads test 256
-//      consecutive slots, whatever Gaussians they belong to.  This generalises the paper's
-//      size-aware remapping of a large ellipse onto a warp (Section 5.1.2) to any mix of sizes,
-//      so one Gaussian covering thousands of tiles no longer serialises a warp;
-//   3. the CTA's hit count goes through a decoupled look-back across chunks (chunk order fixed
-//      by an atomic ticket, waits bounded) to give the CTA its output offset;
-//   4. the tests are repeated and every hit is written at offset + its rank in slot order,
-//      i.e. pairs land in (Gaussian id, tile row-major) order -- deterministic, unlike the
-//      paper's atomicAdd slots;
-//   5. the SH colour is evaluated and the render record stored only for Gaussians with at
-//      least one pair (Algorithm 4, last step).
+// Three kernels over chunks of 256 consecutive Gaussians:
+//   k_pre_count  each thread culls and projects its Gaussian and finds its candidate tiles (tight
+//                box); then the exact tile tests run load-balanced over the whole CTA: a block
+//                scan of the candidate counts numbers every (Gaussian, candidate tile) slot, and
+//                each step the 256 threads test 256 consecutive slots, whatever Gaussians they
+//                belong to.  This generalises the paper's size-aware remapping of a large ellipse
+//                onto a warp (Section 5.1.2) to any mix of sizes.  It writes the chunk's hit
+//                count, the geometry of paired Gaussians, and their render records with the SH
+//                colour (Algorithm 4, last step: colour only for Gaussians that are used);
+//   k_pre_scan   exclusive scan of the chunk hit counts (one CTA);
+//   k_pre_emit   repeats the tests and writes every hit at its chunk's base + its rank in slot
+//                order, so pairs land in (Gaussian id, tile row-major) order -- deterministic,
+//                unlike the paper's atomicAdd slots, and without any inter-CTA waiting, so a
+//                chunk holding a huge Gaussian delays nobody else.
 #include "gs_internal.cuh"
 
 namespace gs {
 
 constexpr int kPreBlock = 256;
 constexpr int kPackBlock = 128;
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagPrefix = 2ull << 62;
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
 
 int preprocess_chunk() { return kPreBlock; }
 
@@ -115,7 +112,7 @@ __device__ __forceinline__ void sh_colour(const SceneView &S, long long gid, con
 
 // ------------------------------------------------------------------------------------------ geometry
 struct Geom {
-    float u, v, a, b, c, t, t_full, z, alpha0;
+    float u, v, a, b, c, t, t_full, z, alpha0, hx, hy;
     int tx0, tx1, ty0, ty1;
 };
 
@@ -250,6 +247,8 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
     G.ty1 = fy1 > mxy ? cam.tiles_y - 1 : (int)fy1;
     G.u = u;
     G.v = v;
+    G.hx = hx;
+    G.hy = hy;
     G.t = t;
     G.t_full = t_full;
     G.z = p[2];
@@ -264,55 +263,7 @@ __device__ __forceinline__ bool test_tile(const Cam &cam, float u, float v, floa
     return tile_hits(u, v, a, b, c, t, x0, x1, y0, y1);
 }
 
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
-    return *(const volatile unsigned long long *)p;
-}
-
-__device__ __forceinline__ void st_volatile_u64(unsigned long long *p, unsigned long long v) {
-    *(volatile unsigned long long *)p = v;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Decoupled look-back over chunk descriptors (warp 0 of the CTA); returns the exclusive prefix.
-__device__ unsigned long long chunk_lookback(unsigned long long *desc, long long chunk, FrameCounters *ctr) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long excl = 0;
-    long long j = chunk - 1;
-    unsigned spins = 0;
-    bool timed_out = false;
-    while (true) {
-        const long long idx = j - lane;
-        unsigned long long d = idx >= 0 ? ld_volatile_u64(desc + idx) : kFlagPrefix;
-        while (__any_sync(0xffffffffu, (d >> 62) == 0)) {
-            if ((d >> 62) == 0) d = ld_volatile_u64(desc + idx);
-            if (++spins > kSpinLimit) {
-                timed_out = true;
-                break;
-            }
-            __nanosleep(32);
-        }
-        if (timed_out) {
-            if (lane == 0) atomicOr(&ctr->status, kStTimeout);
-            return excl;
-        }
-        const unsigned pm = __ballot_sync(0xffffffffu, (d >> 62) == 2);
-        unsigned long long val = d & kValMask;
-        if (pm) {
-            const int first = __ffs(pm) - 1;
-            excl += warp_sum_u64(lane <= first ? val : 0ull);
-            return excl;
-        }
-        excl += warp_sum_u64(val);
-        j -= 32;
-    }
-}
-
-// ------------------------------------------------------------------------------------------ kernel
+// ------------------------------------------------------------------------------------------ kernels
 struct PreSmem {
     float u[kPreBlock], v[kPreBlock], a[kPreBlock], b[kPreBlock], c[kPreBlock], t[kPreBlock];
     unsigned zb[kPreBlock];
@@ -320,8 +271,6 @@ struct PreSmem {
     int cstart[kPreBlock + 1];        // exclusive scan of candidate-tile counts
     unsigned char any[kPreBlock];     // Gaussian has at least one pair
     unsigned wsum[kPreBlock / 32];
-    unsigned long long base;
-    unsigned chunk;
 };
 
 // Candidate slot -> (Gaussian g of the CTA, tile); slot s belongs to the last g with
@@ -346,24 +295,49 @@ __device__ __forceinline__ bool slot_test(const PreSmem &S, const Cam &cam, int 
     return test_tile(cam, S.u[g], S.v[g], S.a[g], S.b[g], S.c[g], S.t[g], tx, ty);
 }
 
-__global__ void __launch_bounds__(kPreBlock, 3) k_preprocess(const __grid_constant__ PreprocessArgs A) {
-    __shared__ PreSmem S;
+// Block exclusive scan of one int per thread into S.cstart; returns the block total.
+__device__ __forceinline__ int block_scan_cand(PreSmem &S, int ncand) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned FULL = 0xffffffffu;
-    if (tid == 0) S.chunk = atomicAdd(&A.ctr->chunk_ticket, 1u);
+    int incl = ncand;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) S.wsum[warp] = (unsigned)incl;
     __syncthreads();
-    const long long chunk = S.chunk;
+    int wex = 0, total = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
+        const int x = (int)S.wsum[w2];
+        wex += w2 < warp ? x : 0;
+        total += x;
+    }
+    S.cstart[tid] = wex + incl - ncand;
+    if (tid == 0) S.cstart[kPreBlock] = total;
+    __syncthreads();
+    return total;
+}
+
+// Pass 1: geometry, exact tests counted over all candidate tiles of the chunk (load-balanced),
+// render records of paired Gaussians, the chunk's pair count, and each paired Gaussian's
+// geometry for pass 3.
+__global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constant__ PreprocessArgs A) {
+    __shared__ PreSmem S;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned FULL = 0xffffffffu;
+    const long long chunk = blockIdx.x;
     const long long gid = chunk * kPreBlock + tid;
     const Cam &cam = A.cam;
 
-    // ---- per-Gaussian geometry (one Gaussian per thread)
     Geom G;
     bool valid = false, passed_cull = false;
     if (gid < A.scene.P) valid = gaussian_geometry(A.scene, gid, cam, A.opt, G, passed_cull);
     const unsigned n_in = __popc(__ballot_sync(FULL, passed_cull));
     if (lane == 0 && n_in) atomicAdd(&A.ctr->n_culled_in, n_in);
     const int w = valid ? G.tx1 - G.tx0 + 1 : 0;
-    const int ncand = valid ? w * (G.ty1 - G.ty0 + 1) : 0;
+    const int h = valid ? G.ty1 - G.ty0 + 1 : 0;
+    const int ncand = w * h;
     if (valid) {
         S.u[tid] = G.u;
         S.v[tid] = G.v;
@@ -371,34 +345,13 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_preprocess(const __grid_consta
         S.b[tid] = G.b;
         S.c[tid] = G.c;
         S.t[tid] = G.t;
-        S.zb[tid] = __float_as_uint(G.z);
         S.tx0[tid] = G.tx0;
         S.ty0[tid] = G.ty0;
     }
     S.w[tid] = w > 0 ? w : 1;
     S.any[tid] = 0;
+    const int ctotal = block_scan_cand(S, ncand);
 
-    // ---- block exclusive scan of candidate counts
-    int incl = ncand;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) S.wsum[warp] = (unsigned)incl;
-    __syncthreads();
-    int wex = 0, ctotal = 0;
-#pragma unroll
-    for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
-        const int x = (int)S.wsum[w2];
-        wex += w2 < warp ? x : 0;
-        ctotal += x;
-    }
-    S.cstart[tid] = wex + incl - ncand;
-    if (tid == 0) S.cstart[kPreBlock] = ctotal;
-    __syncthreads();
-
-    // ---- exact tests, load-balanced over all candidate tiles of the CTA: count hits
     unsigned hits = 0;
     for (int base = 0; base < ctotal; base += kPreBlock) {
         const int slot = base + tid;
@@ -410,32 +363,108 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_preprocess(const __grid_consta
         }
         hits += (unsigned)__syncthreads_count(hit);
     }
+    if (tid == 0) A.chunk_hits[chunk] = hits;
 
-    // ---- chained scan across CTAs (decoupled look-back, warp 0)
-    if (warp == 0) {
-        const unsigned long long block_total = hits;
-        if (lane == 0) {
-            __threadfence();
-            st_volatile_u64(A.scan_desc + chunk, (chunk == 0 ? kFlagPrefix : kFlagAgg) | block_total);
-        }
-        unsigned long long excl = 0;
-        if (chunk > 0) excl = chunk_lookback(A.scan_desc, chunk, A.ctr);
-        if (lane == 0) {
-            if (chunk > 0) st_volatile_u64(A.scan_desc + chunk, kFlagPrefix | (excl + block_total));
-            S.base = excl;
-            if (chunk == A.n_chunks - 1) {
-                const unsigned long long n = excl + block_total;
-                A.ctr->n_pairs = n;
-                if ((long long)n > A.pair_cap) atomicOr(&A.ctr->status, kStPairOverflow);
-            }
-        }
+    const bool vis = S.any[tid] != 0;
+    const unsigned nvis = __popc(__ballot_sync(FULL, vis));
+    if (lane == 0 && nvis) atomicAdd(&A.ctr->n_visible, nvis);
+    if (gid < A.scene.P) A.geo2[gid] = vis ? make_int4(G.tx0, G.ty0, w, h) : make_int4(0, 0, 0, 0);
+    if (vis) {
+        A.geo0[gid] = make_float4(G.u, G.v, G.a, G.b);
+        A.geo1[gid] = make_float4(G.c, G.t, __uint_as_float(__float_as_uint(G.z)), 0.0f);
+        const float4 po = __ldg(A.scene.pos_opa + gid);
+        float rgb[3];
+        sh_colour(A.scene, gid, cam, po.x, po.y, po.z, rgb);
+        const float LOG2E = 1.4426950408889634f;
+        const float Gl = log_rn(G.alpha0) * LOG2E;
+        Rec rc;
+        rc.r0 = make_float4(G.u, G.v, G.a, G.b + G.b);
+        rc.r1 = make_float4(G.c, G.t, Gl, rgb[0]);
+        rc.r2 = make_float4(rgb[1], rgb[2], G.hx + 1.0f, G.hy + 1.0f);
+        A.recs[gid] = rc;
     }
-    __syncthreads();
+}
 
-    // ---- emission: the CTA's pairs are [base, base + hits) in slot order
+// Pass 2: exclusive scan of the chunk pair counts (one CTA; each thread sums a run of chunks).
+constexpr int kScanThreads = 1024;
+constexpr int kScanRun = 16;
+__global__ void __launch_bounds__(kScanThreads) k_pre_scan(const __grid_constant__ PreprocessArgs A) {
+    __shared__ unsigned long long s_w[kScanThreads / 32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    const long long n = A.n_chunks;
+    for (long long base = 0; base < n; base += (long long)kScanThreads * kScanRun) {
+        const long long my0 = base + (long long)tid * kScanRun;
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int r = 0; r < kScanRun; ++r)
+            if (my0 + r < n) sum += A.chunk_hits[my0 + r];
+        unsigned long long incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        unsigned long long wex = 0, tot = 0;
+        for (int w2 = 0; w2 < kScanThreads / 32; ++w2) {
+            const unsigned long long x = s_w[w2];
+            wex += w2 < warp ? x : 0ull;
+            tot += x;
+        }
+        unsigned long long run = s_carry + wex + incl - sum;
+#pragma unroll
+        for (int r = 0; r < kScanRun; ++r)
+            if (my0 + r < n) {
+                A.chunk_base[my0 + r] = run;
+                run += A.chunk_hits[my0 + r];
+            }
+        __syncthreads();
+        if (tid == 0) s_carry += tot;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        A.ctr->n_pairs = s_carry;
+        if ((long long)s_carry > A.pair_cap) atomicOr(&A.ctr->status, kStPairOverflow);
+    }
+}
+
+// Pass 3: the same load-balanced tests; every hit is written at the chunk's base + its rank in
+// slot order, i.e. pairs land in (Gaussian id, tile row-major) order.
+__global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
+    __shared__ PreSmem S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned FULL = 0xffffffffu;
+    const long long chunk = blockIdx.x;
+    const long long gid = chunk * kPreBlock + tid;
+    const Cam &cam = A.cam;
+    int ncand = 0;
+    if (gid < A.scene.P) {
+        const int4 g2 = A.geo2[gid];
+        ncand = g2.z * g2.w;
+        if (ncand > 0) {
+            const float4 g0 = A.geo0[gid], g1 = A.geo1[gid];
+            S.u[tid] = g0.x;
+            S.v[tid] = g0.y;
+            S.a[tid] = g0.z;
+            S.b[tid] = g0.w;
+            S.c[tid] = g1.x;
+            S.t[tid] = g1.y;
+            S.zb[tid] = __float_as_uint(g1.z);
+            S.tx0[tid] = g2.x;
+            S.ty0[tid] = g2.y;
+        }
+        S.w[tid] = g2.z > 0 ? g2.z : 1;
+    } else {
+        S.w[tid] = 1;
+    }
+    const int ctotal = block_scan_cand(S, ncand);
     const long long cap = A.pair_cap;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long run = S.base;
+    unsigned long long run = A.chunk_base[chunk];
     for (int base = 0; base < ctotal; base += kPreBlock) {
         const int slot = base + tid;
         bool hit = false;
@@ -461,28 +490,13 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_preprocess(const __grid_consta
         run += tot;
         __syncthreads();
     }
-
-    // ---- render record of paired Gaussians
-    const bool vis = S.any[tid] != 0;
-    const unsigned nvis = __popc(__ballot_sync(FULL, vis));
-    if (lane == 0 && nvis) atomicAdd(&A.ctr->n_visible, nvis);
-    if (vis) {
-        const float4 po = __ldg(A.scene.pos_opa + gid);
-        float rgb[3];
-        sh_colour(A.scene, gid, cam, po.x, po.y, po.z, rgb);
-        const float LOG2E = 1.4426950408889634f;
-        const float Gl = log_rn(G.alpha0) * LOG2E;
-        Rec rc;
-        rc.r0 = make_float4(G.u, G.v, G.a, G.b + G.b);
-        rc.r1 = make_float4(G.c, G.t, Gl, rgb[0]);
-        rc.r2 = make_float4(rgb[1], rgb[2], G.z, G.alpha0);
-        A.recs[gid] = rc;
-    }
 }
 
 void launch_preprocess(const PreprocessArgs &a, cudaStream_t s) {
     if (a.n_chunks <= 0) return;
-    k_preprocess<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    k_pre_count<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    k_pre_scan<<<1, kScanThreads, 0, s>>>(a);
+    k_pre_emit<<<a.n_chunks, kPreBlock, 0, s>>>(a);
 }
 
 }  // namespace gs

@@ -6,9 +6,12 @@
 //   * two-level prefetch (Section 5.2.1): while batch b is blended, the records of batch b+1
 //     are in flight to shared memory (cp.async, double buffer) and the Gaussian ids of batch
 //     b+2 are in flight to registers;
-//   * divergence control (Section 5.2.2): a warp-uniform vote skips a Gaussian that reaches
-//     alpha >= tau at none of the warp's pixels, and one CTA-wide count stops the tile when
-//     every pixel has saturated;
+//   * divergence control (Section 5.2.2): each warp filters every staged batch against its own
+//     pixel region with the exact ellipse/rectangle test of Algorithm 3 (one Gaussian per lane,
+//     one ballot per 32 entries) and walks only the entries that can reach its pixels -- the
+//     paper's tile-level exact intersection applied again at warp granularity; a warp-uniform vote skips an entry
+//     that passes q <= t at none of the warp's pixels; a saturated pixel is parked at x = +inf,
+//     and one CTA-wide count stops the tile when every pixel has saturated;
 //   * the exponent is folded into one FMA in the log2 domain and evaluated by
 //     ex2.approx.ftz.f32 (Section 5.3.2).
 //
@@ -41,55 +44,77 @@ struct BlendSmem {
     float4 r2[2][BATCH];
 };
 
+// Warp region of a launch shape: RC columns x RR rows of pixels, RC * RR = 32 * PX.
+template <int PX>
+struct WarpRegion {
+    static constexpr int RC = PX == 4 ? 16 : 8;
+    static constexpr int RR = 32 * PX / RC;
+    static constexpr int LANES_PER_ROW = RC / PX;
+};
+
 // PX pixels per thread along a row; 256/PX threads per 16x16 tile; BATCH records per stage.
-template <int PX, int BATCH>
+// Each warp owns an RR x RC pixel region of the tile.  Per staged batch, lane l tests entries
+// l, l+32, ... exactly against the region's pixel-area rectangle; the warp then walks only the
+// entries that meet it, in list order, so a pixel's entries are still evaluated in order and
+// with the same arithmetic.  (A pixel sample passing q <= t lies inside the ellipse, half a
+// pixel inside the rectangle, so no contributing entry is filtered out.)  COUNT adds the
+// per-pixel evaluation and contribution counters used for the roofline (not in timed runs).
+template <int PX, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ BlendArgs A) {
     constexpr int NT = 256 / PX;            // threads per tile
     constexpr int PER = BATCH / NT;         // records each thread stages per batch
-    static_assert(BATCH % NT == 0, "batch must be a multiple of the thread count");
+    constexpr int WORDS = BATCH / 32;       // filter mask words per batch
+    using WR = WarpRegion<PX>;
+    static_assert(BATCH % NT == 0 && BATCH % 32 == 0, "batch must be a multiple of the thread count");
     __shared__ BlendSmem<PX, BATCH> S;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
     const int tx = tile % A.tiles_x, ty = tile / A.tiles_x;
-    constexpr int GROUPS = 16 / PX;         // thread groups per row
-    const int row = tid / GROUPS, grp = tid % GROUPS;
-    const int py = ty * kTile + row;
-    const int px0 = tx * kTile + grp * PX;
+    constexpr int REGIONS_PER_ROW = 16 / WR::RC;
+    const int rx0 = tx * kTile + (warp % REGIONS_PER_ROW) * WR::RC;    // region origin (pixels)
+    const int ry0 = ty * kTile + (warp / REGIONS_PER_ROW) * WR::RR;
+    const int py = ry0 + lane / WR::LANES_PER_ROW;
+    const int px0 = rx0 + (lane % WR::LANES_PER_ROW) * PX;
+    // the region's pixel-area rectangle (its pixel samples lie half a pixel inside it)
+    const float qx0 = (float)rx0, qx1 = (float)(rx0 + WR::RC), qy0 = (float)ry0, qy1 = (float)(ry0 + WR::RR);
     long long n = (long long)*A.n_dev;
     if (n > A.cap) n = A.cap;
     const long long start = min((long long)A.starts[tile], n);
     const long long end = min((long long)A.starts[tile + 1], n);
     const float fpy = (float)py + 0.5f;
+    const float INF = __int_as_float(0x7f800000);
     float fpx[PX];
-    bool done[PX];
+    bool inside[PX];
     float T[PX], C0[PX], C1[PX], C2[PX];
-    unsigned last[PX], stop[PX];
+    unsigned last[PX];
+    unsigned stop[PX], contrib[PX];
+    int alive_px = 0;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
-        fpx[k] = (float)(px0 + k) + 0.5f;
-        done[k] = !(px0 + k < A.W && py < A.H);
+        inside[k] = px0 + k < A.W && py < A.H;
+        // a finished pixel keeps x = +inf: its q is +inf or NaN and never passes q <= t
+        fpx[k] = inside[k] ? (float)(px0 + k) + 0.5f : INF;
+        alive_px += inside[k];
         T[k] = 1.0f;
         C0[k] = C1[k] = C2[k] = 0.0f;
         last[k] = 0;
         stop[k] = 0;
+        contrib[k] = 0;
     }
     const float HALF_LOG2E = 0.72134752044448170f;
     const float amax = A.opt.alpha_max, tmin = A.opt.T_min;
     const unsigned FULL = 0xffffffffu;
 
     // ---- pipeline prologue: ids of batches 0 and 1, records of batch 0
-    unsigned ids[PER], ids_next[PER];
+    unsigned ids_next[PER];
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         const long long i0 = start + r * NT + tid, i1 = start + BATCH + r * NT + tid;
-        ids[r] = i0 < end ? __ldg(A.vals + i0) : 0u;
+        const unsigned id0 = i0 < end ? __ldg(A.vals + i0) : 0u;
         ids_next[r] = i1 < end ? __ldg(A.vals + i1) : 0u;
-    }
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int e = r * NT + tid;
-        if (start + e < end) {
-            const Rec *src = A.recs + ids[r];
+        if (i0 < end) {
+            const Rec *src = A.recs + id0;
+            const int e = r * NT + tid;
             cp_async16(&S.r0[0][e], &src->r0);
             cp_async16(&S.r1[0][e], &src->r1);
             cp_async16(&S.r2[0][e], &src->r2);
@@ -121,73 +146,99 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
         __syncthreads();
         const int cnt = (int)min((long long)BATCH, end - b);
         const unsigned pos0 = (unsigned)(b - start);
-        bool alive = false;
+        if (__any_sync(FULL, alive_px > 0)) {
+            // per-warp filter of the batch against the warp's pixel region
+            unsigned mask[WORDS];
 #pragma unroll
-        for (int k = 0; k < PX; ++k) alive |= !done[k];
-        if (__any_sync(FULL, alive)) {
-            for (int j = 0; j < cnt; ++j) {
-                const float4 r0 = S.r0[buf][j];
-                const float4 r1 = S.r1[buf][j];
-                const float dy = fsub(fpy, r0.y);
-                const float By = fmul(r0.w, dy);
-                const float Cy = fmul(fmul(r1.x, dy), dy);
-                float q[PX];
-                bool pass[PX];
-                bool anyp = false;
-#pragma unroll
-                for (int k = 0; k < PX; ++k) {
-                    const float dx = fsub(fpx[k], r0.x);
-                    q[k] = ffma(ffma(r0.z, dx, By), dx, Cy);
-                    pass[k] = (q[k] <= r1.y) && !done[k];
-                    anyp |= pass[k];
+            for (int w = 0; w < WORDS; ++w) {
+                const int e = w * 32 + lane;
+                bool rel = false;
+                if (e < cnt) {
+                    // exact ellipse / rectangle test (Algorithm 3) of {q <= t} against the region
+                    const float4 a0 = S.r0[buf][e];
+                    const float4 a1 = S.r1[buf][e];
+                    rel = tile_hits(a0.x, a0.y, a0.z, 0.5f * a0.w, a1.x, a1.y, qx0, qx1, qy0, qy1);
                 }
-                if (!__any_sync(FULL, anyp)) continue;
-                const float4 r2 = S.r2[buf][j];
-                const unsigned pos = pos0 + (unsigned)j + 1u;
+                mask[w] = __ballot_sync(FULL, rel);
+            }
 #pragma unroll
-                for (int k = 0; k < PX; ++k) {
-                    if (pass[k]) {
-                        const float al = fminf(amax, ex2_approx(fmaf(q[k], -HALF_LOG2E, r1.z)));
-                        const float Tn = T[k] * (1.0f - al);
-                        if (Tn < tmin) {
-                            done[k] = true;
-                            stop[k] = pos;
-                        } else {
-                            const float w = al * T[k];
-                            C0[k] = fmaf(w, r1.w, C0[k]);
-                            C1[k] = fmaf(w, r2.x, C1[k]);
-                            C2[k] = fmaf(w, r2.y, C2[k]);
-                            T[k] = Tn;
-                            last[k] = pos;
+            for (int w = 0; w < WORDS; ++w) {
+                unsigned m = mask[w];
+                while (m) {
+                    const int j = w * 32 + __ffs(m) - 1;
+                    m &= m - 1;
+                    const float4 r0 = S.r0[buf][j];
+                    const float4 r1 = S.r1[buf][j];
+                    const float dy = fsub(fpy, r0.y);
+                    const float By = fmul(r0.w, dy);
+                    const float Cy = fmul(fmul(r1.x, dy), dy);
+                    float q[PX];
+                    bool pass[PX];
+                    bool anyp = false;
+#pragma unroll
+                    for (int k = 0; k < PX; ++k) {
+                        const float dx = fsub(fpx[k], r0.x);
+                        q[k] = ffma(ffma(r0.z, dx, By), dx, Cy);
+                        pass[k] = q[k] <= r1.y;
+                        anyp |= pass[k];
+                    }
+                    if (!__any_sync(FULL, anyp)) continue;
+                    const float4 r2 = S.r2[buf][j];
+                    const unsigned pos = pos0 + (unsigned)j + 1u;
+#pragma unroll
+                    for (int k = 0; k < PX; ++k) {
+                        if (pass[k]) {
+                            const float al = fminf(amax, ex2_approx(fmaf(q[k], -HALF_LOG2E, r1.z)));
+                            const float Tn = fmaf(-al, T[k], T[k]);
+                            if (COUNT) ++contrib[k];
+                            if (Tn < tmin) {
+                                fpx[k] = INF;
+                                --alive_px;
+                                if (COUNT) stop[k] = pos;
+                            } else {
+                                const float w = al * T[k];
+                                C0[k] = fmaf(w, r1.w, C0[k]);
+                                C1[k] = fmaf(w, r2.x, C1[k]);
+                                C2[k] = fmaf(w, r2.y, C2[k]);
+                                T[k] = Tn;
+                                last[k] = pos;
+                            }
                         }
                     }
                 }
             }
         }
-        bool alive2 = false;
-#pragma unroll
-        for (int k = 0; k < PX; ++k) alive2 |= !done[k];
-        if (__syncthreads_count(alive2) == 0) break;   // also orders buffer reuse
+        if (__syncthreads_count(alive_px > 0) == 0) break;   // also orders buffer reuse
         buf ^= 1;
     }
     cp_async_wait<0>();
 
-    // evaluation count for the roofline: entries walked per pixel, skipped ones included
-    unsigned long long walked = 0;
+    if (COUNT) {
+        // entries walked per pixel (skipped ones included) and entries that passed q <= t
+        unsigned long long walked = 0, contributed = 0;
 #pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        const bool in = px0 + k < A.W && py < A.H;
-        if (in) walked += stop[k] ? stop[k] : (unsigned long long)(end - start);
+        for (int k = 0; k < PX; ++k) {
+            if (inside[k]) {
+                walked += stop[k] ? stop[k] : (unsigned long long)(end - start);
+                contributed += contrib[k];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            walked += __shfl_xor_sync(FULL, walked, o);
+            contributed += __shfl_xor_sync(FULL, contributed, o);
+        }
+        if (lane == 0) {
+            if (walked) atomicAdd(A.evals, walked);
+            if (contributed) atomicAdd(A.evals + 1, contributed);
+        }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) walked += __shfl_xor_sync(FULL, walked, o);
-    if ((tid & 31) == 0 && walked) atomicAdd(A.evals, walked);
 
     const long long npx = (long long)A.W * A.H;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
         const int px = px0 + k;
-        if (px < A.W && py < A.H) {
+        if (inside[k]) {
             const long long o = (long long)py * A.W + px;
             A.rgb[o] = C0[k] + T[k] * A.opt.bg[0];
             A.rgb[npx + o] = C1[k] + T[k] * A.opt.bg[1];
@@ -203,17 +254,25 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
 // the outputs are bit-identical across variants.
 int blend_variant_count() { return 6; }
 
+template <bool COUNT>
+static void launch_blend_t(const BlendArgs &a, int ntiles, cudaStream_t s) {
+    switch (a.variant) {
+        case 0: k_blend<1, 256, COUNT><<<ntiles, 256, 0, s>>>(a); break;
+        case 1: k_blend<2, 128, COUNT><<<ntiles, 128, 0, s>>>(a); break;
+        case 2: k_blend<4, 128, COUNT><<<ntiles, 64, 0, s>>>(a); break;
+        case 3: k_blend<2, 256, COUNT><<<ntiles, 128, 0, s>>>(a); break;
+        case 4: k_blend<4, 64, COUNT><<<ntiles, 64, 0, s>>>(a); break;
+        default: k_blend<4, 256, COUNT><<<ntiles, 64, 0, s>>>(a); break;
+    }
+}
+
 void launch_blend(const BlendArgs &a, cudaStream_t s) {
     const int ntiles = a.tiles_x * a.tiles_y;
     if (ntiles <= 0) return;
-    switch (a.variant) {
-        case 0: k_blend<1, 256><<<ntiles, 256, 0, s>>>(a); break;
-        case 1: k_blend<2, 128><<<ntiles, 128, 0, s>>>(a); break;
-        case 2: k_blend<4, 128><<<ntiles, 64, 0, s>>>(a); break;
-        case 3: k_blend<2, 256><<<ntiles, 128, 0, s>>>(a); break;
-        case 4: k_blend<4, 64><<<ntiles, 64, 0, s>>>(a); break;
-        default: k_blend<4, 256><<<ntiles, 64, 0, s>>>(a); break;
-    }
+    if (a.count)
+        launch_blend_t<true>(a, ntiles, s);
+    else
+        launch_blend_t<false>(a, ntiles, s);
 }
 
 }  // namespace gs

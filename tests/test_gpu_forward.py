@@ -178,6 +178,40 @@ def test_blend_variants_bit_identical(ctx, variant):
     check(res, oracle.Frame(scene, cam, mode=64))
 
 
+def test_counting_blend_same_image_and_oracle_walk_count(ctx):
+    """The instrumented blend gives the same image, and its count of (pixel, entry) pairs walked
+    before early stop equals the oracle's (up to early-stop near ties)."""
+    scene, cams = synth.load_config("tiny")
+    cam = cams[0]
+    ref = oracle.Frame(scene, cam, mode=32)
+    sc = gs.Scene.from_numpy(ctx, scene)
+    fr = gs.Frame(ctx, scene.P, 1 << 20, cam.width, cam.height)
+    a, _, _ = fr.render(sc, cam)
+    fr.gs_frame_set_counting(True)
+    b, _, _ = fr.render(sc, cam)
+    st = fr.stats()
+    assert torch.equal(a, b)
+    assert abs(st["evaluations"] - ref.evals) <= 1e-4 * ref.evals
+    assert 0 < st["contributions"] <= st["evaluations"]
+
+
+def test_autotune_picks_a_shape_and_caches_it(ctx, tmp_path):
+    scene, cams = synth.load_config("tiny")
+    sc = gs.Scene.from_numpy(ctx, scene)
+    fr = gs.Frame(ctx, scene.P, 1 << 20, 256, 256)
+    ref, _, _ = fr.render(sc, cams[0])
+    cache = tmp_path / "tune.txt"
+    t1 = fr.gs_autotune(sc, cams, cache_path=cache)
+    assert 0 <= t1["blend_variant"] < 6
+    assert fr.gs_frame_get_tuning() == t1
+    line = cache.read_text().strip().split()
+    assert line[0] == "gs-autotune-v1" and int(line[-1]) == t1["blend_variant"]
+    fr2 = gs.Frame(ctx, scene.P, 1 << 20, 256, 256)
+    assert fr2.gs_autotune(sc, cams, cache_path=cache) == t1          # served from the cache
+    out, _, _ = fr2.render(sc, cams[0])
+    assert torch.equal(out, ref)
+
+
 def test_graph_replay_many_cameras(ctx):
     scene, cams = synth.load_config("tiny")
     sc = gs.Scene.from_numpy(ctx, scene)
