@@ -146,9 +146,11 @@ int64_t gs_frame_bytes(const gs_frame *frame);
 gs_status gs_preprocess(gs_frame *frame, const gs_scene *scene, const gs_camera *cam,
                         const gs_render_opts *opts, gs_stream stream);
 
-/* Stage b (Section 2.2 sort): stable LSD radix sort of the frame's pairs by key, over bits
-   [0, 32 + ceil(log2(tiles))) in 8-bit digits (one histogram pass, then one chained-scan
-   scatter pass per digit).  The pair count is read on the device. */
+/* Stage b (Section 2.2 sort): stable LSD radix sort of the frame's pairs by key in 8-bit digits
+   (one histogram pass, then one chained-scan scatter pass per digit): over bits
+   [0, 32 + ceil(log2(tiles))) of the 64-bit keys in sort_mode 0, over the tile bits of the 32-bit
+   keys in sort_mode 1 (where gs_preprocess already ordered the pairs by depth).  The pair count is
+   read on the device. */
 gs_status gs_sort(gs_frame *frame, gs_stream stream);
 
 /* Stage c: start of every tile's run in the sorted keys (binary search per tile). */
@@ -172,22 +174,29 @@ gs_status gs_render(gs_frame *frame, const gs_scene *scene, const gs_camera *cam
 /* Enables (1) or disables (0) CUDA-graph replay of gs_render on this frame. */
 gs_status gs_frame_use_graph(gs_frame *frame, int32_t enable);
 
-/* Launch-shape choices of a frame (picked by the autotuner in the Python package):
+/* Launch-shape and ordering choices of a frame (picked by gs_autotune).
    blend_variant 0..5 = (pixels per thread, records per staged batch) of (1, 256), (2, 128),
    (4, 128), (2, 256), (4, 64), (4, 256); 256 / pixels-per-thread threads per 16x16 tile.
-   Results are bit-identical across variants.  GS_ERR_INVALID_ARG for out-of-range values. */
+   sort_mode 0: pairs emitted in (Gaussian id, tile) order with 64-bit (tile << 32 | depth bits)
+   keys and sorted over 32 + ceil(log2 tiles) bits; sort_mode 1 (two-level): the paired
+   Gaussians are sorted once by depth (32-bit keys), pairs are emitted in that order with the
+   tile id alone as a 32-bit key, and a stable sort over ceil(log2 tiles) bits finishes -- the
+   same (tile, depth, id) order with far fewer bytes moved.  Results are bit-identical across
+   all choices.  GS_ERR_INVALID_ARG for out-of-range values. */
 typedef struct {
     int32_t blend_variant;
-    int32_t reserved[7];
+    int32_t sort_mode;
+    int32_t reserved[6];
 } gs_tuning;
 gs_status gs_frame_set_tuning(gs_frame *frame, const gs_tuning *tuning);
 gs_status gs_frame_get_tuning(const gs_frame *frame, gs_tuning *tuning);
 
-/* Autotuner: picks the frame's launch shape (gs_tuning) for rendering `scene` at the size of
-   cams[0].  With cache_path non-NULL, a line "gs-autotune-v1 <device> <P> <W> <H> <variant>"
-   matching this device, scene size and image size is reused when present; otherwise every
-   blend_variant is timed over the ncams cameras (one warm-up render, then CUDA-event stage
-   times of the blend, summed) and the fastest is kept and appended to the cache file.  The frame
+/* Autotuner: picks the frame's gs_tuning for rendering `scene` at the size of cams[0].  With
+   cache_path non-NULL, a line "gs-autotune-v1 <device> <P> <W> <H> <blend_variant> <sort_mode>"
+   matching this device, scene size and image size is reused when present; otherwise both sort
+   modes are timed (preprocess + sort + ranges) and then every blend_variant (blend), each over the
+   ncams cameras after one warm-up render with CUDA-event stage times, and the fastest choices are
+   kept and appended to the cache file.  The frame
    is left with the chosen tuning, which is also written to *out (nullable).  Synchronises
    `stream`; renders into frame-owned buffers.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA; an
    unreadable or unwritable cache file is ignored. */

@@ -35,7 +35,7 @@ class gs_frame_stats(C.Structure):
 
 
 class gs_tuning(C.Structure):
-    _fields_ = [("blend_variant", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("blend_variant", C.c_int32), ("sort_mode", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 _vp = C.c_void_p

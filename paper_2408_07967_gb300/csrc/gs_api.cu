@@ -111,8 +111,10 @@ struct gs_frame {
     unsigned long long *keys[2] = {nullptr, nullptr};
     unsigned *vals[2] = {nullptr, nullptr};
     unsigned *starts = nullptr;
-    unsigned long long *chunk_base = nullptr;
-    unsigned *chunk_hits = nullptr;
+    unsigned long long *chunk_base = nullptr, *vis_base = nullptr, *chunk_base2 = nullptr;
+    unsigned *chunk_hits = nullptr, *chunk_vis = nullptr, *chunk_hits2 = nullptr, *counts = nullptr;
+    unsigned *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
+    int mode_used = 0;
     float4 *geo0 = nullptr, *geo1 = nullptr;
     int4 *geo2 = nullptr;
     SortScratch sort{};
@@ -128,7 +130,7 @@ struct gs_frame {
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // frame-owned outputs for gs_render_host (allocated on first use)
     void *out_mem = nullptr;
-    gs_tuning tuning{2, {0, 0, 0, 0, 0, 0, 0}};
+    gs_tuning tuning{1, 1, {0, 0, 0, 0, 0, 0}};
     int counting = 0;
 };
 
@@ -274,7 +276,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     f->max_h = max_h;
     f->max_tiles = tiles;
     f->max_chunks = (max_g + preprocess_chunk() - 1) / preprocess_chunk();
-    f->sort.max_tiles = sort_max_tiles_for(max_pairs);
+    f->sort.max_tiles = sort_max_tiles_for(max_pairs > max_g ? max_pairs : max_g);
     Carver cv;
     size_t o_recs = cv.take<Rec>(max_g);
     size_t o_k0 = cv.take<unsigned long long>(max_pairs), o_k1 = cv.take<unsigned long long>(max_pairs);
@@ -282,6 +284,11 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     size_t o_starts = cv.take<unsigned>(tiles + 1);
     size_t o_cbase = cv.take<unsigned long long>(f->max_chunks);
     size_t o_chits = cv.take<unsigned>(f->max_chunks);
+    size_t o_vbase = cv.take<unsigned long long>(f->max_chunks), o_cbase2 = cv.take<unsigned long long>(f->max_chunks);
+    size_t o_cvis = cv.take<unsigned>(f->max_chunks), o_chits2 = cv.take<unsigned>(f->max_chunks);
+    size_t o_counts = cv.take<unsigned>(max_g);
+    size_t o_dk0 = cv.take<unsigned>(max_g), o_dk1 = cv.take<unsigned>(max_g);
+    size_t o_dv0 = cv.take<unsigned>(max_g), o_dv1 = cv.take<unsigned>(max_g);
     size_t o_geo0 = cv.take<float4>(max_g), o_geo1 = cv.take<float4>(max_g), o_geo2 = cv.take<int4>(max_g);
     size_t o_hist = cv.take<unsigned>(8 * 256), o_offs = cv.take<unsigned>(8 * 256);
     size_t o_desc = cv.take<unsigned long long>(f->sort.max_tiles * 256);
@@ -302,6 +309,15 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     f->starts = (unsigned *)(b + o_starts);
     f->chunk_base = (unsigned long long *)(b + o_cbase);
     f->chunk_hits = (unsigned *)(b + o_chits);
+    f->vis_base = (unsigned long long *)(b + o_vbase);
+    f->chunk_base2 = (unsigned long long *)(b + o_cbase2);
+    f->chunk_vis = (unsigned *)(b + o_cvis);
+    f->chunk_hits2 = (unsigned *)(b + o_chits2);
+    f->counts = (unsigned *)(b + o_counts);
+    f->dkey[0] = (unsigned *)(b + o_dk0);
+    f->dkey[1] = (unsigned *)(b + o_dk1);
+    f->dval[0] = (unsigned *)(b + o_dv0);
+    f->dval[1] = (unsigned *)(b + o_dv1);
     f->geo0 = (float4 *)(b + o_geo0);
     f->geo1 = (float4 *)(b + o_geo1);
     f->geo2 = (int4 *)(b + o_geo2);
@@ -346,7 +362,8 @@ gs_status gs_frame_set_tuning(gs_frame *f, const gs_tuning *t) {
     if (!f || !t) return fail(GS_ERR_INVALID_ARG, "NULL frame or tuning");
     if (t->blend_variant < 0 || t->blend_variant >= blend_variant_count())
         return fail(GS_ERR_INVALID_ARG, "blend_variant %d out of range", t->blend_variant);
-    if (t->blend_variant != f->tuning.blend_variant && f->exec) {
+    if (t->sort_mode < 0 || t->sort_mode > 1) return fail(GS_ERR_INVALID_ARG, "sort_mode %d not 0 or 1", t->sort_mode);
+    if ((t->blend_variant != f->tuning.blend_variant || t->sort_mode != f->tuning.sort_mode) && f->exec) {
         cudaGraphExecDestroy(f->exec);
         f->exec = nullptr;
     }
@@ -439,11 +456,26 @@ gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, co
     a.geo2 = f->geo2;
     a.chunk_hits = f->chunk_hits;
     a.chunk_base = f->chunk_base;
+    a.counts = f->counts;
+    a.tkeys = (unsigned *)f->keys[0];
+    a.chunk_vis = f->chunk_vis;
+    a.vis_base = f->vis_base;
+    a.dkey = f->dkey[0];
+    a.dval = f->dval[0];
+    a.dkey_tmp = f->dkey[1];
+    a.dval_tmp = f->dval[1];
+    a.dsorted = f->dval[0];
+    a.chunk_hits2 = f->chunk_hits2;
+    a.chunk_base2 = f->chunk_base2;
     a.ctr = f->ctr;
     a.pair_cap = f->max_pairs;
     a.n_chunks = (int)((s->P + preprocess_chunk() - 1) / preprocess_chunk());
     GS_CUDA(cudaMemsetAsync(f->ctr, 0, offsetof(FrameCounters, sort_epoch), st));
-    launch_preprocess(a, st);
+    f->mode_used = f->tuning.sort_mode;
+    if (f->mode_used == 1)
+        launch_preprocess_depth(a, f->sort, st);
+    else
+        launch_preprocess(a, st);
     GS_CUDA(cudaGetLastError());
     f->W = c.W;
     f->H = c.H;
@@ -456,9 +488,15 @@ gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, co
 gs_status gs_sort(gs_frame *f, gs_stream stream) {
     if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
     if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_sort before gs_preprocess");
-    const int end_bit = 32 + ceil_log2((long long)f->tiles_x * f->tiles_y);
-    f->passes = launch_sort(f->keys[0], f->vals[0], f->keys[1], f->vals[1], &f->ctr->n_pairs, 0, f->max_pairs,
-                            end_bit, f->sort, f->ctr, (cudaStream_t)stream);
+    const int tile_bits = ceil_log2((long long)f->tiles_x * f->tiles_y);
+    if (f->mode_used == 1) {
+        f->passes = launch_sort32((unsigned *)f->keys[0], f->vals[0], (unsigned *)f->keys[1], f->vals[1],
+                                  &f->ctr->n_pairs, f->max_pairs, tile_bits > 0 ? tile_bits : 1, f->sort, f->ctr,
+                                  (cudaStream_t)stream);
+    } else {
+        f->passes = launch_sort(f->keys[0], f->vals[0], f->keys[1], f->vals[1], &f->ctr->n_pairs, 0, f->max_pairs,
+                                32 + tile_bits, f->sort, f->ctr, (cudaStream_t)stream);
+    }
     GS_CUDA(cudaGetLastError());
     f->sorted_buf = f->passes & 1;
     return GS_OK;
@@ -467,8 +505,12 @@ gs_status gs_sort(gs_frame *f, gs_stream stream) {
 gs_status gs_ranges(gs_frame *f, gs_stream stream) {
     if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
     if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_ranges before gs_preprocess");
-    launch_ranges(f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs, f->tiles_x * f->tiles_y, f->starts,
-                  (cudaStream_t)stream);
+    if (f->mode_used == 1)
+        launch_ranges32((const unsigned *)f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs,
+                        f->tiles_x * f->tiles_y, f->starts, (cudaStream_t)stream);
+    else
+        launch_ranges(f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs, f->tiles_x * f->tiles_y, f->starts,
+                      (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -588,7 +630,7 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     out->culled_in = c.n_culled_in;
     out->evaluations = (int64_t)c.evals[0];
     out->contributions = (int64_t)c.evals[1];
-    out->kernels = 7 + f->passes;
+    out->kernels = f->mode_used == 1 ? 16 + f->passes : 7 + f->passes;
     return GS_OK;
 }
 
@@ -625,7 +667,13 @@ gs_status gs_frame_pairs(gs_frame *f, int32_t which, uint64_t *keys, uint32_t *v
     if (m > cap) m = cap;
     const int b = which ? f->sorted_buf : 0;
     if (m > 0) {
-        if (keys) GS_CUDA(cudaMemcpyAsync(keys, f->keys[b], (size_t)m * 8, cudaMemcpyDeviceToDevice, st));
+        if (keys) {
+            if (f->mode_used == 1)   // rebuild (tile << 32 | depth bits) from the 32-bit tile keys
+                launch_make_keys((const unsigned *)f->keys[b], f->vals[b], f->geo1, m, (unsigned long long *)keys, st);
+            else
+                GS_CUDA(cudaMemcpyAsync(keys, f->keys[b], (size_t)m * 8, cudaMemcpyDeviceToDevice, st));
+            GS_CUDA(cudaGetLastError());
+        }
         if (vals) GS_CUDA(cudaMemcpyAsync(vals, f->vals[b], (size_t)m * 4, cudaMemcpyDeviceToDevice, st));
     }
     GS_CUDA(cudaStreamSynchronize(st));
@@ -704,14 +752,15 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
         FILE *fp = fopen(cache_path, "r");
         if (fp) {
             char line[512];
-            int found = -1;
+            int found_v = -1, found_m = -1;
             const size_t kl = strlen(key);
             while (fgets(line, sizeof(line), fp))
-                if (strncmp(line, key, kl) == 0 && line[kl] == ' ') found = atoi(line + kl + 1);
+                if (strncmp(line, key, kl) == 0 && line[kl] == ' ') sscanf(line + kl + 1, "%d %d", &found_v, &found_m);
             fclose(fp);
-            if (found >= 0 && found < blend_variant_count()) {
+            if (found_v >= 0 && found_v < blend_variant_count() && (found_m == 0 || found_m == 1)) {
                 gs_tuning t = f->tuning;
-                t.blend_variant = found;
+                t.blend_variant = found_v;
+                t.sort_mode = found_m;
                 gs_status st = gs_frame_set_tuning(f, &t);
                 if (st) return st;
                 if (out) *out = f->tuning;
@@ -726,34 +775,58 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
     const int timing_before = f->timing;
     if ((st = gs_frame_enable_timing(f, 1))) return st;
     cudaStream_t cs = (cudaStream_t)stream;
-    int best = f->tuning.blend_variant;
+    // time `ncams` renders with the current tuning; returns the summed stage times
+    auto timed = [&](float stage_ms[4]) -> gs_status {
+        gs_status r = gs_render(f, s, &cams[0], opts, rgb, T, last, stream);   // warm-up
+        if (r) return r;
+        for (int i = 0; i < 4; ++i) stage_ms[i] = 0.0f;
+        for (int c = 0; c < ncams; ++c) {
+            if ((r = gs_render(f, s, &cams[c], opts, rgb, T, last, stream))) return r;
+            float ms[4];
+            if ((r = gs_frame_stage_ms(f, ms))) return r;
+            for (int i = 0; i < 4; ++i) stage_ms[i] += ms[i];
+        }
+        return GS_OK;
+    };
+    // 1) ordering: preprocess + sort + ranges time of each sort mode
+    int best_mode = f->tuning.sort_mode;
     float best_ms = 1e30f;
+    for (int m = 0; m <= 1; ++m) {
+        gs_tuning t = f->tuning;
+        t.sort_mode = m;
+        if ((st = gs_frame_set_tuning(f, &t))) return st;
+        float ms[4];
+        if ((st = timed(ms))) return st;
+        if (ms[0] + ms[1] + ms[2] < best_ms) {
+            best_ms = ms[0] + ms[1] + ms[2];
+            best_mode = m;
+        }
+    }
+    // 2) blend launch shape
+    int best = f->tuning.blend_variant;
+    best_ms = 1e30f;
     for (int v = 0; v < blend_variant_count(); ++v) {
         gs_tuning t = f->tuning;
+        t.sort_mode = best_mode;
         t.blend_variant = v;
         if ((st = gs_frame_set_tuning(f, &t))) return st;
-        if ((st = gs_render(f, s, &cams[0], opts, rgb, T, last, stream))) return st;
-        float total = 0.0f;
-        for (int c = 0; c < ncams; ++c) {
-            if ((st = gs_render(f, s, &cams[c], opts, rgb, T, last, stream))) return st;
-            float ms[4];
-            if ((st = gs_frame_stage_ms(f, ms))) return st;
-            total += ms[3];
-        }
-        if (total < best_ms) {
-            best_ms = total;
+        float ms[4];
+        if ((st = timed(ms))) return st;
+        if (ms[3] < best_ms) {
+            best_ms = ms[3];
             best = v;
         }
     }
     GS_CUDA(cudaStreamSynchronize(cs));
     gs_tuning t = f->tuning;
     t.blend_variant = best;
+    t.sort_mode = best_mode;
     if ((st = gs_frame_set_tuning(f, &t))) return st;
     if ((st = gs_frame_enable_timing(f, timing_before))) return st;
     if (cache_path) {
         FILE *fp = fopen(cache_path, "a");
         if (fp) {
-            fprintf(fp, "%s %d\n", key, best);
+            fprintf(fp, "%s %d %d\n", key, best, best_mode);
             fclose(fp);
         }
     }

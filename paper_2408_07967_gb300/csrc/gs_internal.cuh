@@ -68,6 +68,8 @@ struct FrameCounters {
     unsigned int n_culled_in;        // Gaussians passing the near-plane / opacity cull
     unsigned int status;             // kSt* bits
     unsigned int chunk_ticket;       // preprocess chunk ticket
+    unsigned long long n_vis64;      // paired Gaussians (two-level order)
+    unsigned long long scratch64;    // unused scan total
     unsigned int sort_ticket[8];     // scatter-pass tickets
     unsigned int sort_epoch;         // bumped once per sort; tags look-back descriptors
     unsigned int pad1[7];
@@ -209,6 +211,15 @@ struct PreprocessArgs {
     int4 *geo2;                      // per Gaussian: (tx0, ty0, w, h) of the candidate box, 0 if unpaired
     unsigned *chunk_hits;            // pairs per 256-Gaussian chunk
     unsigned long long *chunk_base;  // exclusive scan of chunk_hits
+    unsigned *counts;                // pairs per Gaussian
+    // two-level order
+    unsigned *tkeys;                 // 32-bit tile keys (aliases the pair key buffer)
+    unsigned *chunk_vis;             // paired Gaussians per chunk
+    unsigned long long *vis_base;    // exclusive scan of chunk_vis
+    unsigned *dkey, *dval, *dkey_tmp, *dval_tmp;   // (depth bits, id) of paired Gaussians + ping-pong
+    const unsigned *dsorted;         // ids in depth order (== dval after the sort)
+    unsigned *chunk_hits2;           // pairs per chunk of 256 depth-sorted Gaussians
+    unsigned long long *chunk_base2; // exclusive scan of chunk_hits2
     FrameCounters *ctr;
     long long pair_cap;
     int n_chunks;
@@ -217,6 +228,10 @@ struct PreprocessArgs {
 void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *scale, float4 *quat, float4 *sh,
                        cudaStream_t s);
 void launch_preprocess(const PreprocessArgs &a, cudaStream_t s);
+struct SortScratch;
+int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cudaStream_t s);
+void launch_make_keys(const unsigned *tkeys, const unsigned *vals, const float4 *geo1, long long n,
+                      unsigned long long *out, cudaStream_t s);
 int preprocess_chunk();
 
 struct SortScratch {
@@ -235,6 +250,12 @@ int launch_sort(unsigned long long *keys, unsigned *vals, unsigned long long *ke
                 const SortScratch &scr, FrameCounters *ctr, cudaStream_t s);
 void launch_ranges(const unsigned long long *keys, const unsigned long long *n_dev, long long cap, int ntiles,
                    unsigned *starts, cudaStream_t s);
+// 32-bit-key forms (depth bits alone, tile id alone) used by the two-level sort.
+int launch_sort32(unsigned *keys, unsigned *vals, unsigned *keys_tmp, unsigned *vals_tmp,
+                  const unsigned long long *n_dev, long long cap, int end_bit, const SortScratch &scr,
+                  FrameCounters *ctr, cudaStream_t s);
+void launch_ranges32(const unsigned *keys, const unsigned long long *n_dev, long long cap, int ntiles,
+                     unsigned *starts, cudaStream_t s);
 
 struct BlendArgs {
     const Rec *recs;

@@ -269,7 +269,7 @@ struct PreSmem {
     unsigned zb[kPreBlock];
     int tx0[kPreBlock], ty0[kPreBlock], w[kPreBlock];
     int cstart[kPreBlock + 1];        // exclusive scan of candidate-tile counts
-    unsigned char any[kPreBlock];     // Gaussian has at least one pair
+    unsigned cnt[kPreBlock];          // pairs of each Gaussian of the chunk
     unsigned wsum[kPreBlock / 32];
 };
 
@@ -349,25 +349,32 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constan
         S.ty0[tid] = G.ty0;
     }
     S.w[tid] = w > 0 ? w : 1;
-    S.any[tid] = 0;
+    S.cnt[tid] = 0;
     const int ctotal = block_scan_cand(S, ncand);
 
     unsigned hits = 0;
     for (int base = 0; base < ctotal; base += kPreBlock) {
         const int slot = base + tid;
         bool hit = false;
+        int g = -1;
         if (slot < ctotal) {
-            int g, tile;
+            int tile;
             hit = slot_test(S, cam, slot, g, tile);
-            if (hit) S.any[g] = 1;
         }
+        // consecutive slots share Gaussians: one shared-memory add per (warp, Gaussian)
+        const unsigned peers = __match_any_sync(FULL, g);
+        const unsigned hm = __ballot_sync(FULL, hit) & peers;
+        if (g >= 0 && hm && lane == __ffs(peers) - 1) atomicAdd(&S.cnt[g], (unsigned)__popc(hm));
         hits += (unsigned)__syncthreads_count(hit);
     }
-    if (tid == 0) A.chunk_hits[chunk] = hits;
-
-    const bool vis = S.any[tid] != 0;
-    const unsigned nvis = __popc(__ballot_sync(FULL, vis));
-    if (lane == 0 && nvis) atomicAdd(&A.ctr->n_visible, nvis);
+    const bool vis = S.cnt[tid] != 0;
+    const unsigned nvis_block = (unsigned)__syncthreads_count(vis);
+    if (tid == 0) {
+        A.chunk_hits[chunk] = hits;
+        A.chunk_vis[chunk] = nvis_block;
+        if (nvis_block) atomicAdd(&A.ctr->n_visible, nvis_block);
+    }
+    if (gid < A.scene.P) A.counts[gid] = S.cnt[tid];
     if (gid < A.scene.P) A.geo2[gid] = vis ? make_int4(G.tx0, G.ty0, w, h) : make_int4(0, 0, 0, 0);
     if (vis) {
         A.geo0[gid] = make_float4(G.u, G.v, G.a, G.b);
@@ -385,22 +392,22 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constan
     }
 }
 
-// Pass 2: exclusive scan of the chunk pair counts (one CTA; each thread sums a run of chunks).
+// Exclusive scan of up to two arrays of chunk counts (one CTA; each thread sums a run of chunks).
+// Writes the totals to *tot_a / *tot_b.
 constexpr int kScanThreads = 1024;
 constexpr int kScanRun = 16;
-__global__ void __launch_bounds__(kScanThreads) k_pre_scan(const __grid_constant__ PreprocessArgs A) {
+__device__ void chunk_scan(const unsigned *in, unsigned long long *out, long long n, unsigned long long *total) {
     __shared__ unsigned long long s_w[kScanThreads / 32];
     __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_carry = 0;
     __syncthreads();
-    const long long n = A.n_chunks;
     for (long long base = 0; base < n; base += (long long)kScanThreads * kScanRun) {
         const long long my0 = base + (long long)tid * kScanRun;
         unsigned long long sum = 0;
 #pragma unroll
         for (int r = 0; r < kScanRun; ++r)
-            if (my0 + r < n) sum += A.chunk_hits[my0 + r];
+            if (my0 + r < n) sum += in[my0 + r];
         unsigned long long incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -416,33 +423,91 @@ __global__ void __launch_bounds__(kScanThreads) k_pre_scan(const __grid_constant
             tot += x;
         }
         unsigned long long run = s_carry + wex + incl - sum;
+        if (out) {
 #pragma unroll
-        for (int r = 0; r < kScanRun; ++r)
-            if (my0 + r < n) {
-                A.chunk_base[my0 + r] = run;
-                run += A.chunk_hits[my0 + r];
-            }
+            for (int r = 0; r < kScanRun; ++r)
+                if (my0 + r < n) {
+                    out[my0 + r] = run;
+                    run += in[my0 + r];
+                }
+        }
         __syncthreads();
         if (tid == 0) s_carry += tot;
         __syncthreads();
     }
-    if (tid == 0) {
-        A.ctr->n_pairs = s_carry;
-        if ((long long)s_carry > A.pair_cap) atomicOr(&A.ctr->status, kStPairOverflow);
+    if (tid == 0) *total = s_carry;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_chunk_scan(const unsigned *in_a, unsigned long long *out_a,
+                                                             unsigned long long *tot_a, const unsigned *in_b,
+                                                             unsigned long long *out_b, unsigned long long *tot_b,
+                                                             long long n, long long pair_cap, unsigned *status) {
+    chunk_scan(in_a, out_a, n, tot_a);
+    if (in_b) chunk_scan(in_b, out_b, n, tot_b);
+    if (threadIdx.x == 0 && status && (long long)*tot_a > pair_cap) atomicOr(status, kStPairOverflow);
+}
+
+// Two-level order, step 1: the paired Gaussians of each chunk, compacted in id order, as
+// (depth bits, id) for the depth sort.
+__global__ void __launch_bounds__(kPreBlock) k_vis_compact(const __grid_constant__ PreprocessArgs A) {
+    const long long chunk = blockIdx.x;
+    const long long gid = chunk * kPreBlock + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ unsigned s_w[kPreBlock / 32];
+    const bool vis = gid < A.scene.P && A.counts[gid] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, vis);
+    if (lane == 0) s_w[warp] = __popc(bal);
+    __syncthreads();
+    unsigned pre = 0;
+    for (int w2 = 0; w2 < warp; ++w2) pre += s_w[w2];
+    if (vis) {
+        const unsigned long long pos = A.vis_base[chunk] + pre + __popc(bal & ((1u << lane) - 1u));
+        A.dkey[pos] = __float_as_uint(A.geo1[gid].z);
+        A.dval[pos] = (unsigned)gid;
     }
 }
 
-// Pass 3: the same load-balanced tests; every hit is written at the chunk's base + its rank in
-// slot order, i.e. pairs land in (Gaussian id, tile row-major) order.
+// Two-level order, step 2: pairs per chunk of 256 depth-sorted Gaussians.
+__global__ void __launch_bounds__(kPreBlock) k_emit_sum(const __grid_constant__ PreprocessArgs A) {
+    const long long r = (long long)blockIdx.x * kPreBlock + threadIdx.x;
+    const long long V = (long long)A.ctr->n_vis64;
+    const unsigned c = r < V ? A.counts[A.dsorted[r]] : 0u;
+    unsigned v = c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ unsigned s_w[kPreBlock / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w2 = 0; w2 < kPreBlock / 32; ++w2) t += s_w[w2];
+        A.chunk_hits2[blockIdx.x] = t;
+    }
+}
+
+// Emission: the same load-balanced tests; every hit is written at the chunk's base + its rank in
+// slot order.  DEPTH = false: chunk c holds Gaussians 256c .. 256c+255 and the pairs land in
+// (Gaussian id, tile row-major) order with 64-bit (tile, depth) keys.  DEPTH = true: chunk c holds
+// the depth-sorted Gaussians of ranks 256c .. 256c+255 and the pairs land in (depth, id, tile)
+// order with the tile id alone as a 32-bit key -- a stable sort by tile then yields exactly the
+// (tile, depth, id) order of the 64-bit keys.
+template <bool DEPTH>
 __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
     __shared__ PreSmem S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const long long chunk = blockIdx.x;
-    const long long gid = chunk * kPreBlock + tid;
+    long long gid = chunk * kPreBlock + tid;
+    bool in_range = gid < A.scene.P;
+    if (DEPTH) {
+        in_range = gid < (long long)A.ctr->n_vis64;
+        gid = in_range ? (long long)A.dsorted[gid] : 0;
+    }
     const Cam &cam = A.cam;
     int ncand = 0;
-    if (gid < A.scene.P) {
+    S.cnt[tid] = (unsigned)gid;
+    if (in_range) {
         const int4 g2 = A.geo2[gid];
         ncand = g2.z * g2.w;
         if (ncand > 0) {
@@ -464,7 +529,7 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
     const int ctotal = block_scan_cand(S, ncand);
     const long long cap = A.pair_cap;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long run = A.chunk_base[chunk];
+    unsigned long long run = DEPTH ? A.chunk_base2[chunk] : A.chunk_base[chunk];
     for (int base = 0; base < ctotal; base += kPreBlock) {
         const int slot = base + tid;
         bool hit = false;
@@ -483,8 +548,11 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
         if (hit) {
             const unsigned long long pos = run + wpre + __popc(bal & lt);
             if ((long long)pos < cap) {
-                A.keys[pos] = ((unsigned long long)(unsigned)tile << 32) | S.zb[g];
-                A.vals[pos] = (unsigned)(chunk * kPreBlock + g);
+                if (DEPTH)
+                    A.tkeys[pos] = (unsigned)tile;
+                else
+                    A.keys[pos] = ((unsigned long long)(unsigned)tile << 32) | S.zb[g];
+                A.vals[pos] = S.cnt[g];        // Gaussian id of slot g
             }
         }
         run += tot;
@@ -495,8 +563,38 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
 void launch_preprocess(const PreprocessArgs &a, cudaStream_t s) {
     if (a.n_chunks <= 0) return;
     k_pre_count<<<a.n_chunks, kPreBlock, 0, s>>>(a);
-    k_pre_scan<<<1, kScanThreads, 0, s>>>(a);
-    k_pre_emit<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, a.chunk_base, &a.ctr->n_pairs, nullptr, nullptr, nullptr,
+                                            a.n_chunks, a.pair_cap, &a.ctr->status);
+    k_pre_emit<false><<<a.n_chunks, kPreBlock, 0, s>>>(a);
+}
+
+int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cudaStream_t s) {
+    if (a.n_chunks <= 0) return 0;
+    k_pre_count<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, nullptr, &a.ctr->n_pairs, a.chunk_vis, a.vis_base,
+                                            &a.ctr->n_vis64, a.n_chunks, a.pair_cap, &a.ctr->status);
+    k_vis_compact<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    // depth sort of the paired Gaussians: 32-bit float bits of z (positive, so bit order = value order)
+    const int dp = launch_sort32(a.dkey, a.dval, a.dkey_tmp, a.dval_tmp, &a.ctr->n_vis64, a.scene.P, 32, scr, a.ctr, s);
+    (void)dp;   // four passes: the result is back in dkey / dval
+    k_emit_sum<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    unsigned long long *unused_total = &a.ctr->scratch64;
+    k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits2, a.chunk_base2, unused_total, nullptr, nullptr, nullptr,
+                                            a.n_chunks, 1ll << 62, nullptr);
+    k_pre_emit<true><<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    return 4;
+}
+
+__global__ void k_make_keys(const unsigned *tkeys, const unsigned *vals, const float4 *geo1, long long n,
+                            unsigned long long *out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ((unsigned long long)tkeys[i] << 32) | __float_as_uint(geo1[vals[i]].z);
+}
+
+void launch_make_keys(const unsigned *tkeys, const unsigned *vals, const float4 *geo1, long long n,
+                      unsigned long long *out, cudaStream_t s) {
+    if (n <= 0) return;
+    k_make_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tkeys, vals, geo1, n, out);
 }
 
 }  // namespace gs

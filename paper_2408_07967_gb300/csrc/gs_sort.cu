@@ -33,7 +33,8 @@ __device__ __forceinline__ long long pair_count(const unsigned long long *n_dev,
 }
 
 // ------------------------------------------------------------------------------------------ histogram
-__global__ void __launch_bounds__(512) k_sort_hist(const unsigned long long *keys, const unsigned long long *n_dev,
+template <class K>
+__global__ void __launch_bounds__(512) k_sort_hist(const K *keys, const unsigned long long *n_dev,
                                                    long long n_host, long long cap, int passes, unsigned *hist) {
     __shared__ unsigned s_h[8 * 256];
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) s_h[i] = 0;
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(512) k_sort_hist(const unsigned long long *key
     const long long n = pair_count(n_dev, n_host, cap);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned long long k = keys[i];
+        const K k = keys[i];
         for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k >> (8 * p)) & 0xffu)], 1u);
     }
     __syncthreads();
@@ -75,8 +76,9 @@ __global__ void __launch_bounds__(256) k_sort_offsets(unsigned *hist, unsigned *
 }
 
 // ------------------------------------------------------------------------------------------ scatter
+template <class K>
 struct ScatterSmem {
-    unsigned long long keys[kSortTile];
+    K keys[kSortTile];
     unsigned vals[kSortTile];
     unsigned whist[kSortWarps][256];
     unsigned local_off[256];
@@ -85,15 +87,16 @@ struct ScatterSmem {
     unsigned tile;
 };
 
-__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const unsigned long long *__restrict__ kin,
+template <class K>
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__restrict__ kin,
                                                                const unsigned *__restrict__ vin,
-                                                               unsigned long long *__restrict__ kout,
+                                                               K *__restrict__ kout,
                                                                unsigned *__restrict__ vout,
                                                                const unsigned long long *n_dev, long long n_host,
                                                                long long cap, int pass, const unsigned *offs,
                                                                unsigned long long *desc, FrameCounters *ctr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const int shift = 8 * pass;
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const unsigned
         const long long tbase = tile * kSortTile;
         const long long wbase = tbase + (long long)warp * (32 * kSortItems);
 
-        unsigned long long k[kSortItems];
+        K k[kSortItems];
         unsigned v[kSortItems];
         unsigned rank[kSortItems];
 #pragma unroll
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const unsigned
                 k[i] = kin[idx];
                 v[i] = vin[idx];
             } else {
-                k[i] = ~0ull;
+                k[i] = (K)~(K)0;
                 v[i] = 0u;
             }
         }
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const unsigned
         }
         __syncthreads();
         for (int s = tid; s < valid_here; s += kSortThreads) {
-            const unsigned long long key = S.keys[s];
+            const K key = S.keys[s];
             const unsigned d = (unsigned)(key >> shift) & 0xffu;
             const unsigned long long dst = S.gbase[d] + (unsigned long long)(s - S.local_off[d]);
             kout[dst] = key;
@@ -213,33 +216,41 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const unsigned
     }
 }
 
-static int g_scatter_grid = 0;
-
-int launch_sort(unsigned long long *keys, unsigned *vals, unsigned long long *keys_tmp, unsigned *vals_tmp,
-                const unsigned long long *n_dev, long long n_host, long long cap, int end_bit,
-                const SortScratch &scr, FrameCounters *ctr, cudaStream_t s) {
-    const int passes = (end_bit + 7) / 8;
-    if (g_scatter_grid == 0) {
+template <class K>
+static int scatter_grid() {
+    static int grid = 0;
+    if (grid == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter, kSortThreads, sizeof(ScatterSmem));
-        g_scatter_grid = sms * (per_sm > 0 ? per_sm : 1);
+        cudaFuncSetAttribute(k_sort_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ScatterSmem<K>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter<K>, kSortThreads,
+                                                      sizeof(ScatterSmem<K>));
+        grid = sms * (per_sm > 0 ? per_sm : 1);
     }
+    return grid;
+}
+
+template <class K>
+static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tmp, const unsigned long long *n_dev,
+                         long long n_host, long long cap, int end_bit, const SortScratch &scr, FrameCounters *ctr,
+                         cudaStream_t s) {
+    const int passes = (end_bit + 7) / 8;
+    const int sgrid = scatter_grid<K>();
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_sort_hist<<<sms * 2, 512, 0, s>>>(keys, n_dev, n_host, cap, passes, scr.hist);
+    k_sort_hist<K><<<sms * 2, 512, 0, s>>>(keys, n_dev, n_host, cap, passes, scr.hist);
     k_sort_offsets<<<passes, 256, 0, s>>>(scr.hist, scr.offs, ctr);
     long long max_tiles = sort_max_tiles_for(cap);
-    int grid = (int)min((long long)g_scatter_grid, max_tiles > 0 ? max_tiles : 1);
-    unsigned long long *ka = keys, *kb = keys_tmp;
+    int grid = (int)min((long long)sgrid, max_tiles > 0 ? max_tiles : 1);
+    K *ka = keys, *kb = keys_tmp;
     unsigned *va = vals, *vb = vals_tmp;
     for (int p = 0; p < passes; ++p) {
-        k_sort_scatter<<<grid, kSortThreads, sizeof(ScatterSmem), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p, scr.offs,
-                                                                       scr.desc, ctr);
-        unsigned long long *tk = ka;
+        k_sort_scatter<K><<<grid, kSortThreads, sizeof(ScatterSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
+                                                                             scr.offs, scr.desc, ctr);
+        K *tk = ka;
         ka = kb;
         kb = tk;
         unsigned *tv = va;
@@ -249,13 +260,28 @@ int launch_sort(unsigned long long *keys, unsigned *vals, unsigned long long *ke
     return passes;
 }
 
+int launch_sort(unsigned long long *keys, unsigned *vals, unsigned long long *keys_tmp, unsigned *vals_tmp,
+                const unsigned long long *n_dev, long long n_host, long long cap, int end_bit,
+                const SortScratch &scr, FrameCounters *ctr, cudaStream_t s) {
+    return launch_sort_t<unsigned long long>(keys, vals, keys_tmp, vals_tmp, n_dev, n_host, cap, end_bit, scr, ctr,
+                                             s);
+}
+
+int launch_sort32(unsigned *keys, unsigned *vals, unsigned *keys_tmp, unsigned *vals_tmp,
+                  const unsigned long long *n_dev, long long cap, int end_bit, const SortScratch &scr,
+                  FrameCounters *ctr, cudaStream_t s) {
+    return launch_sort_t<unsigned>(keys, vals, keys_tmp, vals_tmp, n_dev, 0, cap, end_bit, scr, ctr, s);
+}
+
 // ------------------------------------------------------------------------------------------ ranges
-__global__ void k_tile_starts(const unsigned long long *keys, const unsigned long long *n_dev, long long cap,
-                              int ntiles, unsigned *starts) {
+// Key layouts: (tile << 32 | depth bits) as u64 (shift 32), or the tile id alone as u32 (shift 0).
+template <class K, int SHIFT>
+__global__ void k_tile_starts(const K *keys, const unsigned long long *n_dev, long long cap, int ntiles,
+                              unsigned *starts) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b > ntiles) return;
     const long long n = pair_count(n_dev, 0, cap);
-    const unsigned long long target = (unsigned long long)b << 32;
+    const K target = (K)b << SHIFT;
     long long lo = 0, hi = n;
     while (lo < hi) {
         const long long mid = (lo + hi) >> 1;
@@ -271,7 +297,14 @@ void launch_ranges(const unsigned long long *keys, const unsigned long long *n_d
                    unsigned *starts, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (ntiles + 1 + threads - 1) / threads;
-    k_tile_starts<<<blocks, threads, 0, s>>>(keys, n_dev, cap, ntiles, starts);
+    k_tile_starts<unsigned long long, 32><<<blocks, threads, 0, s>>>(keys, n_dev, cap, ntiles, starts);
+}
+
+void launch_ranges32(const unsigned *keys, const unsigned long long *n_dev, long long cap, int ntiles,
+                     unsigned *starts, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (ntiles + 1 + threads - 1) / threads;
+    k_tile_starts<unsigned, 0><<<blocks, threads, 0, s>>>(keys, n_dev, cap, ntiles, starts);
 }
 
 }  // namespace gs

@@ -29,11 +29,10 @@ def ctx():
     return gs.Context(0)
 
 
-def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False, variant=None):
+def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False, variant=None, sort_mode=None):
     sc = gs.Scene.from_numpy(ctx, scene)
     fr = gs.Frame(ctx, scene.P, max_pairs, cam.width, cam.height)
-    if variant is not None:
-        fr.gs_frame_set_tuning(variant)
+    fr.gs_frame_set_tuning(blend_variant=variant, sort_mode=sort_mode)
     o = gs.gs_opts(**(opts_kw or {}))
     H, W = cam.height, cam.width
     rgb = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
@@ -61,6 +60,7 @@ def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False, varia
     if ku is not None:
         out["keys_unsorted"] = ku.cpu().numpy().view(np.uint64)
         out["vals_unsorted"] = vu.cpu().numpy().view(np.uint32)
+    out["sort_mode"] = fr.gs_frame_get_tuning()["sort_mode"]
     fr.close()
     sc.close()
     return out
@@ -72,8 +72,13 @@ def check(res, ref, check_unsorted=True):
     assert st["pairs"] == ref.N
     assert st["visible"] == ref.visible
     if check_unsorted and "keys_unsorted" in res:
-        assert np.array_equal(res["keys_unsorted"], ref.keys_unsorted)
-        assert np.array_equal(res["vals_unsorted"], ref.vals_unsorted)
+        ku, vu = ref.keys_unsorted, ref.vals_unsorted
+        if res["sort_mode"] == 1:
+            # two-level order: pairs emitted in (depth bits, Gaussian id, tile) order
+            order = np.lexsort((ku >> np.uint64(32), vu, ku & np.uint64(0xffffffff)))
+            ku, vu = ku[order], vu[order]
+        assert np.array_equal(res["keys_unsorted"], ku)
+        assert np.array_equal(res["vals_unsorted"], vu)
     assert np.array_equal(res["keys"], ref.keys)
     assert np.array_equal(res["vals"], ref.vals)
     starts = res["starts"].astype(np.int64)
@@ -92,25 +97,28 @@ def check(res, ref, check_unsorted=True):
         assert np.all(np.abs(ref.T[diff] - 1e-4) <= 5e-5 + 0.01 * ref.T[diff])
 
 
-def test_tiny_config_parity(ctx):
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_tiny_config_parity(ctx, sort_mode):
     scene, cams = synth.load_config("tiny")
     ref = oracle.Frame(scene, cams[0], mode=64)
-    check(run_gpu(ctx, scene, cams[0]), ref)
+    check(run_gpu(ctx, scene, cams[0], sort_mode=sort_mode), ref)
 
 
+@pytest.mark.parametrize("sort_mode", [0, 1])
 @pytest.mark.parametrize("W,H", [(100, 76), (17, 33), (1, 1), (256, 130)])
-def test_ragged_images(ctx, W, H):
+def test_ragged_images(ctx, W, H, sort_mode):
     scene, cam = synth.random_small_scene(2500, 31 + W, W, H, log_scale_mu=-2.6, log_scale_sigma=1.0)
     ref = oracle.Frame(scene, cam, mode=64)
-    check(run_gpu(ctx, scene, cam), ref)
+    check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
 
 
+@pytest.mark.parametrize("sort_mode", [0, 1])
 @pytest.mark.parametrize("opts_kw", [dict(cap_3sigma=True), dict(bg=(0.3, 0.6, 0.1)),
                                      dict(clamp_fov=False, dilation=0.1), dict(tau=0.02, T_min=1e-3)])
-def test_options(ctx, opts_kw):
+def test_options(ctx, opts_kw, sort_mode):
     scene, cam = synth.random_small_scene(3000, 11, 128, 96, log_scale_mu=-2.4, log_scale_sigma=1.0)
     ref = oracle.Frame(scene, cam, oracle.opts(**opts_kw), mode=64)
-    check(run_gpu(ctx, scene, cam, opts_kw), ref)
+    check(run_gpu(ctx, scene, cam, opts_kw, sort_mode=sort_mode), ref)
 
 
 def test_raw_parameters_activated_on_device(ctx):
@@ -119,13 +127,14 @@ def test_raw_parameters_activated_on_device(ctx):
     check(run_gpu(ctx, scene, cam), ref)
 
 
-def test_large_gaussians_multi_chunk_tile_tests(ctx):
-    """Gaussians covering more than 32 candidate tiles take the multi-ballot path."""
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_large_gaussians_many_candidate_tiles(ctx, sort_mode):
+    """Gaussians with hundreds of candidate tiles spread over many load-balanced steps."""
     scene, cam = synth.random_small_scene(400, 13, 320, 240, log_scale_mu=-1.2, log_scale_sigma=0.5)
     ref = oracle.Frame(scene, cam, mode=64)
-    big = ((ref.rect[:, 1] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 2] + 1) > 32) & (ref.valid > 0)
-    assert big.sum() > 20
-    check(run_gpu(ctx, scene, cam), ref)
+    big = ((ref.rect[:, 1] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 2] + 1) > 256) & (ref.valid > 0)
+    assert big.sum() > 10
+    check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
 
 
 def test_empty_view(ctx):
@@ -146,24 +155,27 @@ def test_single_gaussian_and_tiny_scene_sizes(ctx):
         check(run_gpu(ctx, scene, cam), ref)
 
 
-def test_pair_overflow_is_reported(ctx):
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_pair_overflow_is_reported(ctx, sort_mode):
     scene, cam = synth.random_small_scene(2000, 16, 128, 96, log_scale_mu=-2.4)
     ref = oracle.Frame(scene, cam, mode=32)
-    res = run_gpu(ctx, scene, cam, max_pairs=ref.N // 3)
+    res = run_gpu(ctx, scene, cam, max_pairs=ref.N // 3, sort_mode=sort_mode)
     assert res["stats"]["status"] == -3, res["stats"]
     assert res["stats"]["pairs"] == ref.N
     # the frame stays usable
     check(run_gpu(ctx, scene, cam), oracle.Frame(scene, cam, mode=64))
 
 
-def test_deterministic_and_graph_replay(ctx):
+def test_deterministic_graph_replay_and_modes_agree(ctx):
     scene, cam = synth.random_small_scene(4000, 17, 160, 120, log_scale_mu=-2.5)
-    a = run_gpu(ctx, scene, cam)
-    b = run_gpu(ctx, scene, cam)
-    c = run_gpu(ctx, scene, cam, graph=True)
+    a = run_gpu(ctx, scene, cam, sort_mode=0)
+    b = run_gpu(ctx, scene, cam, sort_mode=0)
+    c = run_gpu(ctx, scene, cam, graph=True, sort_mode=0)
+    d = run_gpu(ctx, scene, cam, sort_mode=1)
+    e = run_gpu(ctx, scene, cam, graph=True, sort_mode=1)
     for k in ("rgb", "T", "last", "keys", "vals", "starts"):
-        assert np.array_equal(a[k], b[k]), k
-        assert np.array_equal(a[k], c[k]), k
+        for other in (b, c, d, e):
+            assert np.array_equal(a[k], other[k]), k
 
 
 @pytest.mark.parametrize("variant", range(6))
@@ -202,10 +214,10 @@ def test_autotune_picks_a_shape_and_caches_it(ctx, tmp_path):
     ref, _, _ = fr.render(sc, cams[0])
     cache = tmp_path / "tune.txt"
     t1 = fr.gs_autotune(sc, cams, cache_path=cache)
-    assert 0 <= t1["blend_variant"] < 6
+    assert 0 <= t1["blend_variant"] < 6 and t1["sort_mode"] in (0, 1)
     assert fr.gs_frame_get_tuning() == t1
     line = cache.read_text().strip().split()
-    assert line[0] == "gs-autotune-v1" and int(line[-1]) == t1["blend_variant"]
+    assert line[0] == "gs-autotune-v1" and int(line[-2]) == t1["blend_variant"] and int(line[-1]) == t1["sort_mode"]
     fr2 = gs.Frame(ctx, scene.P, 1 << 20, 256, 256)
     assert fr2.gs_autotune(sc, cams, cache_path=cache) == t1          # served from the cache
     out, _, _ = fr2.render(sc, cams[0])
