@@ -16,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gs_oracle.c")
+_SRC_GRAD = os.path.join(_HERE, "gs_oracle_grad.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -26,9 +27,10 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no contraction: binary32 decisions must be reproducible)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_GRAD))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, _SRC_GRAD, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -96,6 +98,20 @@ def lib():
                                     C.c_void_p, C.c_int32, C.c_int32, C.POINTER(OrCamera), C.POINTER(OrOpts),
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, _i64,
                                     C.c_void_p]
+            _vp = C.c_void_p
+            L.or_grad_flags.restype = None
+            L.or_grad_flags.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(OrCamera),
+                                        C.POINTER(OrOpts), _vp, _vp]
+            L.or_forward_fixed.restype = None
+            L.or_forward_fixed.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(OrCamera),
+                                           C.POINTER(OrOpts), _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.or_backward_fixed.restype = None
+            L.or_backward_fixed.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.POINTER(OrCamera),
+                                            C.POINTER(OrOpts), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                            _vp, _vp]
+            L.or_contrib_lists.restype = _i64
+            L.or_contrib_lists.argtypes = [C.POINTER(OrCamera), C.POINTER(OrOpts), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                           _i64]
             L.or_set_threads.restype = None
             L.or_set_threads.argtypes = [C.c_int]
             L.or_get_threads.restype = C.c_int
@@ -303,3 +319,74 @@ def render(scene, cam, o=None, mode=64, sh_degree=3, want_pairs=False):
         out["keys"] = keys[:N]
         out["vals"] = vals[:N]
     return out
+
+
+# ---------------------------------------------------------------------------------------- gradients
+class Params64:
+    """Binary64 copies of a scene's parameters (the variables of the gradient)."""
+
+    def __init__(self, scene):
+        self.means = np.ascontiguousarray(scene.means, np.float64)
+        self.scales = np.ascontiguousarray(scene.scales, np.float64)
+        self.quats = np.ascontiguousarray(scene.quats, np.float64)
+        self.opacity = np.ascontiguousarray(scene.opacity, np.float64)
+        self.sh = np.ascontiguousarray(scene.sh, np.float64).reshape(-1, 16, 3)
+        self.activated = bool(scene.activated)
+        self.P = self.means.shape[0]
+
+    def arrays(self):
+        return [self.means, self.scales, self.quats, self.opacity, self.sh]
+
+    def copy(self):
+        c = Params64.__new__(Params64)
+        c.means, c.scales, c.quats, c.opacity, c.sh = (a.copy() for a in self.arrays())
+        c.activated, c.P = self.activated, self.P
+        return c
+
+
+class Frozen:
+    """The decisions of a reference render (binary64 mode): per-pixel contributor lists with
+    alpha-clamp flags, and per-Gaussian colour / FOV clamp flags.  forward() and backward() are
+    the frozen-decision image and its exact gradient."""
+
+    def __init__(self, scene, cam, o=None, sh_degree=3):
+        self.o = o or opts()
+        self.cam = cam
+        self.cc = camera(cam)
+        self.sh_degree = sh_degree
+        self.ref = Frame(scene, cam, self.o, mode=64, sh_degree=sh_degree)
+        self.valid = self.ref.valid
+        npx = cam.width * cam.height
+        self.off = np.zeros(npx + 1, np.int64)
+        n = lib().or_contrib_lists(C.byref(self.cc), C.byref(self.o), _ptr(self.ref.ranges), _ptr(self.ref.vals),
+                                   _ptr(self.ref.rec32), _ptr(self.ref.rec64), _ptr(self.off), None, None, 0)
+        self.gid = np.zeros(max(n, 1), np.int32)
+        self.aclamp = np.zeros(max(n, 1), np.uint8)
+        lib().or_contrib_lists(C.byref(self.cc), C.byref(self.o), _ptr(self.ref.ranges), _ptr(self.ref.vals),
+                               _ptr(self.ref.rec32), _ptr(self.ref.rec64), _ptr(self.off), _ptr(self.gid),
+                               _ptr(self.aclamp), n)
+        self.n_contrib = int(n)
+        self.p0 = Params64(scene)
+        self.flags = np.zeros(scene.P, np.int32)
+        a = self.p0.arrays()
+        lib().or_grad_flags(scene.P, *(_ptr(x) for x in a), sh_degree, int(self.p0.activated), C.byref(self.cc),
+                            C.byref(self.o), _ptr(self.valid), _ptr(self.flags))
+
+    def forward(self, p: Params64):
+        H, W = self.cam.height, self.cam.width
+        rgb = np.zeros((3, H, W), np.float64)
+        T = np.zeros((H, W), np.float64)
+        lib().or_forward_fixed(p.P, *(_ptr(x) for x in p.arrays()), self.sh_degree, int(p.activated),
+                               C.byref(self.cc), C.byref(self.o), _ptr(self.valid), _ptr(self.flags), _ptr(self.off),
+                               _ptr(self.gid), _ptr(self.aclamp), _ptr(rgb), _ptr(T))
+        return rgb, T
+
+    def backward(self, p: Params64, dimg):
+        dimg = np.ascontiguousarray(dimg, np.float64)
+        g = [np.zeros_like(x) for x in p.arrays()]
+        d2 = np.zeros((p.P, 9), np.float64)
+        lib().or_backward_fixed(p.P, *(_ptr(x) for x in p.arrays()), self.sh_degree, int(p.activated),
+                                C.byref(self.cc), C.byref(self.o), _ptr(self.valid), _ptr(self.flags),
+                                _ptr(self.off), _ptr(self.gid), _ptr(self.aclamp), _ptr(dimg),
+                                *(_ptr(x) for x in g), _ptr(d2))
+        return dict(means=g[0], scales=g[1], quats=g[2], opacity=g[3], sh=g[4], d2=d2)
