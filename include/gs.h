@@ -171,6 +171,31 @@ gs_status gs_render(gs_frame *frame, const gs_scene *scene, const gs_camera *cam
                     const gs_render_opts *opts, float *rgb_dev, float *T_dev, uint32_t *last_dev,
                     gs_stream stream);
 
+/* Gradients w.r.t. the parameters as given to gs_scene_create / gs_scene_update (log-scales
+   and logits when the scene is not activated).  Device arrays owned by the caller. */
+typedef struct {
+    float *means;    /* [P,3] */
+    float *scales;   /* [P,3] */
+    float *quats;    /* [P,4] (w.r.t. the unnormalised quaternion) */
+    float *opacity;  /* [P]   */
+    float *sh;       /* [P,16,3] */
+} gs_gaussian_grads;
+
+/* Backward of the last gs_render on this frame (the paper claims a differentiable rasterizer,
+   abstract; no backward is described, so this is the exact derivative of the forward with its
+   decisions held fixed: contributing entries, early stop, alpha / colour / Jacobian clamps).
+   dL_drgb_dev [3,H,W] is the loss gradient of the rendered image; T_dev and last_dev are the
+   transmittance and last-contributor outputs of that render (required).  The scene must be the
+   one rendered, unchanged since.  Per tile, pixels walk their lists back to front recovering T
+   by division; per-Gaussian sums are warp-reduced, accumulated per CTA in shared memory and
+   added to a frame-owned buffer; a per-Gaussian kernel then applies the chain rule through the
+   projection, covariance, quaternion, activations and SH.  accumulate = 0 overwrites `grads`,
+   1 adds to them.  Errors: GS_ERR_INVALID_ARG (no render on the frame, NULL pointers, scene
+   size mismatch). */
+gs_status gs_render_backward(gs_frame *frame, const gs_scene *scene, const float *dL_drgb_dev,
+                             const float *T_dev, const uint32_t *last_dev, const gs_gaussian_grads *grads,
+                             int32_t accumulate, gs_stream stream);
+
 /* Enables (1) or disables (0) CUDA-graph replay of gs_render on this frame. */
 gs_status gs_frame_use_graph(gs_frame *frame, int32_t enable);
 

@@ -185,6 +185,22 @@ class Frame:
         _check(lib().gs_render(self.h, scene.h, C.byref(gs_camera_from(cam)), C.byref(o), _ptr(rgb), _ptr(T),
                                _ptr(last), _stream(stream)))
 
+    def gs_render_backward(self, scene: Scene, dL_drgb, T, last, grads=None, accumulate=False, stream=None):
+        """Gradients of the last render w.r.t. the scene parameters (dict of tensors)."""
+        import torch
+        P = scene.P
+        if grads is None:
+            dev = dL_drgb.device
+            grads = dict(means=torch.empty((P, 3), device=dev), scales=torch.empty((P, 3), device=dev),
+                         quats=torch.empty((P, 4), device=dev), opacity=torch.empty((P,), device=dev),
+                         sh=torch.empty((P, 16, 3), device=dev))
+        g = _native.gs_gaussian_grads()
+        g.means, g.scales, g.quats, g.opacity, g.sh = (_ptr(grads[k]) for k in
+                                                       ("means", "scales", "quats", "opacity", "sh"))
+        _check(lib().gs_render_backward(self.h, scene.h, _ptr(dL_drgb), _ptr(T), _ptr(last), C.byref(g),
+                                        int(bool(accumulate)), _stream(stream)))
+        return grads
+
     def gs_frame_use_graph(self, enable: bool):
         _check(lib().gs_frame_use_graph(self.h, int(bool(enable))))
 

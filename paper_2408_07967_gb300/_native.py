@@ -34,6 +34,11 @@ class gs_frame_stats(C.Structure):
                 ("contributions", C.c_int64), ("kernels", C.c_int32), ("pad", C.c_int32)]
 
 
+class gs_gaussian_grads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacity", C.c_void_p),
+                ("sh", C.c_void_p)]
+
+
 class gs_tuning(C.Structure):
     _fields_ = [("blend_variant", C.c_int32), ("sort_mode", C.c_int32), ("reserved", C.c_int32 * 6)]
 
@@ -62,6 +67,7 @@ PROTOTYPES = {
     "gs_blend": (_st, [_vp, C.POINTER(gs_render_opts), _vp, _vp, _vp, _vp]),
     "gs_render": (_st, [_vp, _vp, C.POINTER(gs_camera), C.POINTER(gs_render_opts), _vp, _vp, _vp, _vp]),
     "gs_frame_use_graph": (_st, [_vp, C.c_int32]),
+    "gs_render_backward": (_st, [_vp, _vp, _vp, _vp, _vp, C.POINTER(gs_gaussian_grads), C.c_int32, _vp]),
     "gs_frame_enable_timing": (_st, [_vp, C.c_int32]),
     "gs_frame_set_tuning": (_st, [_vp, C.POINTER(gs_tuning)]),
     "gs_frame_get_tuning": (_st, [_vp, C.POINTER(gs_tuning)]),

@@ -132,6 +132,11 @@ struct gs_frame {
     void *out_mem = nullptr;
     gs_tuning tuning{1, 1, {0, 0, 0, 0, 0, 0}};
     int counting = 0;
+    // camera and options of the last preprocess (used by the backward)
+    Cam cam{};
+    Opts opt{};
+    const gs_scene *scene_used = nullptr;
+    float *grad2d = nullptr;         // allocated on the first backward
 };
 
 extern "C" {
@@ -345,6 +350,7 @@ gs_status gs_frame_destroy(gs_frame *f) {
     for (int i = 0; i < 5; ++i)
         if (f->ev[i]) cudaEventDestroy(f->ev[i]);
     cudaFree(f->out_mem);
+    cudaFree(f->grad2d);
     cudaFree(f->mem);
     delete f;
     return GS_OK;
@@ -482,6 +488,9 @@ gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, co
     f->tiles_x = c.tiles_x;
     f->tiles_y = c.tiles_y;
     f->sorted_buf = 0;
+    f->cam = c;
+    f->opt = a.opt;
+    f->scene_used = s;
     return GS_OK;
 }
 
@@ -831,5 +840,53 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
         }
     }
     if (out) *out = f->tuning;
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------------------------------ backward
+extern "C" gs_status gs_render_backward(gs_frame *f, const gs_scene *s, const float *dL_drgb, const float *T,
+                                        const uint32_t *last, const gs_gaussian_grads *g, int32_t accumulate,
+                                        gs_stream stream) {
+    if (!f || !s || !dL_drgb || !T || !last || !g) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    if (!g->means || !g->scales || !g->quats || !g->opacity || !g->sh)
+        return fail(GS_ERR_INVALID_ARG, "a gradient array is NULL");
+    if (f->W <= 0 || f->scene_used != s) return fail(GS_ERR_INVALID_ARG, "no render of this scene on the frame");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!f->grad2d) {
+        GS_CUDA(cudaSetDevice(f->ctx->device));
+        GS_CUDA(cudaMalloc(&f->grad2d, sizeof(float) * (size_t)grad2d_floats() * (size_t)f->max_g));
+    }
+    GS_CUDA(cudaMemsetAsync(f->grad2d, 0, sizeof(float) * (size_t)grad2d_floats() * (size_t)s->P, st));
+    BwdArgs a;
+    a.recs = f->recs;
+    a.vals = f->vals[f->sorted_buf];
+    a.starts = f->starts;
+    a.n_dev = &f->ctr->n_pairs;
+    a.cap = f->max_pairs;
+    a.opt = f->opt;
+    a.cam = f->cam;
+    a.scene.pos_opa = s->pos_opa;
+    a.scene.scale = s->scale;
+    a.scene.quat = s->quat;
+    a.scene.sh = s->sh;
+    a.scene.P = s->P;
+    a.scene.sh_degree = s->sh_degree;
+    a.scene.activated = s->activated;
+    a.W = f->W;
+    a.H = f->H;
+    a.tiles_x = f->tiles_x;
+    a.tiles_y = f->tiles_y;
+    a.dL_drgb = dL_drgb;
+    a.T_final = T;
+    a.last = last;
+    a.grad2d = f->grad2d;
+    a.g_means = g->means;
+    a.g_scales = g->scales;
+    a.g_quats = g->quats;
+    a.g_opacity = g->opacity;
+    a.g_sh = g->sh;
+    a.accumulate = accumulate ? 1 : 0;
+    launch_backward(a, st);
+    GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

@@ -1,0 +1,418 @@
+// gs_backward.cu -- gradient of the forward rasterizer (the paper claims a differentiable
+// rasterizer but describes no backward pass; this is the exact derivative of the forward with its
+// decisions held: which entries contribute to a pixel, where the walk stops, whether alpha or a
+// colour channel or the Jacobian's x/z, y/z were clamped).
+//
+// k_blend_backward: per 16x16 tile, every pixel walks its list back to front from its last
+//   contributor, recovering the transmittance before each contribution by division
+//   (T_before = T_after / (1 - alpha)) from the final T stored by the forward.  With g = dL/dC:
+//     dL/drgb   += alpha T g
+//     dL/dalpha  = T (g . rgb) - S / (1 - alpha),   S = g . (sum of later contributions + T_final bg)
+//     alpha = alpha0 e^(-q/2):  dL/dalpha0 = dL/dalpha e^(-q/2),  dL/dq = -alpha/2 dL/dalpha
+//     q = a dx^2 + 2 b dx dy + c dy^2 with dx = px - u, dy = py - v.
+//   The nine per-Gaussian sums (u, v, a, b, c, alpha0, r, g, b) of a warp are reduced with
+//   shuffles, accumulated over the CTA in shared memory, then added to global memory once per
+//   CTA and entry (warp-level reduction before atomics, the idea DISTWAR applies to 3DGS).
+// k_gauss_backward: per Gaussian, the chain from those 2D gradients to the parameters: colour ->
+//   SH coefficients and the view direction; alpha0 -> opacity (logit); conic -> Sigma'
+//   (dQ = -Q dSigma' Q) -> Sigma and J W -> scales, quaternion and the camera-space mean; (u, v)
+//   -> camera-space mean -> mean.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+constexpr int kBwdThreads = 256;
+constexpr int kG2 = 10;   // floats per Gaussian in the 2D-gradient buffer
+
+__device__ __forceinline__ float ex2_approx_b(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__global__ void __launch_bounds__(kBwdThreads) k_blend_backward(const __grid_constant__ BwdArgs A) {
+    __shared__ float4 s_r0[kBwdThreads];
+    __shared__ float4 s_r1[kBwdThreads];
+    __shared__ float2 s_r2[kBwdThreads];
+    __shared__ unsigned s_gid[kBwdThreads];
+    __shared__ float s_acc[kBwdThreads][9];
+    __shared__ unsigned s_maxlast;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned FULL = 0xffffffffu;
+    const int tile = blockIdx.x;
+    const int tx = tile % A.tiles_x, ty = tile / A.tiles_x;
+    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
+    const bool inside = px < A.W && py < A.H;
+    long long n = (long long)*A.n_dev;
+    if (n > A.cap) n = A.cap;
+    const long long start = min((long long)A.starts[tile], n);
+    const long long o = (long long)py * A.W + px;
+    const long long npx = (long long)A.W * A.H;
+    unsigned my_last = inside ? A.last[o] : 0u;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f, T = 1.f;
+    if (inside) {
+        g0 = A.dL_drgb[o];
+        g1 = A.dL_drgb[npx + o];
+        g2 = A.dL_drgb[2 * npx + o];
+        T = A.T_final[o];
+    }
+    float Sg = T * (g0 * A.opt.bg[0] + g1 * A.opt.bg[1] + g2 * A.opt.bg[2]);
+    if (tid == 0) s_maxlast = 0;
+    __syncthreads();
+    if (my_last) atomicMax(&s_maxlast, my_last);
+    __syncthreads();
+    const int max_last = (int)s_maxlast;
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float HALF_LOG2E = 0.72134752044448170f;
+    const float amax = A.opt.alpha_max;
+
+    for (int hi = max_last; hi > 0; hi -= kBwdThreads) {
+        const int lo = max(0, hi - kBwdThreads);
+        __syncthreads();
+        const int e = lo + tid;
+        if (e < hi) {
+            const unsigned g = A.vals[start + e];
+            const Rec r = A.recs[g];
+            s_r0[tid] = r.r0;
+            s_r1[tid] = r.r1;
+            s_r2[tid] = make_float2(r.r2.x, r.r2.y);
+            s_gid[tid] = g;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s_acc[tid][k] = 0.0f;
+        __syncthreads();
+        for (int j = hi - 1; j >= lo; --j) {
+            const int jj = j - lo;
+            const float4 r0 = s_r0[jj];
+            const float4 r1 = s_r1[jj];
+            const float dx = fsub(fpx, r0.x), dy = fsub(fpy, r0.y);
+            const float q = pixel_q(r0.z, r0.w, r1.x, dx, dy);
+            const bool pass = (unsigned)j < my_last && q <= r1.y;
+            if (!__any_sync(FULL, pass)) continue;
+            float d[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) d[k] = 0.0f;
+            if (pass) {
+                const float2 r2 = s_r2[jj];
+                const float e2 = ex2_approx_b(fmaf(q, -HALF_LOG2E, r1.z));   // alpha0 e^(-q/2), as forward
+                const float al = fminf(amax, e2);
+                const float Tb = T / (1.0f - al);
+                const float gc = g0 * r1.w + g1 * r2.x + g2 * r2.y;
+                const float w = al * Tb;
+                d[6] = w * g0;
+                d[7] = w * g1;
+                d[8] = w * g2;
+                const float dal = Tb * gc - Sg / (1.0f - al);
+                Sg = fmaf(gc, w, Sg);
+                T = Tb;
+                if (e2 <= amax) {
+                    const float a0 = ex2_approx_b(r1.z);
+                    d[5] = dal * (al / a0);
+                    const float dq = -0.5f * al * dal;
+                    const float a = r0.z, b2 = r0.w, c = r1.x;
+                    d[0] = -dq * (2.0f * a * dx + b2 * dy);
+                    d[1] = -dq * (b2 * dx + 2.0f * c * dy);
+                    d[2] = dq * dx * dx;
+                    d[3] = dq * 2.0f * dx * dy;
+                    d[4] = dq * dy * dy;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                float v = d[k];
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(FULL, v, s);
+                d[k] = v;
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    if (d[k] != 0.0f) atomicAdd(&s_acc[jj][k], d[k]);
+            }
+        }
+        __syncthreads();
+        if (lo + tid < hi) {
+            float *dst = A.grad2d + (long long)s_gid[tid] * kG2;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float v = s_acc[tid][k];
+                if (v != 0.0f) atomicAdd(dst + k, v);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------ per Gaussian
+__device__ __forceinline__ void sh_basis_and_grad(float x, float y, float z, float Y[16], float dY[16][3]) {
+    const float K0 = 0.28209479177387814f, K1 = 0.48860251190291992f;
+    const float K2a = 1.0925484305920792f, K2b = 0.31539156525252005f, K2c = 0.54627421529603959f;
+    const float K3a = 0.59004358992664352f, K3b = 2.8906114426405538f, K3c = 0.45704579946446572f;
+    const float K3d = 0.3731763325901154f, K3e = 1.4453057213202769f;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = K0;
+    Y[1] = -K1 * y;
+    Y[2] = K1 * z;
+    Y[3] = -K1 * x;
+    Y[4] = K2a * x * y;
+    Y[5] = -K2a * y * z;
+    Y[6] = K2b * (2.0f * zz - xx - yy);
+    Y[7] = -K2a * x * z;
+    Y[8] = K2c * (xx - yy);
+    Y[9] = -K3a * y * (3.0f * xx - yy);
+    Y[10] = K3b * x * y * z;
+    Y[11] = -K3c * y * (4.0f * zz - xx - yy);
+    Y[12] = K3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -K3c * x * (4.0f * zz - xx - yy);
+    Y[14] = K3e * z * (xx - yy);
+    Y[15] = -K3a * x * (xx - 3.0f * yy);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dY[i][0] = dY[i][1] = dY[i][2] = 0.0f;
+    dY[1][1] = -K1;
+    dY[2][2] = K1;
+    dY[3][0] = -K1;
+    dY[4][0] = K2a * y; dY[4][1] = K2a * x;
+    dY[5][1] = -K2a * z; dY[5][2] = -K2a * y;
+    dY[6][0] = -2.0f * K2b * x; dY[6][1] = -2.0f * K2b * y; dY[6][2] = 4.0f * K2b * z;
+    dY[7][0] = -K2a * z; dY[7][2] = -K2a * x;
+    dY[8][0] = 2.0f * K2c * x; dY[8][1] = -2.0f * K2c * y;
+    dY[9][0] = -6.0f * K3a * x * y; dY[9][1] = -K3a * (3.0f * xx - 3.0f * yy);
+    dY[10][0] = K3b * y * z; dY[10][1] = K3b * x * z; dY[10][2] = K3b * x * y;
+    dY[11][0] = 2.0f * K3c * x * y; dY[11][1] = -K3c * (4.0f * zz - xx - 3.0f * yy); dY[11][2] = -8.0f * K3c * y * z;
+    dY[12][0] = -6.0f * K3d * x * z; dY[12][1] = -6.0f * K3d * y * z; dY[12][2] = K3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+    dY[13][0] = -K3c * (4.0f * zz - 3.0f * xx - yy); dY[13][1] = 2.0f * K3c * x * y; dY[13][2] = -8.0f * K3c * x * z;
+    dY[14][0] = 2.0f * K3e * x * z; dY[14][1] = -2.0f * K3e * y * z; dY[14][2] = K3e * (xx - yy);
+    dY[15][0] = -K3a * (3.0f * xx - 3.0f * yy); dY[15][1] = 6.0f * K3a * x * y;
+}
+
+__global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ BwdArgs A) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= A.scene.P) return;
+    const float *d2 = A.grad2d + gid * kG2;
+    float D[9];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        D[k] = d2[k];
+        any |= D[k] != 0.0f;
+    }
+    float gm[3] = {0, 0, 0}, gsc[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gop = 0.0f;
+    float gsh[48];
+#pragma unroll
+    for (int i = 0; i < 48; ++i) gsh[i] = 0.0f;
+    if (any) {
+        const Cam &cam = A.cam;
+        const SceneView &S = A.scene;
+        const float4 po = S.pos_opa[gid];
+        const float *Rc = cam.R;
+        float p[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) p[i] = Rc[3 * i] * po.x + Rc[3 * i + 1] * po.y + Rc[3 * i + 2] * po.z + cam.t[i];
+        const float alpha0 = S.activated ? po.w : 1.0f / (1.0f + __expf(-po.w));
+        const float4 sc4 = S.scale[gid];
+        float s[3] = {sc4.x, sc4.y, sc4.z};
+        if (!S.activated) {
+            s[0] = __expf(s[0]);
+            s[1] = __expf(s[1]);
+            s[2] = __expf(s[2]);
+        }
+        const float4 q4 = S.quat[gid];
+        const float qlen = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+        const float w = q4.x / qlen, x = q4.y / qlen, y = q4.z / qlen, z = q4.w / qlen;
+        float R[9];
+        R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+        R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+        R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+        float Sg[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                Sg[3 * i + j] = R[3 * i] * s[0] * s[0] * R[3 * j] + R[3 * i + 1] * s[1] * s[1] * R[3 * j + 1] +
+                                R[3 * i + 2] * s[2] * s[2] * R[3 * j + 2];
+        const float fx = cam.fx, fy = cam.fy, pz = p[2];
+        float txz = p[0] / pz, tyz = p[1] / pz;
+        bool clx = false, cly = false;
+        if (A.opt.clamp_fov) {
+            if (txz < -cam.limx) { txz = -cam.limx; clx = true; }
+            if (txz > cam.limx) { txz = cam.limx; clx = true; }
+            if (tyz < -cam.limy) { tyz = -cam.limy; cly = true; }
+            if (tyz > cam.limy) { tyz = cam.limy; cly = true; }
+        }
+        const float J00 = fx / pz, J02 = -fx * txz / pz, J11 = fy / pz, J12 = -fy * tyz / pz;
+        float M[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            M[k] = J00 * Rc[k] + J02 * Rc[6 + k];
+            M[3 + k] = J11 * Rc[3 + k] + J12 * Rc[6 + k];
+        }
+        float S2[4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) acc += M[3 * i + k] * Sg[3 * k + m] * M[3 * l + m];
+                S2[2 * i + l] = acc;
+            }
+        S2[0] += A.opt.dilation;
+        S2[3] += A.opt.dilation;
+        const float det = S2[0] * S2[3] - S2[1] * S2[2];
+        const float Q[4] = {S2[3] / det, -S2[1] / det, -S2[2] / det, S2[0] / det};
+
+        // colour -> SH and direction
+        float dvec[3] = {po.x - cam.campos[0], po.y - cam.campos[1], po.z - cam.campos[2]};
+        const float dlen = sqrtf(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
+        const float dir[3] = {dvec[0] / dlen, dvec[1] / dlen, dvec[2] / dlen};
+        float Y[16], dY[16][3];
+        sh_basis_and_grad(dir[0], dir[1], dir[2], Y, dY);
+        const int ncoef = (S.sh_degree + 1) * (S.sh_degree + 1);
+        float f[48];
+#pragma unroll
+        for (int k = 0; k < kShPlanes; ++k) {
+            const float4 v4 = S.sh[(long long)k * S.P + gid];
+            f[4 * k] = v4.x;
+            f[4 * k + 1] = v4.y;
+            f[4 * k + 2] = v4.z;
+            f[4 * k + 3] = v4.w;
+        }
+        float ddir[3] = {0, 0, 0};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc += (i < ncoef ? Y[i] : 0.f) * f[3 * i + ch];
+            if (acc + 0.5f < 0.0f) continue;   // channel clamped at 0
+            const float dr = D[6 + ch];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (i < ncoef) {
+                    gsh[3 * i + ch] = Y[i] * dr;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) ddir[a] += dr * f[3 * i + ch] * dY[i][a];
+                }
+            }
+        }
+        const float dd = ddir[0] * dir[0] + ddir[1] * dir[1] + ddir[2] * dir[2];
+        float dmean[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dmean[a] = (ddir[a] - dir[a] * dd) / dlen;
+        // opacity
+        gop = S.activated ? D[5] : D[5] * alpha0 * (1.0f - alpha0);
+        // conic -> Sigma'
+        const float GQ[4] = {D[2], 0.5f * D[3], 0.5f * D[3], D[4]};
+        float T1[4], GS2[4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) T1[2 * i + j] = Q[2 * i] * GQ[j] + Q[2 * i + 1] * GQ[2 + j];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) GS2[2 * i + j] = -(T1[2 * i] * Q[j] + T1[2 * i + 1] * Q[2 + j]);
+        float GSg[9], GM[6];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float acc = 0.f;
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) acc += M[3 * a + i] * GS2[2 * a + b] * M[3 * b + j];
+                GSg[3 * i + j] = acc;
+            }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) acc += GS2[2 * a + b] * M[3 * b + m] * Sg[3 * m + k];
+                GM[3 * a + k] = 2.0f * acc;
+            }
+        float GJ[6];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) GJ[3 * a + j] = GM[3 * a] * Rc[3 * j] + GM[3 * a + 1] * Rc[3 * j + 1] +
+                                                        GM[3 * a + 2] * Rc[3 * j + 2];
+        float dp[3] = {0.f, 0.f, 0.f};
+        dp[2] += GJ[0] * (-fx / (pz * pz)) + GJ[4] * (-fy / (pz * pz));
+        if (!clx) {
+            dp[0] += GJ[2] * (-fx / (pz * pz));
+            dp[2] += GJ[2] * (2.0f * fx * p[0] / (pz * pz * pz));
+        } else {
+            dp[2] += GJ[2] * (fx * txz / (pz * pz));
+        }
+        if (!cly) {
+            dp[1] += GJ[5] * (-fy / (pz * pz));
+            dp[2] += GJ[5] * (2.0f * fy * p[1] / (pz * pz * pz));
+        } else {
+            dp[2] += GJ[5] * (fy * tyz / (pz * pz));
+        }
+        dp[0] += D[0] * fx / pz;
+        dp[1] += D[1] * fy / pz;
+        dp[2] += D[0] * (-fx * p[0] / (pz * pz)) + D[1] * (-fy * p[1] / (pz * pz));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gm[a] = dmean[a] + Rc[a] * dp[0] + Rc[3 + a] * dp[1] + Rc[6 + a] * dp[2];
+        // Sigma = R diag(s^2) R^T
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) acc += R[3 * i + k] * GSg[3 * i + j] * R[3 * j + k];
+            const float ds = 2.0f * s[k] * acc;
+            gsc[k] = S.activated ? ds : ds * s[k];
+        }
+        float GR[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                GR[3 * i + k] = 2.0f * (GSg[3 * i] * R[k] + GSg[3 * i + 1] * R[3 + k] + GSg[3 * i + 2] * R[6 + k]) *
+                                s[k] * s[k];
+        float dq[4];
+        dq[0] = GR[1] * (-2 * z) + GR[2] * (2 * y) + GR[3] * (2 * z) + GR[5] * (-2 * x) + GR[6] * (-2 * y) + GR[7] * (2 * x);
+        dq[1] = GR[1] * (2 * y) + GR[2] * (2 * z) + GR[3] * (2 * y) + GR[4] * (-4 * x) + GR[5] * (-2 * w) +
+                GR[6] * (2 * z) + GR[7] * (2 * w) + GR[8] * (-4 * x);
+        dq[2] = GR[0] * (-4 * y) + GR[1] * (2 * x) + GR[2] * (2 * w) + GR[3] * (2 * x) + GR[5] * (2 * z) +
+                GR[6] * (-2 * w) + GR[7] * (2 * z) + GR[8] * (-4 * y);
+        dq[3] = GR[0] * (-4 * z) + GR[1] * (-2 * w) + GR[2] * (2 * x) + GR[3] * (2 * w) + GR[4] * (-4 * z) +
+                GR[5] * (2 * y) + GR[6] * (2 * x) + GR[7] * (2 * y);
+        const float proj = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
+        gq[0] = (dq[0] - w * proj) / qlen;
+        gq[1] = (dq[1] - x * proj) / qlen;
+        gq[2] = (dq[2] - y * proj) / qlen;
+        gq[3] = (dq[3] - z * proj) / qlen;
+    }
+    if (!any && A.accumulate) return;
+    const bool add = A.accumulate != 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        A.g_means[3 * gid + a] = add ? A.g_means[3 * gid + a] + gm[a] : gm[a];
+        A.g_scales[3 * gid + a] = add ? A.g_scales[3 * gid + a] + gsc[a] : gsc[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) A.g_quats[4 * gid + a] = add ? A.g_quats[4 * gid + a] + gq[a] : gq[a];
+    A.g_opacity[gid] = add ? A.g_opacity[gid] + gop : gop;
+#pragma unroll
+    for (int i = 0; i < 48; ++i) A.g_sh[48 * gid + i] = add ? A.g_sh[48 * gid + i] + gsh[i] : gsh[i];
+}
+
+void launch_backward(const BwdArgs &a, cudaStream_t s) {
+    const int ntiles = a.tiles_x * a.tiles_y;
+    if (ntiles > 0) k_blend_backward<<<ntiles, kBwdThreads, 0, s>>>(a);
+    const long long P = a.scene.P;
+    if (P > 0) k_gauss_backward<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(a);
+}
+
+int grad2d_floats() { return kG2; }
+
+}  // namespace gs

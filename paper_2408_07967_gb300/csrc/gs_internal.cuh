@@ -275,4 +275,24 @@ struct BlendArgs {
 void launch_blend(const BlendArgs &a, cudaStream_t s);
 int blend_variant_count();
 
+struct BwdArgs {
+    const Rec *recs;
+    const unsigned *vals;
+    const unsigned *starts;
+    const unsigned long long *n_dev;
+    long long cap;
+    Opts opt;
+    Cam cam;
+    SceneView scene;
+    int W, H, tiles_x, tiles_y;
+    const float *dL_drgb;            // [3,H,W]
+    const float *T_final;            // [H,W]
+    const unsigned *last;            // [H,W]
+    float *grad2d;                   // [P][10]: u, v, a, b, c, alpha0, r, g, b, -
+    float *g_means, *g_scales, *g_quats, *g_opacity, *g_sh;
+    int accumulate;
+};
+void launch_backward(const BwdArgs &a, cudaStream_t s);
+int grad2d_floats();
+
 }  // namespace gs
