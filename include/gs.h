@@ -196,6 +196,18 @@ gs_status gs_render_backward(gs_frame *frame, const gs_scene *scene, const float
                              const float *T_dev, const uint32_t *last_dev, const gs_gaussian_grads *grads,
                              int32_t accumulate, gs_stream stream);
 
+/* Renders n (1..16) requests in one pass of every stage: each request r has its own scene
+   (any of the device-resident scenes), camera, image size and options (opts: array of n, or
+   NULL for defaults) and writes rgb[r] [3,H_r,W_r] (device), T[r] and last[r] (arrays of n
+   device pointers, or NULL).  Request r's Gaussians occupy records rec0_r + id, its tiles the
+   global tile ids tile0_r .. in the (tile, depth) keys, so the preprocess, the sort, the ranges
+   and the blend each run once over the whole batch with per-request tile ranges.  Each request's
+   result is bit-identical to rendering it alone.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CAPACITY
+   (more Gaussians or tiles than the frame holds). */
+gs_status gs_render_batch(gs_frame *frame, int32_t n, const gs_scene *const *scenes, const gs_camera *cams,
+                          const gs_render_opts *opts, float *const *rgb_dev, float *const *T_dev,
+                          uint32_t *const *last_dev, gs_stream stream);
+
 /* Enables (1) or disables (0) CUDA-graph replay of gs_render on this frame. */
 gs_status gs_frame_use_graph(gs_frame *frame, int32_t enable);
 
@@ -275,6 +287,65 @@ gs_status gs_frame_ranges(gs_frame *frame, uint32_t *starts_dev, int64_t cap, gs
 gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys_dev, uint32_t *vals_dev, uint64_t *keys_tmp_dev,
                         uint32_t *vals_tmp_dev, int64_t n, int32_t end_bit, int32_t *in_tmp,
                         gs_stream stream);
+
+/* ------------------------------------------------------------------------------------------
+   Serving: a continuous-batching request loop over device-resident scenes (a worker thread
+   inside the library).  Requests -- a scene, a camera of any size up to the configured maximum,
+   options and a HOST output buffer -- are queued by gs_server_submit.  Up to `slots` batches are
+   in flight at once, each on its own stream with its own frame and output pool, so batches
+   overlap on the device.  When a slot is free the oldest waiting requests (at most max_batch,
+   at most max_gaussians Gaussians together) are admitted by pair-buffer memory: one count pass
+   (geometry + exact pair counts) gives each request's pairs, and the oldest requests whose
+   pairs fit pair_capacity run as one batch through gs_render_batch's single pass per stage with
+   per-request tile ranges; the rest wait for the next free slot.  Images are copied to the
+   callers' host buffers (asynchronous when page-locked).  Every request's image is
+   bit-identical to rendering it alone.  plain = 1 is the baseline loop: one request at a time,
+   synchronously, no count pass.  The paper describes single frames only; batching requests is
+   this library's extension (Section 5.3.1's static allocation carries over: all buffers are
+   allocated at creation). */
+typedef struct gs_server gs_server;
+typedef struct {
+    int32_t slots;            /* batches in flight at once, 1..8 (plain: 1) */
+    int32_t max_batch;        /* requests per batch, 1..16 (plain: 1) */
+    int64_t pair_capacity;    /* pairs per batch (pair buffers of each slot), < 2^30 */
+    int64_t max_gaussians;    /* Gaussians per batch, summed over its requests */
+    int32_t max_width, max_height;   /* largest request image */
+    int32_t sort_mode;        /* gs_tuning.sort_mode of the slots' frames, -1 for the default */
+    int32_t blend_variant;    /* gs_tuning.blend_variant, -1 for the default */
+    int32_t plain;            /* 1: one request at a time (the baseline loop) */
+    int32_t reserved;
+} gs_server_cfg;
+typedef struct {
+    int32_t status;           /* GS_OK, GS_ERR_PAIR_OVERFLOW (alone over the pair capacity), ... */
+    int32_t batch_size;       /* requests in the batch it ran in */
+    double arrival_s;         /* gs_clock_s() time of arrival (as submitted) */
+    double admit_s;           /* time the batch was formed */
+    double done_s;            /* time its image was in the host buffer */
+    int64_t pairs;            /* its Gaussian/tile pairs */
+} gs_request_stats;
+typedef struct {
+    int64_t completed, batches, batched_requests, pending;
+} gs_server_stats;
+
+/* Monotonic clock of the server, seconds (for arrival times). */
+double gs_clock_s(void);
+/* Defaults: 3 slots, batches of up to 8, 2^26 pairs and 2^26 Gaussians per batch, 3840x2160. */
+gs_status gs_default_server_cfg(gs_server_cfg *cfg);
+/* Allocates every slot's frame, stream and output pool and starts the worker.  Errors:
+   GS_ERR_INVALID_ARG, GS_ERR_OOM. */
+gs_status gs_server_create(gs_context *ctx, const gs_server_cfg *cfg, gs_server **out);
+/* Stops the worker after the batches in flight; unfinished queued requests are dropped. */
+gs_status gs_server_destroy(gs_server *server);
+/* Queues a request; rgb_host receives [3,H,W] floats and must stay valid until the request is
+   waited for.  arrival_s <= 0 means now.  The scene must stay alive and unchanged until then.
+   Returns at once with *ticket.  Errors: GS_ERR_INVALID_ARG (image larger than the maximum),
+   GS_ERR_CAPACITY (scene larger than a batch). */
+gs_status gs_server_submit(gs_server *server, const gs_scene *scene, const gs_camera *cam,
+                           const gs_render_opts *opts, float *rgb_host, double arrival_s, uint64_t *ticket);
+/* Waits for a request (timeout_ms < 0: no limit) and returns its status; GS_ERR_DEVICE_TIMEOUT
+   when the limit passes first (the request stays queued).  *out (nullable) gets its times. */
+gs_status gs_server_wait(gs_server *server, uint64_t ticket, int32_t timeout_ms, gs_request_stats *out);
+gs_status gs_server_get_stats(gs_server *server, gs_server_stats *out);
 
 /* gs_sort_pairs without any allocation.  The paper has no counterpart: this entry point exists
    for callers that must not allocate device memory -- code handed its buffers by a host

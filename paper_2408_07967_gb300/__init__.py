@@ -14,7 +14,7 @@ import ctypes as C
 
 from . import _native
 
-__all__ = ["GsError", "Context", "Scene", "Frame", "gs_camera_from", "gs_opts", "gs_sort_pairs", "lib"]
+__all__ = ["GsError", "Context", "Scene", "Frame", "Server", "gs_camera_from", "gs_opts", "gs_sort_pairs", "lib"]
 
 GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_PAIR_OVERFLOW", -4: "GS_ERR_CUDA",
@@ -201,6 +201,28 @@ class Frame:
                                         int(bool(accumulate)), _stream(stream)))
         return grads
 
+    def gs_render_batch(self, scenes, cams, opts=None, stream=None, want_T=False, want_last=False):
+        """Render several requests (scenes and cameras of any sizes) in one pass of every stage.
+        Returns a list of (rgb, T, last) tensors."""
+        import torch
+        n = len(cams)
+        sc = (C.c_void_p * n)(*[s.h.value for s in scenes])
+        cm = (_native.gs_camera * n)(*[gs_camera_from(c) for c in cams])
+        op = None
+        if opts is not None:
+            op = (_native.gs_render_opts * n)(*opts)
+        outs = []
+        for c in cams:
+            H, W = int(c.height), int(c.width)
+            outs.append((torch.empty((3, H, W), device="cuda"),
+                         torch.empty((H, W), device="cuda") if want_T else None,
+                         torch.empty((H, W), dtype=torch.int32, device="cuda") if want_last else None))
+        rgb = (C.c_void_p * n)(*[o[0].data_ptr() for o in outs])
+        T = (C.c_void_p * n)(*[o[1].data_ptr() for o in outs]) if want_T else None
+        last = (C.c_void_p * n)(*[o[2].data_ptr() for o in outs]) if want_last else None
+        _check(lib().gs_render_batch(self.h, n, sc, cm, op, rgb, T, last, _stream(stream)))
+        return outs
+
     def gs_frame_use_graph(self, enable: bool):
         _check(lib().gs_frame_use_graph(self.h, int(bool(enable))))
 
@@ -285,6 +307,61 @@ class Frame:
     def close(self):
         if getattr(self, "h", None):
             lib().gs_frame_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """gs_server: continuous-batching request loop (worker thread inside the library)."""
+
+    def __init__(self, ctx: Context, plain=False, **cfg):
+        c = _native.gs_server_cfg()
+        _check(lib().gs_default_server_cfg(C.byref(c)))
+        for k, v in cfg.items():
+            setattr(c, k, int(v))
+        c.plain = int(bool(plain))
+        h = C.c_void_p()
+        _check(lib().gs_server_create(ctx.h, C.byref(c), C.byref(h)))
+        self.h = h
+        self.ctx = ctx
+        self.cfg = c
+        self._bufs = {}
+
+    @staticmethod
+    def clock() -> float:
+        return float(lib().gs_clock_s())
+
+    def gs_server_submit(self, scene: Scene, cam, rgb_host, opts=None, arrival_s=0.0) -> int:
+        """rgb_host: a CPU float32 tensor [3,H,W] (page-locked for asynchronous copies)."""
+        assert rgb_host.dtype.is_floating_point and not rgb_host.is_cuda and rgb_host.is_contiguous()
+        t = C.c_uint64()
+        o = opts or gs_opts()
+        _check(lib().gs_server_submit(self.h, scene.h, C.byref(gs_camera_from(cam)), C.byref(o),
+                                      C.c_void_p(rgb_host.data_ptr()), float(arrival_s), C.byref(t)))
+        self._bufs[t.value] = rgb_host
+        return t.value
+
+    def gs_server_wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        st = _native.gs_request_stats()
+        status = lib().gs_server_wait(self.h, C.c_uint64(ticket), int(timeout_ms), C.byref(st))
+        if status == -5:
+            raise GsError(status, lib().gs_last_error().decode())
+        self._bufs.pop(ticket, None)
+        return {k: getattr(st, k) for k, _ in _native.gs_request_stats._fields_}
+
+    def stats(self) -> dict:
+        st = _native.gs_server_stats()
+        _check(lib().gs_server_get_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in _native.gs_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gs_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -39,6 +39,22 @@ class gs_gaussian_grads(C.Structure):
                 ("sh", C.c_void_p)]
 
 
+class gs_server_cfg(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("pair_capacity", C.c_int64),
+                ("max_gaussians", C.c_int64), ("max_width", C.c_int32), ("max_height", C.c_int32),
+                ("sort_mode", C.c_int32), ("blend_variant", C.c_int32), ("plain", C.c_int32), ("reserved", C.c_int32)]
+
+
+class gs_request_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("batch_size", C.c_int32), ("arrival_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double), ("pairs", C.c_int64)]
+
+
+class gs_server_stats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("batches", C.c_int64), ("batched_requests", C.c_int64),
+                ("pending", C.c_int64)]
+
+
 class gs_tuning(C.Structure):
     _fields_ = [("blend_variant", C.c_int32), ("sort_mode", C.c_int32), ("reserved", C.c_int32 * 6)]
 
@@ -67,6 +83,7 @@ PROTOTYPES = {
     "gs_blend": (_st, [_vp, C.POINTER(gs_render_opts), _vp, _vp, _vp, _vp]),
     "gs_render": (_st, [_vp, _vp, C.POINTER(gs_camera), C.POINTER(gs_render_opts), _vp, _vp, _vp, _vp]),
     "gs_frame_use_graph": (_st, [_vp, C.c_int32]),
+    "gs_render_batch": (_st, [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "gs_render_backward": (_st, [_vp, _vp, _vp, _vp, _vp, C.POINTER(gs_gaussian_grads), C.c_int32, _vp]),
     "gs_frame_enable_timing": (_st, [_vp, C.c_int32]),
     "gs_frame_set_tuning": (_st, [_vp, C.POINTER(gs_tuning)]),
@@ -80,6 +97,14 @@ PROTOTYPES = {
     "gs_frame_pairs": (_st, [_vp, C.c_int32, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
     "gs_frame_ranges": (_st, [_vp, _vp, C.c_int64, _vp]),
     "gs_sort_pairs": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _vp]),
+    "gs_clock_s": (C.c_double, []),
+    "gs_default_server_cfg": (_st, [C.POINTER(gs_server_cfg)]),
+    "gs_server_create": (_st, [_vp, C.POINTER(gs_server_cfg), _pp]),
+    "gs_server_destroy": (_st, [_vp]),
+    "gs_server_submit": (_st, [_vp, _vp, C.POINTER(gs_camera), C.POINTER(gs_render_opts), _vp, C.c_double,
+                               C.POINTER(C.c_uint64)]),
+    "gs_server_wait": (_st, [_vp, C.c_uint64, C.c_int32, C.POINTER(gs_request_stats)]),
+    "gs_server_get_stats": (_st, [_vp, C.POINTER(gs_server_stats)]),
     "gs_sort_pairs_noalloc": (_st, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _vp]),
 }
 

@@ -91,8 +91,11 @@ struct gs_context {
     void *sort_mem = nullptr;
 };
 
+int context_device(const gs_context *ctx);
+
 struct gs_scene {
     gs_context *ctx = nullptr;
+    int device = 0;                  // kept here so that destruction never reads the context
     long long P = 0;
     int sh_degree = 3;
     int activated = 1;
@@ -102,6 +105,7 @@ struct gs_scene {
 
 struct gs_frame {
     gs_context *ctx = nullptr;
+    int device = 0;                  // kept here so that destruction never reads the context
     long long max_g = 0, max_pairs = 0;
     int max_w = 0, max_h = 0;
     long long max_tiles = 0, max_chunks = 0;
@@ -137,7 +141,10 @@ struct gs_frame {
     Opts opt{};
     const gs_scene *scene_used = nullptr;
     float *grad2d = nullptr;         // allocated on the first backward
+    BatchDesc batch{};               // requests of the last preprocess
 };
+
+int context_device(const gs_context *ctx) { return ctx ? ctx->device : 0; }
 
 extern "C" {
 
@@ -193,6 +200,7 @@ gs_status gs_context_destroy(gs_context *c) {
     cudaDeviceSynchronize();
     cudaFree(c->ctr);
     cudaFree(c->sort_mem);
+    cudaGetLastError();
     delete c;
     return GS_OK;
 }
@@ -216,6 +224,7 @@ gs_status gs_scene_create(gs_context *ctx, const gs_gaussians *g, gs_stream stre
     gs_scene *s = new (std::nothrow) gs_scene();
     if (!s) return fail(GS_ERR_OOM, "host allocation failed");
     s->ctx = ctx;
+    s->device = ctx->device;
     s->P = g->P;
     size_t planes = 3 + kShPlanes;
     cudaError_t e = cudaMalloc(&s->mem, planes * (size_t)g->P * sizeof(float4));
@@ -252,9 +261,10 @@ gs_status gs_scene_update(gs_scene *s, const gs_gaussians *g, gs_stream stream) 
 
 gs_status gs_scene_destroy(gs_scene *s) {
     if (!s) return GS_OK;
-    cudaSetDevice(s->ctx->device);
+    cudaSetDevice(s->device);
     cudaDeviceSynchronize();
     cudaFree(s->mem);
+    cudaGetLastError();   // leave no error behind for unrelated later calls
     delete s;
     return GS_OK;
 }
@@ -275,6 +285,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     gs_frame *f = new (std::nothrow) gs_frame();
     if (!f) return fail(GS_ERR_OOM, "host allocation failed");
     f->ctx = ctx;
+    f->device = ctx->device;
     f->max_g = max_g;
     f->max_pairs = max_pairs;
     f->max_w = max_w;
@@ -344,7 +355,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
 
 gs_status gs_frame_destroy(gs_frame *f) {
     if (!f) return GS_OK;
-    cudaSetDevice(f->ctx->device);
+    cudaSetDevice(f->device);
     cudaDeviceSynchronize();
     if (f->exec) cudaGraphExecDestroy(f->exec);
     for (int i = 0; i < 5; ++i)
@@ -352,6 +363,7 @@ gs_status gs_frame_destroy(gs_frame *f) {
     cudaFree(f->out_mem);
     cudaFree(f->grad2d);
     cudaFree(f->mem);
+    cudaGetLastError();
     delete f;
     return GS_OK;
 }
@@ -396,7 +408,7 @@ gs_status gs_frame_get_tuning(const gs_frame *f, gs_tuning *t) {
 gs_status gs_frame_enable_timing(gs_frame *f, int32_t enable) {
     if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
     if (enable && !f->ev[0]) {
-        GS_CUDA(cudaSetDevice(f->ctx->device));
+        GS_CUDA(cudaSetDevice(f->device));
         for (int i = 0; i < 5; ++i) GS_CUDA(cudaEventCreate(&f->ev[i]));
     }
     if (f->timing != (enable ? 1 : 0) && f->exec) {   // topology changes: re-instantiate the graph
@@ -417,24 +429,13 @@ gs_status gs_frame_stage_ms(gs_frame *f, float ms[4]) {
 }
 
 // ------------------------------------------------------------------------------------------ stages
-gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, const gs_render_opts *opts,
-                        gs_stream stream) {
-    if (!f || !s || !cam) return fail(GS_ERR_INVALID_ARG, "NULL frame, scene or camera");
-    if (s->P > f->max_g) return fail(GS_ERR_INVALID_ARG, "scene has %lld Gaussians, frame holds %lld", s->P, f->max_g);
-    if (cam->width <= 0 || cam->height <= 0 || cam->width > f->max_w || cam->height > f->max_h)
-        return fail(GS_ERR_INVALID_ARG, "image %dx%d outside the frame's %dx%d", cam->width, cam->height, f->max_w,
-                    f->max_h);
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------ batches
+static gs_status make_cam(const gs_camera *cam, Cam &c) {
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 || cam->height > 65535)
+        return fail(GS_ERR_INVALID_ARG, "bad image size %dx%d", cam->width, cam->height);
     if (!(cam->fx > 0.0f) || !(cam->fy > 0.0f)) return fail(GS_ERR_INVALID_ARG, "focal lengths must be positive");
-    cudaStream_t st = (cudaStream_t)stream;
-    PreprocessArgs a;
-    a.scene.pos_opa = s->pos_opa;
-    a.scene.scale = s->scale;
-    a.scene.quat = s->quat;
-    a.scene.sh = s->sh;
-    a.scene.P = s->P;
-    a.scene.sh_degree = s->sh_degree;
-    a.scene.activated = s->activated;
-    Cam &c = a.cam;
     for (int i = 0; i < 9; ++i) c.R[i] = cam->R[i];
     for (int i = 0; i < 3; ++i) c.t[i] = cam->t[i];
     c.fx = cam->fx;
@@ -453,7 +454,58 @@ gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, co
     c.limy = 1.3f * qy;
     for (int i = 0; i < 3; ++i)
         c.campos[i] = -(cam->R[i] * cam->t[0] + cam->R[3 + i] * cam->t[1] + cam->R[6 + i] * cam->t[2]);
-    a.opt = make_opts(opts);
+    return GS_OK;
+}
+
+static SceneView view_of(const gs_scene *s) {
+    SceneView v;
+    v.pos_opa = s->pos_opa;
+    v.scale = s->scale;
+    v.quat = s->quat;
+    v.sh = s->sh;
+    v.P = s->P;
+    v.sh_degree = s->sh_degree;
+    v.activated = s->activated;
+    return v;
+}
+
+// Builds the descriptor of n requests into f->batch after checking the frame's capacities.
+static gs_status make_batch(gs_frame *f, int n, const gs_scene *const *scenes, const gs_camera *cams,
+                            const gs_render_opts *opts) {
+    if (n < 1 || n > kMaxBatch) return fail(GS_ERR_INVALID_ARG, "batch of %d requests (1..%d)", n, kMaxBatch);
+    BatchDesc &B = f->batch;
+    B.n = n;
+    long long chunks = 0, recs = 0;
+    long long tiles = 0;
+    for (int r = 0; r < n; ++r) {
+        if (!scenes[r]) return fail(GS_ERR_INVALID_ARG, "scene %d is NULL", r);
+        ReqDesc &R = B.r[r];
+        gs_status st = make_cam(&cams[r], R.cam);
+        if (st) return st;
+        R.opt = make_opts(opts ? &opts[r] : nullptr);
+        R.scene = view_of(scenes[r]);
+        R.chunk0 = chunks;
+        R.rec0 = recs;
+        R.tile0 = (int)tiles;
+        R.rgb = nullptr;
+        R.T = nullptr;
+        R.last = nullptr;
+        chunks += (scenes[r]->P + preprocess_chunk() - 1) / preprocess_chunk();
+        recs += scenes[r]->P;
+        tiles += (long long)R.cam.tiles_x * R.cam.tiles_y;
+    }
+    if (recs > f->max_g)
+        return fail(GS_ERR_CAPACITY, "batch has %lld Gaussians, the frame holds %lld", recs, f->max_g);
+    if (tiles > f->max_tiles) return fail(GS_ERR_CAPACITY, "batch has %lld tiles, the frame holds %lld", tiles, f->max_tiles);
+    B.total_chunks = chunks;
+    B.total_recs = recs;
+    B.total_tiles = (int)tiles;
+    return GS_OK;
+}
+
+static PreprocessArgs pre_args(gs_frame *f) {
+    PreprocessArgs a;
+    a.B = f->batch;
     a.recs = f->recs;
     a.keys = f->keys[0];
     a.vals = f->vals[0];
@@ -475,21 +527,63 @@ gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, co
     a.chunk_base2 = f->chunk_base2;
     a.ctr = f->ctr;
     a.pair_cap = f->max_pairs;
-    a.n_chunks = (int)((s->P + preprocess_chunk() - 1) / preprocess_chunk());
+    a.n_chunks = f->batch.total_chunks;
+    return a;
+}
+
+// First half of the preprocess of f->batch: geometry and exact pair counts (k_pre_count).
+static gs_status batch_count(gs_frame *f, cudaStream_t st) {
     GS_CUDA(cudaMemsetAsync(f->ctr, 0, offsetof(FrameCounters, sort_epoch), st));
-    f->mode_used = f->tuning.sort_mode;
-    if (f->mode_used == 1)
-        launch_preprocess_depth(a, f->sort, st);
-    else
-        launch_preprocess(a, st);
+    launch_pre_count(pre_args(f), st);
     GS_CUDA(cudaGetLastError());
-    f->W = c.W;
-    f->H = c.H;
-    f->tiles_x = c.tiles_x;
-    f->tiles_y = c.tiles_y;
+    return GS_OK;
+}
+
+// Second half: scan, (depth order,) and emission.  `counted`: batch_count already ran.
+static gs_status batch_emit(gs_frame *f, cudaStream_t st, bool counted) {
+    if (!counted) GS_CUDA(cudaMemsetAsync(f->ctr, 0, offsetof(FrameCounters, sort_epoch), st));
+    f->mode_used = f->tuning.sort_mode;
+    const PreprocessArgs a = pre_args(f);
+    if (f->mode_used == 1)
+        launch_preprocess_depth(a, f->sort, st, counted);
+    else
+        launch_preprocess(a, st, counted);
+    GS_CUDA(cudaGetLastError());
+    const ReqDesc &R0 = f->batch.r[0];
+    f->W = R0.cam.W;
+    f->H = R0.cam.H;
+    f->tiles_x = R0.cam.tiles_x;
+    f->tiles_y = R0.cam.tiles_y;
     f->sorted_buf = 0;
-    f->cam = c;
-    f->opt = a.opt;
+    f->cam = R0.cam;
+    f->opt = R0.opt;
+    return GS_OK;
+}
+
+gs_status frame_batch_count(gs_frame *f, int n, const gs_scene *const *scenes, const gs_camera *cams,
+                            const gs_render_opts *opts, unsigned long long *req_pairs_dev, gs_stream stream) {
+    gs_status st = make_batch(f, n, scenes, cams, opts);
+    if (st) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    if ((st = batch_count(f, cs))) return st;
+    launch_req_pairs(pre_args(f), req_pairs_dev, cs);
+    GS_CUDA(cudaGetLastError());
+    f->scene_used = n == 1 ? scenes[0] : nullptr;
+    return GS_OK;
+}
+
+extern "C" {
+
+gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, const gs_render_opts *opts,
+                        gs_stream stream) {
+    if (!f || !s || !cam) return fail(GS_ERR_INVALID_ARG, "NULL frame, scene or camera");
+    if (s->P > f->max_g) return fail(GS_ERR_INVALID_ARG, "scene has %lld Gaussians, frame holds %lld", s->P, f->max_g);
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > f->max_w || cam->height > f->max_h)
+        return fail(GS_ERR_INVALID_ARG, "image %dx%d outside the frame's %dx%d", cam->width, cam->height, f->max_w,
+                    f->max_h);
+    gs_status st = make_batch(f, 1, &s, cam, opts);
+    if (st) return st == GS_ERR_CAPACITY ? GS_ERR_INVALID_ARG : st;
+    if ((st = batch_emit(f, (cudaStream_t)stream, false))) return st;
     f->scene_used = s;
     return GS_OK;
 }
@@ -497,7 +591,7 @@ gs_status gs_preprocess(gs_frame *f, const gs_scene *s, const gs_camera *cam, co
 gs_status gs_sort(gs_frame *f, gs_stream stream) {
     if (!f) return fail(GS_ERR_INVALID_ARG, "frame is NULL");
     if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_sort before gs_preprocess");
-    const int tile_bits = ceil_log2((long long)f->tiles_x * f->tiles_y);
+    const int tile_bits = ceil_log2((long long)f->batch.total_tiles);
     if (f->mode_used == 1) {
         f->passes = launch_sort32((unsigned *)f->keys[0], f->vals[0], (unsigned *)f->keys[1], f->vals[1],
                                   &f->ctr->n_pairs, f->max_pairs, tile_bits > 0 ? tile_bits : 1, f->sort, f->ctr,
@@ -516,10 +610,35 @@ gs_status gs_ranges(gs_frame *f, gs_stream stream) {
     if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_ranges before gs_preprocess");
     if (f->mode_used == 1)
         launch_ranges32((const unsigned *)f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs,
-                        f->tiles_x * f->tiles_y, f->starts, (cudaStream_t)stream);
+                        f->batch.total_tiles, f->starts, (cudaStream_t)stream);
     else
-        launch_ranges(f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs, f->tiles_x * f->tiles_y, f->starts,
+        launch_ranges(f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs, f->batch.total_tiles, f->starts,
                       (cudaStream_t)stream);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+static gs_status blend_batch(gs_frame *f, float *const *rgb, float *const *T, uint32_t *const *last,
+                             const gs_render_opts *opts_override, gs_stream stream) {
+    BlendArgs a;
+    a.B = f->batch;
+    for (int r = 0; r < a.B.n; ++r) {
+        if (!rgb[r]) return fail(GS_ERR_INVALID_ARG, "rgb output %d is NULL", r);
+        a.B.r[r].rgb = rgb[r];
+        a.B.r[r].T = T ? T[r] : nullptr;
+        a.B.r[r].last = last ? (unsigned *)last[r] : nullptr;
+        if (opts_override) a.B.r[r].opt = make_opts(opts_override);
+    }
+    a.recs = f->recs;
+    a.vals = f->vals[f->sorted_buf];
+    a.starts = f->starts;
+    a.n_dev = &f->ctr->n_pairs;
+    a.cap = f->max_pairs;
+    a.evals = f->ctr->evals;
+    a.variant = f->tuning.blend_variant;
+    a.count = f->counting;
+    if (f->counting) GS_CUDA(cudaMemsetAsync(f->ctr->evals, 0, sizeof(f->ctr->evals), (cudaStream_t)stream));
+    launch_blend(a, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -528,27 +647,10 @@ gs_status gs_blend(gs_frame *f, const gs_render_opts *opts, float *rgb, float *T
                    gs_stream stream) {
     if (!f || !rgb) return fail(GS_ERR_INVALID_ARG, "NULL frame or rgb");
     if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_blend before gs_preprocess");
-    BlendArgs a;
-    a.recs = f->recs;
-    a.vals = f->vals[f->sorted_buf];
-    a.starts = f->starts;
-    a.n_dev = &f->ctr->n_pairs;
-    a.cap = f->max_pairs;
-    a.opt = make_opts(opts);
-    a.W = f->W;
-    a.H = f->H;
-    a.tiles_x = f->tiles_x;
-    a.tiles_y = f->tiles_y;
-    a.rgb = rgb;
-    a.T = T;
-    a.last = last;
-    a.evals = f->ctr->evals;
-    a.variant = f->tuning.blend_variant;
-    a.count = f->counting;
-    if (f->counting) GS_CUDA(cudaMemsetAsync(f->ctr->evals, 0, sizeof(f->ctr->evals), (cudaStream_t)stream));
-    launch_blend(a, (cudaStream_t)stream);
-    GS_CUDA(cudaGetLastError());
-    return GS_OK;
+    if (f->batch.n != 1) return fail(GS_ERR_INVALID_ARG, "the frame holds a batch: use gs_render_batch");
+    gs_render_opts o;
+    if (!opts) gs_default_opts(&o);
+    return blend_batch(f, &rgb, &T, &last, opts ? opts : &o, stream);
 }
 
 // Records stage event i; inside a stream capture the record must become an event node of the
@@ -648,7 +750,7 @@ gs_status gs_render_host(gs_frame *f, const gs_scene *s, const gs_camera *cam, c
     if (!f || !cam || !rgb_host) return fail(GS_ERR_INVALID_ARG, "NULL frame, camera or rgb_host");
     const size_t npx = (size_t)f->max_w * (size_t)f->max_h;
     if (!f->out_mem) {
-        GS_CUDA(cudaSetDevice(f->ctx->device));
+        GS_CUDA(cudaSetDevice(f->device));
         GS_CUDA(cudaMalloc(&f->out_mem, npx * 5 * sizeof(float)));
     }
     float *rgb = (float *)f->out_mem;
@@ -733,11 +835,36 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *vals, uint64_
 
 }  // extern "C"
 
+// ------------------------------------------------------------------------------------------ batch API
+extern "C" gs_status gs_render_batch(gs_frame *f, int32_t n, const gs_scene *const *scenes, const gs_camera *cams,
+                                     const gs_render_opts *opts, float *const *rgb, float *const *T,
+                                     uint32_t *const *last, gs_stream stream) {
+    if (!f || !scenes || !cams || !rgb) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+    gs_status st = make_batch(f, n, scenes, cams, opts);
+    if (st) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    if ((st = batch_emit(f, cs, false))) return st;
+    f->scene_used = n == 1 ? scenes[0] : nullptr;
+    if ((st = gs_sort(f, stream))) return st;
+    if ((st = gs_ranges(f, stream))) return st;
+    return blend_batch(f, rgb, T, last, nullptr, stream);
+}
+
+// Server path: finish a batch whose counts are already on the device (frame_batch_count).
+gs_status frame_batch_finish(gs_frame *f, float *const *rgb, float *const *T, uint32_t *const *last,
+                             gs_stream stream) {
+    gs_status st = batch_emit(f, (cudaStream_t)stream, true);
+    if (st) return st;
+    if ((st = gs_sort(f, stream))) return st;
+    if ((st = gs_ranges(f, stream))) return st;
+    return blend_batch(f, rgb, T, last, nullptr, stream);
+}
+
 // ------------------------------------------------------------------------------------------ autotune
 static gs_status frame_outputs(gs_frame *f, float **rgb, float **T, uint32_t **last) {
     const size_t npx = (size_t)f->max_w * (size_t)f->max_h;
     if (!f->out_mem) {
-        GS_CUDA(cudaSetDevice(f->ctx->device));
+        GS_CUDA(cudaSetDevice(f->device));
         GS_CUDA(cudaMalloc(&f->out_mem, npx * 5 * sizeof(float)));
     }
     *rgb = (float *)f->out_mem;
@@ -751,7 +878,7 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
                                  gs_stream stream) {
     if (!f || !s || !cams || ncams <= 0) return fail(GS_ERR_INVALID_ARG, "NULL frame/scene/cameras or ncams <= 0");
     cudaDeviceProp prop;
-    GS_CUDA(cudaGetDeviceProperties(&prop, f->ctx->device));
+    GS_CUDA(cudaGetDeviceProperties(&prop, f->device));
     std::string dev = prop.name;
     for (char &ch : dev)
         if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
@@ -850,10 +977,11 @@ extern "C" gs_status gs_render_backward(gs_frame *f, const gs_scene *s, const fl
     if (!f || !s || !dL_drgb || !T || !last || !g) return fail(GS_ERR_INVALID_ARG, "NULL argument");
     if (!g->means || !g->scales || !g->quats || !g->opacity || !g->sh)
         return fail(GS_ERR_INVALID_ARG, "a gradient array is NULL");
-    if (f->W <= 0 || f->scene_used != s) return fail(GS_ERR_INVALID_ARG, "no render of this scene on the frame");
+    if (f->W <= 0 || f->scene_used != s || f->batch.n != 1)
+        return fail(GS_ERR_INVALID_ARG, "no single render of this scene on the frame");
     cudaStream_t st = (cudaStream_t)stream;
     if (!f->grad2d) {
-        GS_CUDA(cudaSetDevice(f->ctx->device));
+        GS_CUDA(cudaSetDevice(f->device));
         GS_CUDA(cudaMalloc(&f->grad2d, sizeof(float) * (size_t)grad2d_floats() * (size_t)f->max_g));
     }
     GS_CUDA(cudaMemsetAsync(f->grad2d, 0, sizeof(float) * (size_t)grad2d_floats() * (size_t)s->P, st));

@@ -59,6 +59,49 @@ struct Rec {
     float4 r0, r1, r2;
 };
 
+// A batch of render requests, passed by value to every forward kernel (Section 5.3.1: parameters
+// shared by all threads live in the kernel-parameter constant bank).  Request r owns chunks
+// [chunk0, next chunk0) of 256 Gaussians, records rec0 + Gaussian id and global tiles
+// [tile0, tile0 + tiles_x * tiles_y); a single render is a batch of one with all offsets 0.
+constexpr int kMaxBatch = 16;
+struct ReqDesc {
+    Cam cam;
+    Opts opt;
+    SceneView scene;
+    long long chunk0;
+    long long rec0;
+    int tile0;
+    int pad;
+    float *rgb;          // blend outputs ([3,H,W], [H,W], [H,W])
+    float *T;
+    unsigned *last;
+};
+struct BatchDesc {
+    int n;
+    int total_tiles;
+    long long total_chunks;
+    long long total_recs;
+    ReqDesc r[kMaxBatch];
+};
+__device__ __forceinline__ int req_of_chunk(const BatchDesc &B, long long chunk) {
+    int r = 0;
+    for (int i = 1; i < B.n; ++i)
+        if (B.r[i].chunk0 <= chunk) r = i;
+    return r;
+}
+__device__ __forceinline__ int req_of_rec(const BatchDesc &B, long long rec) {
+    int r = 0;
+    for (int i = 1; i < B.n; ++i)
+        if (B.r[i].rec0 <= rec) r = i;
+    return r;
+}
+__device__ __forceinline__ int req_of_tile(const BatchDesc &B, int tile) {
+    int r = 0;
+    for (int i = 1; i < B.n; ++i)
+        if (B.r[i].tile0 <= tile) r = i;
+    return r;
+}
+
 // Device counters of one frame.  Everything before sort_epoch is cleared at the start of every
 // frame; sort_epoch only grows (it tags the sort's look-back descriptors).
 struct FrameCounters {
@@ -201,9 +244,7 @@ __device__ __forceinline__ float pixel_q(float a, float b2, float c, float dx, f
 // ----------------------------------------------------------------------------------------------
 // host-side launchers (defined in the .cu files)
 struct PreprocessArgs {
-    SceneView scene;
-    Cam cam;
-    Opts opt;
+    BatchDesc B;
     Rec *recs;
     unsigned long long *keys;
     unsigned *vals;
@@ -222,14 +263,16 @@ struct PreprocessArgs {
     unsigned long long *chunk_base2; // exclusive scan of chunk_hits2
     FrameCounters *ctr;
     long long pair_cap;
-    int n_chunks;
+    long long n_chunks;
 };
 
 void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *scale, float4 *quat, float4 *sh,
                        cudaStream_t s);
-void launch_preprocess(const PreprocessArgs &a, cudaStream_t s);
+void launch_pre_count(const PreprocessArgs &a, cudaStream_t s);
+void launch_req_pairs(const PreprocessArgs &a, unsigned long long *out, cudaStream_t s);
+void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted);
 struct SortScratch;
-int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cudaStream_t s);
+int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cudaStream_t s, bool counted);
 void launch_make_keys(const unsigned *tkeys, const unsigned *vals, const float4 *geo1, long long n,
                       unsigned long long *out, cudaStream_t s);
 int preprocess_chunk();
@@ -258,16 +301,12 @@ void launch_ranges32(const unsigned *keys, const unsigned long long *n_dev, long
                      unsigned *starts, cudaStream_t s);
 
 struct BlendArgs {
+    BatchDesc B;
     const Rec *recs;
     const unsigned *vals;
     const unsigned *starts;
     const unsigned long long *n_dev;
     long long cap;
-    Opts opt;
-    int W, H, tiles_x, tiles_y;
-    float *rgb;
-    float *T;
-    unsigned *last;
     unsigned long long *evals;       // [2]: entries walked, entries passing q <= t (count mode)
     int variant;                     // launch shape, see launch_blend
     int count;                       // 1: instrumented variant filling evals

@@ -270,12 +270,13 @@ struct PreSmem {
     int tx0[kPreBlock], ty0[kPreBlock], w[kPreBlock];
     int cstart[kPreBlock + 1];        // exclusive scan of candidate-tile counts
     unsigned cnt[kPreBlock];          // pairs of each Gaussian of the chunk
+    unsigned char req[kPreBlock];     // request of each Gaussian (batch index)
     unsigned wsum[kPreBlock / 32];
 };
 
 // Candidate slot -> (Gaussian g of the CTA, tile); slot s belongs to the last g with
 // cstart[g] <= s, and is its k-th candidate tile in row-major order.
-__device__ __forceinline__ bool slot_test(const PreSmem &S, const Cam &cam, int slot, int &g_out, int &tile) {
+__device__ __forceinline__ bool slot_test(const PreSmem &S, const BatchDesc &B, int slot, int &g_out, int &tile) {
     int lo = 0, hi = kPreBlock - 1;
 #pragma unroll
     for (int it = 0; it < 8; ++it) {
@@ -290,9 +291,10 @@ __device__ __forceinline__ bool slot_test(const PreSmem &S, const Cam &cam, int 
     const int w = S.w[g];
     const int dy = k / w;
     const int tx = S.tx0[g] + (k - dy * w), ty = S.ty0[g] + dy;
+    const ReqDesc &R = B.r[S.req[g]];
     g_out = g;
-    tile = ty * cam.tiles_x + tx;
-    return test_tile(cam, S.u[g], S.v[g], S.a[g], S.b[g], S.c[g], S.t[g], tx, ty);
+    tile = R.tile0 + ty * R.cam.tiles_x + tx;     // global tile id of the batch
+    return test_tile(R.cam, S.u[g], S.v[g], S.a[g], S.b[g], S.c[g], S.t[g], tx, ty);
 }
 
 // Block exclusive scan of one int per thread into S.cstart; returns the block total.
@@ -327,12 +329,16 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constan
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned FULL = 0xffffffffu;
     const long long chunk = blockIdx.x;
-    const long long gid = chunk * kPreBlock + tid;
-    const Cam &cam = A.cam;
+    const int ri = req_of_chunk(A.B, chunk);
+    const ReqDesc &R = A.B.r[ri];
+    const long long gid = (chunk - R.chunk0) * kPreBlock + tid;
+    const long long rec = R.rec0 + gid;
+    const Cam &cam = R.cam;
+    S.req[tid] = (unsigned char)ri;
 
     Geom G;
     bool valid = false, passed_cull = false;
-    if (gid < A.scene.P) valid = gaussian_geometry(A.scene, gid, cam, A.opt, G, passed_cull);
+    if (gid < R.scene.P) valid = gaussian_geometry(R.scene, gid, cam, R.opt, G, passed_cull);
     const unsigned n_in = __popc(__ballot_sync(FULL, passed_cull));
     if (lane == 0 && n_in) atomicAdd(&A.ctr->n_culled_in, n_in);
     const int w = valid ? G.tx1 - G.tx0 + 1 : 0;
@@ -359,7 +365,7 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constan
         int g = -1;
         if (slot < ctotal) {
             int tile;
-            hit = slot_test(S, cam, slot, g, tile);
+            hit = slot_test(S, A.B, slot, g, tile);
         }
         // consecutive slots share Gaussians: one shared-memory add per (warp, Gaussian)
         const unsigned peers = __match_any_sync(FULL, g);
@@ -374,21 +380,21 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constan
         A.chunk_vis[chunk] = nvis_block;
         if (nvis_block) atomicAdd(&A.ctr->n_visible, nvis_block);
     }
-    if (gid < A.scene.P) A.counts[gid] = S.cnt[tid];
-    if (gid < A.scene.P) A.geo2[gid] = vis ? make_int4(G.tx0, G.ty0, w, h) : make_int4(0, 0, 0, 0);
+    if (gid < R.scene.P) A.counts[rec] = S.cnt[tid];
+    if (gid < R.scene.P) A.geo2[rec] = vis ? make_int4(G.tx0, G.ty0, w, h) : make_int4(0, 0, 0, 0);
     if (vis) {
-        A.geo0[gid] = make_float4(G.u, G.v, G.a, G.b);
-        A.geo1[gid] = make_float4(G.c, G.t, __uint_as_float(__float_as_uint(G.z)), 0.0f);
-        const float4 po = __ldg(A.scene.pos_opa + gid);
+        A.geo0[rec] = make_float4(G.u, G.v, G.a, G.b);
+        A.geo1[rec] = make_float4(G.c, G.t, __uint_as_float(__float_as_uint(G.z)), 0.0f);
+        const float4 po = __ldg(R.scene.pos_opa + gid);
         float rgb[3];
-        sh_colour(A.scene, gid, cam, po.x, po.y, po.z, rgb);
+        sh_colour(R.scene, gid, cam, po.x, po.y, po.z, rgb);
         const float LOG2E = 1.4426950408889634f;
         const float Gl = log_rn(G.alpha0) * LOG2E;
         Rec rc;
         rc.r0 = make_float4(G.u, G.v, G.a, G.b + G.b);
         rc.r1 = make_float4(G.c, G.t, Gl, rgb[0]);
         rc.r2 = make_float4(rgb[1], rgb[2], G.hx + 1.0f, G.hy + 1.0f);
-        A.recs[gid] = rc;
+        A.recs[rec] = rc;
     }
 }
 
@@ -452,10 +458,12 @@ __global__ void __launch_bounds__(kScanThreads) k_chunk_scan(const unsigned *in_
 // (depth bits, id) for the depth sort.
 __global__ void __launch_bounds__(kPreBlock) k_vis_compact(const __grid_constant__ PreprocessArgs A) {
     const long long chunk = blockIdx.x;
-    const long long gid = chunk * kPreBlock + threadIdx.x;
+    const ReqDesc &R = A.B.r[req_of_chunk(A.B, chunk)];
+    const long long gid = (chunk - R.chunk0) * kPreBlock + threadIdx.x;
+    const long long rec = R.rec0 + gid;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ unsigned s_w[kPreBlock / 32];
-    const bool vis = gid < A.scene.P && A.counts[gid] != 0;
+    const bool vis = gid < R.scene.P && A.counts[rec] != 0;
     const unsigned bal = __ballot_sync(0xffffffffu, vis);
     if (lane == 0) s_w[warp] = __popc(bal);
     __syncthreads();
@@ -463,8 +471,8 @@ __global__ void __launch_bounds__(kPreBlock) k_vis_compact(const __grid_constant
     for (int w2 = 0; w2 < warp; ++w2) pre += s_w[w2];
     if (vis) {
         const unsigned long long pos = A.vis_base[chunk] + pre + __popc(bal & ((1u << lane) - 1u));
-        A.dkey[pos] = __float_as_uint(A.geo1[gid].z);
-        A.dval[pos] = (unsigned)gid;
+        A.dkey[pos] = __float_as_uint(A.geo1[rec].z);
+        A.dval[pos] = (unsigned)rec;
     }
 }
 
@@ -498,13 +506,22 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const long long chunk = blockIdx.x;
-    long long gid = chunk * kPreBlock + tid;
-    bool in_range = gid < A.scene.P;
+    long long gid;                    // here: the record index (request rec0 + Gaussian id)
+    bool in_range;
+    int ri;
     if (DEPTH) {
-        in_range = gid < (long long)A.ctr->n_vis64;
-        gid = in_range ? (long long)A.dsorted[gid] : 0;
+        const long long rank = chunk * kPreBlock + tid;
+        in_range = rank < (long long)A.ctr->n_vis64;
+        gid = in_range ? (long long)A.dsorted[rank] : 0;
+        ri = req_of_rec(A.B, gid);
+    } else {
+        ri = req_of_chunk(A.B, chunk);
+        const ReqDesc &R = A.B.r[ri];
+        const long long lg = (chunk - R.chunk0) * kPreBlock + tid;
+        in_range = lg < R.scene.P;
+        gid = R.rec0 + lg;
     }
-    const Cam &cam = A.cam;
+    S.req[tid] = (unsigned char)ri;
     int ncand = 0;
     S.cnt[tid] = (unsigned)gid;
     if (in_range) {
@@ -534,7 +551,7 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
         const int slot = base + tid;
         bool hit = false;
         int g = 0, tile = 0;
-        if (slot < ctotal) hit = slot_test(S, cam, slot, g, tile);
+        if (slot < ctotal) hit = slot_test(S, A.B, slot, g, tile);
         const unsigned bal = __ballot_sync(FULL, hit);
         if (lane == 0) S.wsum[warp] = __popc(bal);
         __syncthreads();
@@ -552,7 +569,7 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
                     A.tkeys[pos] = (unsigned)tile;
                 else
                     A.keys[pos] = ((unsigned long long)(unsigned)tile << 32) | S.zb[g];
-                A.vals[pos] = S.cnt[g];        // Gaussian id of slot g
+                A.vals[pos] = S.cnt[g];        // record index of slot g
             }
         }
         run += tot;
@@ -560,29 +577,60 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
     }
 }
 
-void launch_preprocess(const PreprocessArgs &a, cudaStream_t s) {
+void launch_pre_count(const PreprocessArgs &a, cudaStream_t s) {
     if (a.n_chunks <= 0) return;
-    k_pre_count<<<a.n_chunks, kPreBlock, 0, s>>>(a);
-    k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, a.chunk_base, &a.ctr->n_pairs, nullptr, nullptr, nullptr,
-                                            a.n_chunks, a.pair_cap, &a.ctr->status);
-    k_pre_emit<false><<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    k_pre_count<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
 }
 
-int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cudaStream_t s) {
+void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted) {
+    if (a.n_chunks <= 0) return;
+    if (!counted) k_pre_count<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
+    k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, a.chunk_base, &a.ctr->n_pairs, nullptr, nullptr, nullptr,
+                                            a.n_chunks, a.pair_cap, &a.ctr->status);
+    k_pre_emit<false><<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
+}
+
+int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cudaStream_t s, bool counted) {
     if (a.n_chunks <= 0) return 0;
-    k_pre_count<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    if (!counted) k_pre_count<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
     k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, nullptr, &a.ctr->n_pairs, a.chunk_vis, a.vis_base,
                                             &a.ctr->n_vis64, a.n_chunks, a.pair_cap, &a.ctr->status);
-    k_vis_compact<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    k_vis_compact<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
     // depth sort of the paired Gaussians: 32-bit float bits of z (positive, so bit order = value order)
-    const int dp = launch_sort32(a.dkey, a.dval, a.dkey_tmp, a.dval_tmp, &a.ctr->n_vis64, a.scene.P, 32, scr, a.ctr, s);
+    const int dp = launch_sort32(a.dkey, a.dval, a.dkey_tmp, a.dval_tmp, &a.ctr->n_vis64, a.B.total_recs, 32, scr,
+                                 a.ctr, s);
     (void)dp;   // four passes: the result is back in dkey / dval
-    k_emit_sum<<<a.n_chunks, kPreBlock, 0, s>>>(a);
+    // depth ranks run over all records of the batch: size the rank chunks by total_recs
+    const long long rank_chunks = (a.B.total_recs + kPreBlock - 1) / kPreBlock;
+    k_emit_sum<<<(unsigned)rank_chunks, kPreBlock, 0, s>>>(a);
     unsigned long long *unused_total = &a.ctr->scratch64;
     k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits2, a.chunk_base2, unused_total, nullptr, nullptr, nullptr,
-                                            a.n_chunks, 1ll << 62, nullptr);
-    k_pre_emit<true><<<a.n_chunks, kPreBlock, 0, s>>>(a);
+                                            rank_chunks, 1ll << 62, nullptr);
+    k_pre_emit<true><<<(unsigned)rank_chunks, kPreBlock, 0, s>>>(a);
     return 4;
+}
+
+// Pairs of each request of the batch (sums of its chunks' counts), for admission decisions.
+__global__ void __launch_bounds__(256) k_req_pairs(const __grid_constant__ PreprocessArgs A, unsigned long long *out) {
+    const int r = blockIdx.x;
+    const long long c0 = A.B.r[r].chunk0;
+    const long long c1 = r + 1 < A.B.n ? A.B.r[r + 1].chunk0 : A.B.total_chunks;
+    unsigned long long sum = 0;
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) sum += A.chunk_hits[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __shared__ unsigned long long s_w[8];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < 8; ++w) t += s_w[w];
+        out[r] = t;
+    }
+}
+
+void launch_req_pairs(const PreprocessArgs &a, unsigned long long *out, cudaStream_t s) {
+    if (a.B.n > 0) k_req_pairs<<<a.B.n, 256, 0, s>>>(a, out);
 }
 
 __global__ void k_make_keys(const unsigned *tkeys, const unsigned *vals, const float4 *geo1, long long n,

@@ -68,8 +68,11 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
     static_assert(BATCH % NT == 0 && BATCH % 32 == 0, "batch must be a multiple of the thread count");
     __shared__ BlendSmem<PX, BATCH> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
-    const int tx = tile % A.tiles_x, ty = tile / A.tiles_x;
+    const int gtile = blockIdx.x;                          // global tile of the batch
+    const ReqDesc &R = A.B.r[req_of_tile(A.B, gtile)];
+    const int tile = gtile - R.tile0;
+    const int W = R.cam.W, H = R.cam.H;
+    const int tx = tile % R.cam.tiles_x, ty = tile / R.cam.tiles_x;
     constexpr int REGIONS_PER_ROW = 16 / WR::RC;
     const int rx0 = tx * kTile + (warp % REGIONS_PER_ROW) * WR::RC;    // region origin (pixels)
     const int ry0 = ty * kTile + (warp / REGIONS_PER_ROW) * WR::RR;
@@ -79,8 +82,8 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
     const float qx0 = (float)rx0, qx1 = (float)(rx0 + WR::RC), qy0 = (float)ry0, qy1 = (float)(ry0 + WR::RR);
     long long n = (long long)*A.n_dev;
     if (n > A.cap) n = A.cap;
-    const long long start = min((long long)A.starts[tile], n);
-    const long long end = min((long long)A.starts[tile + 1], n);
+    const long long start = min((long long)A.starts[gtile], n);
+    const long long end = min((long long)A.starts[gtile + 1], n);
     const float fpy = (float)py + 0.5f;
     const float INF = __int_as_float(0x7f800000);
     float fpx[PX];
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
     int alive_px = 0;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
-        inside[k] = px0 + k < A.W && py < A.H;
+        inside[k] = px0 + k < W && py < H;
         // a finished pixel keeps x = +inf: its q is +inf or NaN and never passes q <= t
         fpx[k] = inside[k] ? (float)(px0 + k) + 0.5f : INF;
         alive_px += inside[k];
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
         contrib[k] = 0;
     }
     const float HALF_LOG2E = 0.72134752044448170f;
-    const float amax = A.opt.alpha_max, tmin = A.opt.T_min;
+    const float amax = R.opt.alpha_max, tmin = R.opt.T_min;
     const unsigned FULL = 0xffffffffu;
 
     // ---- pipeline prologue: ids of batches 0 and 1, records of batch 0
@@ -234,17 +237,17 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
         }
     }
 
-    const long long npx = (long long)A.W * A.H;
+    const long long npx = (long long)W * H;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
         const int px = px0 + k;
         if (inside[k]) {
-            const long long o = (long long)py * A.W + px;
-            A.rgb[o] = C0[k] + T[k] * A.opt.bg[0];
-            A.rgb[npx + o] = C1[k] + T[k] * A.opt.bg[1];
-            A.rgb[2 * npx + o] = C2[k] + T[k] * A.opt.bg[2];
-            if (A.T) A.T[o] = T[k];
-            if (A.last) A.last[o] = last[k];
+            const long long o = (long long)py * W + px;
+            R.rgb[o] = C0[k] + T[k] * R.opt.bg[0];
+            R.rgb[npx + o] = C1[k] + T[k] * R.opt.bg[1];
+            R.rgb[2 * npx + o] = C2[k] + T[k] * R.opt.bg[2];
+            if (R.T) R.T[o] = T[k];
+            if (R.last) R.last[o] = last[k];
         }
     }
 }
@@ -267,7 +270,7 @@ static void launch_blend_t(const BlendArgs &a, int ntiles, cudaStream_t s) {
 }
 
 void launch_blend(const BlendArgs &a, cudaStream_t s) {
-    const int ntiles = a.tiles_x * a.tiles_y;
+    const int ntiles = a.B.total_tiles;
     if (ntiles <= 0) return;
     if (a.count)
         launch_blend_t<true>(a, ntiles, s);

@@ -1,0 +1,114 @@
+"""The serving loop through the C ABI: requests of mixed scenes and sizes submitted together are
+batched (continuous batching over several slots), every image equals the standalone render bit for
+bit, admission by pair-buffer memory splits batches that do not fit and fails a request that alone
+exceeds the capacity, and the plain baseline loop runs one request at a time."""
+import numpy as np
+import pytest
+
+from paper_2408_07967_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2408_07967_gb300 as gs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2408_07967_gb300 import build
+    build.build()
+    ctx = gs.Context(0)
+    sa, ca = synth.random_small_scene(6000, 51, 160, 120, log_scale_mu=-2.6, log_scale_sigma=1.0)
+    sb, cb = synth.random_small_scene(3000, 52, 96, 64, log_scale_mu=-2.2, log_scale_sigma=0.8)
+    A = gs.Scene.from_numpy(ctx, sa)
+    B = gs.Scene.from_numpy(ctx, sb)
+    rng = np.random.default_rng(3)
+    reqs = []
+    for i in range(24):
+        sc = (A, B)[i % 2]
+        W, H = [(160, 120), (96, 64), (200, 90), (64, 64)][i % 4]
+        C = rng.normal(0, 0.2, 3)
+        cam = synth.look_at(C, (rng.normal(0, 0.2), rng.normal(0, 0.2), 3.0), W, H)
+        reqs.append((sc, cam))
+    alone = []
+    for sc, cam in reqs:
+        fr = gs.Frame(ctx, sc.P, 1 << 22, cam.width, cam.height)
+        rgb, _, _ = fr.render(sc, cam)
+        alone.append(rgb.cpu())
+    return ctx, A, B, reqs, alone
+
+
+def run(server, reqs):
+    outs, tickets = [], []
+    for sc, cam in reqs:
+        buf = torch.empty((3, cam.height, cam.width), dtype=torch.float32).pin_memory()
+        outs.append(buf)
+        tickets.append(server.gs_server_submit(sc, cam, buf))
+    stats = [server.gs_server_wait(t, 60000) for t in tickets]
+    return outs, stats
+
+
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_batched_results_equal_alone(setup, sort_mode):
+    ctx, A, B, reqs, alone = setup
+    sv = gs.Server(ctx, slots=3, max_batch=8, pair_capacity=1 << 22, max_gaussians=1 << 20, max_width=256,
+                   max_height=256, sort_mode=sort_mode)
+    outs, stats = run(sv, reqs)
+    assert all(s["status"] == 0 for s in stats)
+    for o, a in zip(outs, alone):
+        assert torch.equal(o, a)
+    assert max(s["batch_size"] for s in stats) > 1           # requests were batched
+    st = sv.stats()
+    assert st["completed"] == len(reqs) and st["batched_requests"] == len(reqs)
+    assert all(s["done_s"] >= s["admit_s"] >= s["arrival_s"] for s in stats)
+    sv.close()
+
+
+def test_admission_by_pair_memory(setup):
+    ctx, A, B, reqs, alone = setup
+    # capacity below the largest request's pairs: that one fails, the others are split into fitting batches
+    fr = gs.Frame(ctx, A.P, 1 << 22, 200, 120)
+    pairs = []
+    for sc, cam in reqs:
+        f = gs.Frame(ctx, sc.P, 1 << 22, cam.width, cam.height)
+        f.render(sc, cam)
+        pairs.append(f.stats()["pairs"])
+    cap = int(sorted(pairs)[-2]) + 1          # the largest request does not fit
+    sv = gs.Server(ctx, slots=2, max_batch=8, pair_capacity=cap, max_gaussians=1 << 20, max_width=256, max_height=256)
+    outs, stats = run(sv, reqs)
+    big = int(np.argmax(pairs))
+    for i, (o, a, s) in enumerate(zip(outs, alone, stats)):
+        if pairs[i] > cap:
+            assert s["status"] == -3 and s["pairs"] == pairs[i]
+        else:
+            assert s["status"] == 0 and torch.equal(o, a)
+            assert s["pairs"] == pairs[i]
+    assert stats[big]["status"] == -3
+    sv.close()
+
+
+def test_plain_loop_one_at_a_time(setup):
+    ctx, A, B, reqs, alone = setup
+    sv = gs.Server(ctx, plain=True, pair_capacity=1 << 22, max_gaussians=1 << 20, max_width=256, max_height=256)
+    outs, stats = run(sv, reqs[:8])
+    assert all(s["status"] == 0 and s["batch_size"] == 1 for s in stats)
+    for o, a in zip(outs, alone[:8]):
+        assert torch.equal(o, a)
+    done = sorted(s["done_s"] for s in stats)
+    admits = sorted(s["admit_s"] for s in stats)
+    assert all(admits[i + 1] >= done[i] - 1e-6 for i in range(7))   # strictly one after another
+    sv.close()
+
+
+def test_wait_timeout_and_bad_requests(setup):
+    ctx, A, B, reqs, alone = setup
+    sv = gs.Server(ctx, slots=1, max_batch=2, pair_capacity=1 << 22, max_gaussians=1 << 20, max_width=128,
+                   max_height=128)
+    big = synth.look_at((0, 0, 0), (0, 0, 3), 512, 512)
+    buf = torch.empty((3, 512, 512)).pin_memory()
+    with pytest.raises(gs.GsError):
+        sv.gs_server_submit(A, big, buf)
+    sv.close()
