@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-training", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=300)
     return ap.parse_args()
 
 
@@ -181,6 +184,132 @@ def cpu_baseline(args, scene, cams):
     return {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "sample": f"{n} full frame(s) (cameras 0..{n - 1}) of the workload, oracle binary32 mode, "
                       f"OpenMP over tiles, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------------------ serving
+def pct(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def serve_run(gs, srv_kw, scenes, poses, schedule, ring):
+    """Submit `schedule` (arrival offset s, scene idx, camera idx, (W, H)) open loop; returns the
+    per-request stats.  ring: page-locked host buffers reused once their request has finished."""
+    import threading
+    from paper_2408_07967_gb300 import synth
+    server = gs.Server(srv_kw.pop("ctx"), **srv_kw)
+    n = len(schedule)
+    stats = [None] * n
+    tickets = [None] * n
+    done = [threading.Event() for _ in range(n)]
+    submitted = threading.Semaphore(0)
+
+    def waiter():
+        for i in range(n):
+            submitted.acquire()
+            stats[i] = server.gs_server_wait(tickets[i], -1)
+            done[i].set()
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    t0 = server.clock() + 0.05
+    for i, (ta, si, ci, (W, H)) in enumerate(schedule):
+        if i >= len(ring):
+            done[i - len(ring)].wait()
+        cam = synth.rescaled(poses[si][ci], W, H)
+        buf = ring[i % len(ring)][: 3 * W * H].view(3, H, W)
+        while True:
+            dt = t0 + ta - server.clock()
+            if dt <= 0:
+                break
+            if dt > 0.002:
+                time.sleep(dt - 0.001)
+        tickets[i] = server.gs_server_submit(scenes[si], cam, buf, arrival_s=t0 + ta)
+        submitted.release()
+    th.join()
+    wall = max(s["done_s"] for s in stats) - t0
+    st = server.stats()
+    server.close()
+    return stats, wall, st
+
+
+def run_serving(args, gs, ctx, room_scene, room_cams):
+    import torch
+    from paper_2408_07967_gb300 import synth
+    city_scene, city_cams = synth.load_config("city")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        city = gs.Scene.from_numpy(ctx, city_scene, stream=stream)
+        room = gs.Scene.from_numpy(ctx, room_scene, stream=stream)
+    stream.synchronize()
+    del city_scene
+    scenes, poses = [room, city], [room_cams, city_cams]
+    ring = [torch.empty(3 * 3840 * 2160, dtype=torch.float32).pin_memory() for _ in range(16)]
+    batched = dict(slots=3, max_batch=8, pair_capacity=(1 << 28), max_gaussians=32_000_000, max_width=3840,
+                   max_height=2160)
+    plain = dict(plain=True, pair_capacity=(1 << 27), max_gaussians=11_000_000, max_width=3840, max_height=2160)
+    out = {"workload": "resident room 1M + city 10M scenes, requests 50/50 over scenes, random pose of the "
+                       "scene's 32, resolution uniform over 1280x720 / 1920x1080 / 3840x2160",
+           "requests_per_run": args.serving_requests}
+    for rate in (60, 240):
+        sched = synth.poisson_requests(args.serving_requests, rate, seed=3)
+        for name, kw in (("plain", plain), ("batched", batched)):
+            st, wall, sst = serve_run(gs, dict(kw, ctx=ctx), scenes, poses, sched, ring)
+            lat = [1000.0 * (s["done_s"] - s["arrival_s"]) for s in st]
+            ok = sum(s["status"] == 0 for s in st)
+            out[f"{name}@{rate}"] = {"frames_per_s": ok / wall, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                                     "mean_batch": sst["batched_requests"] / max(1, sst["batches"]),
+                                     "failed": len(st) - ok}
+    # saturation: every request available at once
+    sched = [(0.0, si, ci, wh) for (_, si, ci, wh) in synth.poisson_requests(args.serving_requests, 1e9, seed=4)]
+    for name, kw in (("plain", plain), ("batched", batched)):
+        st, wall, sst = serve_run(gs, dict(kw, ctx=ctx), scenes, poses, sched, ring)
+        lat = [1000.0 * (s["done_s"] - s["arrival_s"]) for s in st]
+        out[f"{name}@saturated"] = {"frames_per_s": sum(s["status"] == 0 for s in st) / wall,
+                                    "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                                    "mean_batch": sst["batched_requests"] / max(1, sst["batches"])}
+    city.close()
+    room.close()
+    return out
+
+
+def run_training(args, gs, ctx, room_scene, room_cams, steps=10):
+    """Forward + backward over 4-camera batches on the 1M room at 1920x1080, L1 loss against images
+    rendered from perturbed Gaussians (seed 4)."""
+    import numpy as np
+    import torch
+    from paper_2408_07967_gb300 import synth
+    from paper_2408_07967_gb300.autograd import GaussianRasterizer
+    raw = synth.room_scene(activated=False)
+    target = synth.perturbed(raw, seed=4)
+    W, H = room_cams[0].width, room_cams[0].height
+    rast = GaussianRasterizer(ctx, raw.P, W, H, batch=4, max_pairs=1 << 25)
+    tp = [torch.tensor(a, device="cuda") for a in (target.means, target.scales, target.quats, target.opacity,
+                                                    target.sh)]
+    params = [torch.tensor(a, device="cuda", requires_grad=True) for a in (raw.means, raw.scales, raw.quats,
+                                                                          raw.opacity, raw.sh)]
+    batches = [[room_cams[(4 * b + k) % len(room_cams)] for k in range(4)] for b in range(steps + 2)]
+    targets = []
+    with torch.no_grad():
+        for cams in batches:
+            targets.append(rast(*tp, cams).clone())
+    for b in range(2):
+        loss = (rast(*params, batches[b]) - targets[b]).abs().mean()
+        loss.backward()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for b in range(2, steps + 2):
+        for p in params:
+            p.grad = None
+        loss = (rast(*params, batches[b]) - targets[b]).abs().mean()
+        loss.backward()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "room 1M @1920x1080, 4-camera batches, L1 vs perturbed-Gaussian targets (seed 4)",
+            "ms_per_step": ms, "frames_per_s": 4000.0 / ms, "loss": float(loss.item()),
+            "grad_finite": bool(all(torch.isfinite(p.grad).all().item() for p in params))}
 
 
 # ------------------------------------------------------------------------------------ our arm
@@ -342,6 +471,12 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, scene, cams)
+    fr.close()
+    serving = training = None
+    if rank == 0 and not args.no_training and args.config == "room":
+        training = run_training(args, gs, ctx, scene, cams)
+    if rank == 0 and not args.no_serving and args.config == "room":
+        serving = run_serving(args, gs, ctx, scene, cams)
 
     if rank == 0:
         line = {"metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": ws, "steps": K,
@@ -355,7 +490,8 @@ def run_ours(args):
                 "frame": {"pairs": N, "visible": V, "culled_in": Pc, "evaluations": E, "contributions": Ec,
                           "sort_passes": passes,
                           "pairs_per_s": N * value / ws},
-                "wall_s": wall, "e2e": e2e, "cpu_baseline": cpu}
+                "wall_s": wall, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
+                "differentiable": training}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

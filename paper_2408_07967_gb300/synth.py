@@ -245,6 +245,24 @@ def city_cameras(n_aerial=16, n_street=16, width=3840, height=2160, hfov_deg=60.
     return cams
 
 
+def rescaled(cam: Camera, width: int, height: int, hfov_deg: float = 60.0) -> Camera:
+    """The same pose with a pinhole of another resolution and the given horizontal FOV."""
+    fx = 0.5 * width / math.tan(math.radians(hfov_deg) * 0.5)
+    return Camera(cam.R.copy(), cam.t.copy(), float(np.float32(fx)), float(np.float32(fx)), 0.5 * width, 0.5 * height,
+                  int(width), int(height), cam.near)
+
+
+def poisson_requests(n, rate, seed=3, resolutions=((1280, 720), (1920, 1080), (3840, 2160)), n_scenes=2):
+    """Open-loop arrival schedule: exponential inter-arrival times at `rate` per second, each
+    request a uniformly drawn scene index, camera index (0..31) and resolution."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    scene = rng.integers(0, n_scenes, n)
+    cam = rng.integers(0, 32, n)
+    res = rng.integers(0, len(resolutions), n)
+    return [(float(t[i]), int(scene[i]), int(cam[i]), resolutions[int(res[i])]) for i in range(n)]
+
+
 def perturbed(scene: Scene, seed=4, mean_sigma=0.01, dc_sigma=0.05, logit_sigma=0.2) -> Scene:
     """Target scene for the differentiable workload: means += N(0,0.01), DC += N(0,0.05),
     logits += N(0,0.2).  `scene` must hold raw (log-scale / logit) parameters."""
