@@ -113,6 +113,8 @@ struct FrameCounters {
     unsigned int chunk_ticket;       // preprocess chunk ticket
     unsigned long long n_vis64;      // paired Gaussians (two-level order)
     unsigned long long scratch64;    // unused scan total
+    unsigned int n_big;              // two-level order: Gaussians left to k_emit_big
+    unsigned int big_ticket;
     unsigned int sort_ticket[8];     // scatter-pass tickets
     unsigned int sort_epoch;         // bumped once per sort; tags look-back descriptors
     unsigned int pad1[7];
@@ -261,6 +263,7 @@ struct PreprocessArgs {
     const unsigned *dsorted;         // ids in depth order (== dval after the sort)
     unsigned *chunk_hits2;           // pairs per chunk of 256 depth-sorted Gaussians
     unsigned long long *chunk_base2; // exclusive scan of chunk_hits2
+    uint4 *big;                      // (record, request, output base lo, hi) of large Gaussians
     FrameCounters *ctr;
     long long pair_cap;
     long long n_chunks;

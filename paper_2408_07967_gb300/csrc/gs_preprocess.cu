@@ -272,7 +272,13 @@ struct PreSmem {
     unsigned cnt[kPreBlock];          // pairs of each Gaussian of the chunk
     unsigned char req[kPreBlock];     // request of each Gaussian (batch index)
     unsigned wsum[kPreBlock / 32];
+    unsigned long long pbase[kPreBlock];   // depth order: first output position of each Gaussian
+    unsigned run[kPreBlock];               // depth order: hits of each Gaussian written so far
+    unsigned xr[kPreBlock];                // depth order: exclusive hit rank of each slot of a step
 };
+
+// Gaussians with more candidate tiles than this are emitted by k_emit_big, one CTA each.
+constexpr int kBigCand = 1024;
 
 // Candidate slot -> (Gaussian g of the CTA, tile); slot s belongs to the last g with
 // cstart[g] <= s, and is its k-th candidate tile in row-major order.
@@ -543,10 +549,67 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
     } else {
         S.w[tid] = 1;
     }
-    const int ctotal = block_scan_cand(S, ncand);
     const long long cap = A.pair_cap;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long run = DEPTH ? A.chunk_base2[chunk] : A.chunk_base[chunk];
+    if (DEPTH) {
+        // Each Gaussian's pairs start at the chunk base + the pairs of the Gaussians before it in
+        // depth order.  Large Gaussians go to k_emit_big (one CTA each) so that a chunk of
+        // consecutive depth ranks -- where large footprints cluster -- does not serialise them.
+        const unsigned c = in_range ? A.counts[gid] : 0u;
+        unsigned incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) S.wsum[warp] = incl;
+        __syncthreads();
+        unsigned wex = 0;
+        for (int w2 = 0; w2 < warp; ++w2) wex += S.wsum[w2];
+        const unsigned long long pb = A.chunk_base2[chunk] + wex + incl - c;
+        S.pbase[tid] = pb;
+        S.run[tid] = 0;
+        const bool big = ncand > kBigCand;
+        if (big && c > 0) {
+            const unsigned k = atomicAdd(&A.ctr->n_big, 1u);
+            A.big[k] = make_uint4((unsigned)gid, (unsigned)ri, (unsigned)(pb & 0xffffffffu), (unsigned)(pb >> 32));
+        }
+        if (big) ncand = 0;
+        __syncthreads();
+        const int ctotal = block_scan_cand(S, ncand);
+        for (int base = 0; base < ctotal; base += kPreBlock) {
+            const int slot = base + tid;
+            bool hit = false;
+            int g = -1, tile = 0;
+            if (slot < ctotal) hit = slot_test(S, A.B, slot, g, tile);
+            const unsigned bal = __ballot_sync(FULL, hit);
+            if (lane == 0) S.wsum[warp] = __popc(bal);
+            __syncthreads();
+            unsigned wpre = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < kPreBlock / 32; ++w2) wpre += w2 < warp ? S.wsum[w2] : 0u;
+            const unsigned xr = wpre + __popc(bal & lt);      // exclusive hit rank of this slot in the step
+            S.xr[tid] = xr;
+            __syncthreads();
+            if (hit) {
+                const int first = max(S.cstart[g], base) - base;   // g's first slot in this step
+                const unsigned long long pos = S.pbase[g] + S.run[g] + (xr - S.xr[first]);
+                if ((long long)pos < cap) {
+                    A.tkeys[pos] = (unsigned)tile;
+                    A.vals[pos] = S.cnt[g];
+                }
+            }
+            __syncthreads();
+            // advance each Gaussian's running count by its hits in this step
+            const unsigned peers = __match_any_sync(FULL, g);
+            const unsigned hm = bal & peers;
+            if (g >= 0 && hm && lane == __ffs(peers) - 1) atomicAdd(&S.run[g], (unsigned)__popc(hm));
+            __syncthreads();
+        }
+        return;
+    }
+    const int ctotal = block_scan_cand(S, ncand);
+    unsigned long long run = A.chunk_base[chunk];
     for (int base = 0; base < ctotal; base += kPreBlock) {
         const int slot = base + tid;
         bool hit = false;
@@ -565,15 +628,66 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
         if (hit) {
             const unsigned long long pos = run + wpre + __popc(bal & lt);
             if ((long long)pos < cap) {
-                if (DEPTH)
-                    A.tkeys[pos] = (unsigned)tile;
-                else
-                    A.keys[pos] = ((unsigned long long)(unsigned)tile << 32) | S.zb[g];
+                A.keys[pos] = ((unsigned long long)(unsigned)tile << 32) | S.zb[g];
                 A.vals[pos] = S.cnt[g];        // record index of slot g
             }
         }
         run += tot;
         __syncthreads();
+    }
+}
+
+// Depth order, large Gaussians: one CTA per Gaussian (persistent grid, ticketed), its candidate
+// tiles tested 256 at a time, hits written in row-major order from the Gaussian's base.
+__global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ PreprocessArgs A) {
+    __shared__ unsigned s_item, s_w[kPreBlock / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned nbig = *(volatile unsigned *)&A.ctr->n_big;
+    const long long cap = A.pair_cap;
+    while (true) {
+        if (tid == 0) s_item = atomicAdd(&A.ctr->big_ticket, 1u);
+        __syncthreads();
+        const unsigned item = s_item;
+        __syncthreads();
+        if (item >= nbig) break;
+        const uint4 it = A.big[item];
+        const long long rec = it.x;
+        const ReqDesc &R = A.B.r[it.y];
+        unsigned long long run = ((unsigned long long)it.w << 32) | it.z;
+        const float4 g0 = A.geo0[rec], g1 = A.geo1[rec];
+        const int4 g2 = A.geo2[rec];
+        const int ncand = g2.z * g2.w;
+        for (int base = 0; base < ncand; base += kPreBlock) {
+            const int k = base + tid;
+            bool hit = false;
+            int tile = 0;
+            if (k < ncand) {
+                const int dy = k / g2.z;
+                const int tx = g2.x + (k - dy * g2.z), ty = g2.y + dy;
+                tile = R.tile0 + ty * R.cam.tiles_x + tx;
+                hit = test_tile(R.cam, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, ty);
+            }
+            const unsigned bal = __ballot_sync(FULL, hit);
+            if (lane == 0) s_w[warp] = __popc(bal);
+            __syncthreads();
+            unsigned wpre = 0, tot = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
+                const unsigned x = s_w[w2];
+                wpre += w2 < warp ? x : 0u;
+                tot += x;
+            }
+            if (hit) {
+                const unsigned long long pos = run + wpre + __popc(bal & ((1u << lane) - 1u));
+                if ((long long)pos < cap) {
+                    A.tkeys[pos] = (unsigned)tile;
+                    A.vals[pos] = (unsigned)rec;
+                }
+            }
+            run += tot;
+            __syncthreads();
+        }
     }
 }
 
@@ -607,6 +721,14 @@ int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cud
     k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits2, a.chunk_base2, unused_total, nullptr, nullptr, nullptr,
                                             rank_chunks, 1ll << 62, nullptr);
     k_pre_emit<true><<<(unsigned)rank_chunks, kPreBlock, 0, s>>>(a);
+    static int big_grid = 0;
+    if (big_grid == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        big_grid = 4 * sms;
+    }
+    k_emit_big<<<big_grid, kPreBlock, 0, s>>>(a);
     return 4;
 }
 
