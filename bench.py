@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-training", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--no-city", action="store_true")
+    ap.add_argument("--city-steps", type=int, default=64)
+    ap.add_argument("--sort-mode", type=int, default=None, help="force gs_tuning.sort_mode (skips the autotuner)")
+    ap.add_argument("--blend-variant", type=int, default=None, help="force gs_tuning.blend_variant")
     return ap.parse_args()
 
 
@@ -134,6 +138,30 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x):
+    """Largest value of `x` over the ranks of the default process group (the slowest replica sets
+    the whole job's time); a device tensor under NCCL, a host tensor under gloo."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_camera(rank, i, ncam):
+    """Camera index of step i on replica `rank`: each replica walks the camera cycle from its own
+    offset, so the replicas render different frames (independent units, no exchange)."""
+    return (rank * 7 + i) % ncam
+
+
+def job_value(world_size, steps, max_ms):
+    """Whole-job frames/s: frames of all replicas over the slowest replica's timed region."""
+    return world_size * steps / (max_ms / 1000.0)
 
 
 # ------------------------------------------------------------------------------------ reference arm
@@ -233,16 +261,13 @@ def serve_run(gs, srv_kw, scenes, poses, schedule, ring):
     return stats, wall, st
 
 
-def run_serving(args, gs, ctx, room_scene, room_cams):
+def run_serving(args, gs, ctx, room_scene, room_cams, city, city_cams):
     import torch
     from paper_2408_07967_gb300 import synth
-    city_scene, city_cams = synth.load_config("city")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        city = gs.Scene.from_numpy(ctx, city_scene, stream=stream)
         room = gs.Scene.from_numpy(ctx, room_scene, stream=stream)
     stream.synchronize()
-    del city_scene
     scenes, poses = [room, city], [room_cams, city_cams]
     ring = [torch.empty(3 * 3840 * 2160, dtype=torch.float32).pin_memory() for _ in range(16)]
     batched = dict(slots=3, max_batch=8, pair_capacity=(1 << 28), max_gaussians=32_000_000, max_width=3840,
@@ -268,7 +293,6 @@ def run_serving(args, gs, ctx, room_scene, room_cams):
         out[f"{name}@saturated"] = {"frames_per_s": sum(s["status"] == 0 for s in st) / wall,
                                     "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                                     "mean_batch": sst["batched_requests"] / max(1, sst["batches"])}
-    city.close()
     room.close()
     return out
 
@@ -312,73 +336,54 @@ def run_training(args, gs, ctx, room_scene, room_cams, steps=10):
             "grad_finite": bool(all(torch.isfinite(p.grad).all().item() for p in params))}
 
 
-# ------------------------------------------------------------------------------------ our arm
-def run_ours(args):
+# ------------------------------------------------------------------------------------ timed frames
+def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, args, rank=0, sample_clocks=True):
+    """Render `steps` frames (camera cycle), L2 flushed before each, graph replay; per-step CUDA events
+    on the launching stream, per-stage event nodes inside the graph, then the same frames again with
+    the instrumented blend for the evaluation counts.  Returns (result dict, frame, camera of step i)."""
     import numpy as np
     import torch
-
-    ws, rank, local = dist_info()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.cuda.current_device()
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2408_07967_gb300 as gs
-
-    scene, cams, desc = workload(args.config)
-    ctx = gs.Context(dev)
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        sc = gs.Scene.from_numpy(ctx, scene, stream=stream)
-    stream.synchronize()
     W, H = cams[0].width, cams[0].height
-    fr = gs.Frame(ctx, scene.P, pair_capacity(args.config), W, H)
+    fr = gs.Frame(ctx, P, cap, W, H)
     fr.gs_frame_use_graph(True)
-    cache = os.path.join(os.environ.get("XDG_CACHE_HOME", os.path.expanduser("~/.cache")), "gs300_autotune.txt")
-    os.makedirs(os.path.dirname(cache), exist_ok=True)
-    tuning = fr.gs_autotune(sc, cams[:8], cache_path=cache, stream=stream)
+    if args.sort_mode is not None or args.blend_variant is not None:
+        fr.gs_frame_set_tuning(blend_variant=args.blend_variant, sort_mode=args.sort_mode)
+        tuning = fr.gs_frame_get_tuning()
+        tuning["source"] = "forced"
+    else:
+        cache = os.path.join(os.environ.get("XDG_CACHE_HOME", os.path.expanduser("~/.cache")), "gs300_autotune.txt")
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tuning = fr.gs_autotune(dev_scene, cams[:8], cache_path=cache, stream=stream)
+        tuning["source"] = "autotune"
     fr.gs_frame_enable_timing(True)
     rgb = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
     T = torch.empty((H, W), dtype=torch.float32, device="cuda")
     last = torch.empty((H, W), dtype=torch.int32, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ncam = len(cams)
-    cam_of = lambda i: cams[(rank * 7 + i) % ncam]
-
-    def step(i):
-        fr.gs_render(sc, cam_of(i), rgb, T, last, stream=stream)
-
+    cam_of = lambda i: cams[replica_camera(rank, i, ncam)]
     with torch.cuda.stream(stream):
-        for i in range(args.warmup):
+        for i in range(warmup):
             flush.fill_(i & 0xff)
-            step(i)
+            fr.gs_render(dev_scene, cam_of(i), rgb, T, last, stream=stream)
     stream.synchronize()
-
-    # ---- timed region: K steps, L2 flushed before each, per-step device time by CUDA events
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     stage = np.zeros(4)
-    pairs = vis = culled = evals = 0
-    kernels = 0
-    dens = []
-    if ws > 1:
+    pairs = vis = culled = kernels = 0
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clk = ClockSampler(dev)
-    clk.start()
+    clk = ClockSampler(torch.cuda.current_device()) if sample_clocks else None
+    if clk:
+        clk.start()
     wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        for i in range(args.steps):
+        for i in range(steps):
             flush.fill_(i & 0xff)
             ev0[i].record(stream)
-            step(args.warmup + i)
+            fr.gs_render(dev_scene, cam_of(warmup + i), rgb, T, last, stream=stream)
             ev1[i].record(stream)
-            # stage times and counters of this frame (reading them waits for the frame)
-            stage += np.array(fr.gs_frame_stage_ms())
+            stage += np.array(fr.gs_frame_stage_ms())      # waits for the frame
             st = fr.stats(stream)
             pairs += st["pairs"]
             vis += st["visible"]
@@ -388,40 +393,33 @@ def run_ours(args):
                 raise RuntimeError(f"device status {st['status']} at step {i}")
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    clocks = clk.stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    # evaluation counts of the same frames from the instrumented blend (outside the timed region)
+    clocks = clk.stop() if clk else None
+    tot_ms = float(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)))
+    # evaluation counts of the same cameras from the instrumented blend (outside the timed region)
     fr.gs_frame_set_counting(True)
-    contrib = 0
-    ncount = min(args.steps, ncam)
+    evals = contrib = 0
+    ncount = min(steps, ncam)
     with torch.cuda.stream(stream):
         for i in range(ncount):
-            step(args.warmup + i)
+            fr.gs_render(dev_scene, cam_of(warmup + i), rgb, T, last, stream=stream)
             stc = fr.stats(stream)
             evals += stc["evaluations"]
             contrib += stc["contributions"]
     fr.gs_frame_set_counting(False)
-    tot_ms = float(sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        torch.distributed.barrier()
-    value = ws * args.steps / (tot_ms / 1000.0)
-
-    # ---- roofline of the dominant stage
-    peaks = load_peaks()
-    K = args.steps
+    K = steps
     stage_ms = stage / K
-    P = scene.P
     N, V, Pc = pairs / K, vis / K, culled / K
     E, Ec = evals / ncount, contrib / ncount
     passes = st["sort_passes"]
+    peaks = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    sm_mhz = clocks["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
-    alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T ops/s
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
+    alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T lane-ops/s
     pre_bytes = 16 * P + 32 * Pc + 192 * V + 48 * V + 12 * N
-    sort_bytes = 8 * N + passes * 24 * N
+    if tuning.get("sort_mode", 0) == 1:
+        sort_bytes = 4 * N + passes * 16 * N + V * (4 + 4 * 16)     # tile sort (32-bit keys) + depth sort
+    else:
+        sort_bytes = 8 * N + passes * 24 * N
     ntiles = ((W + 15) // 16) * ((H + 15) // 16)
     ranges_bytes = (ntiles + 1) * (4 + 8 * max(1, math.ceil(math.log2(max(N, 2)))))
     blend_ops = Ec * BLEND_OPS_PER_CONTRIB
@@ -439,25 +437,65 @@ def run_ours(args):
         v["frac"] = v["achieved"] / v["peak"]
         for k in ("ms", "achieved", "frac"):
             v[k] = round(v[k], 4)
-    dom = max(("preprocess", "blend"), key=lambda k: per_stage[k]["ms"])
+    dom = max(per_stage, key=lambda k: per_stage[k]["ms"])
     d = per_stage[dom]
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", f"traffic_{dom}_{args.config}.json")
-    if os.path.exists(tr_path):
-        traffic = json.load(open(tr_path)).get("bytes_per_launch")
+    kernel = {"preprocess": "k_pre_count + k_pre_emit", "sort": "k_sort_scatter (all passes)",
+              "ranges": "k_tile_starts", "blend": f"k_blend<variant {tuning.get('blend_variant')}>"}[dom]
+    algo = {"preprocess": "16P + 32 P_culled_in + 240 V + 12 N bytes",
+            "sort": "8N + 24N per pass (64-bit keys) / 4N + 16N per pass + 68V (two-level)",
+            "ranges": "(tiles + 1) x (4 + 8 log2 N) bytes",
+            "blend": f"{BLEND_OPS_PER_CONTRIB} FP32 ops x contributing evaluations (E_c = {Ec:.4g} of "
+                     f"E = {E:.4g} walked per frame)"}[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": traffic, "kernel": f"k_{dom}",
+                "frac": d["frac"], "traffic": None, "kernel": kernel, "stage": dom,
                 "peak_source": ("measured HBM copy (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
                                 f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz median SM clock sampled in this run"),
-                "algorithmic": ("16P + 32P_culled_in + 240V + 12N bytes" if dom == "preprocess" else
-                                f"{BLEND_OPS_PER_CONTRIB} FP32 ops x contributing evaluations "
-                                f"(E_c = {Ec:.4g} of E = {E:.4g} walked per frame)")}
+                "algorithmic": algo}
+    res = {"frames": K, "ms_total": tot_ms, "frames_per_s": K / (tot_ms / 1000.0), "ms_per_frame": tot_ms / K,
+           "wall_s": wall, "clocks": clocks, "gpu_launches": kernels, "tuning": tuning, "roofline": roofline,
+           "stages": per_stage, "frame": {"pairs": N, "visible": V, "culled_in": Pc, "evaluations": E,
+                                          "contributions": Ec, "sort_passes": passes,
+                                          "pairs_per_s": N * K / (tot_ms / 1000.0)}}
+    return res, fr, cam_of
 
-    # ---- end to end through the host-buffer entry point
+
+# ------------------------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2408_07967_gb300 as gs
+    from paper_2408_07967_gb300 import synth
+
+    scene, cams, desc = workload(args.config)
+    ctx = gs.Context(dev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sc = gs.Scene.from_numpy(ctx, scene, stream=stream)
+    stream.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    main, fr, cam_of = time_frames(gs, ctx, sc, scene.P, cams, args.steps, args.warmup, stream, flush,
+                                   pair_capacity(args.config), args, rank)
+    tot_ms = max_over_ranks(main["ms_total"])
+    if ws > 1:
+        torch.distributed.barrier()
+    value = job_value(ws, args.steps, tot_ms)
+    W, H = cams[0].width, cams[0].height
+
+    # ---- end to end through the host-buffer entry point (camera in, image out to pinned memory)
     e2e = None
     if not args.no_e2e:
         rgb_h = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
-        Ke = min(K, 300)
+        Ke = min(args.steps, 300)
         stream.synchronize()
         t0 = time.perf_counter()
         for i in range(Ke):
@@ -467,31 +505,42 @@ def run_ours(args):
         e2e = {"value": ws * Ke / dte, "unit": "frames/s", "h2d_bytes_per_step": 80,
                "d2h_bytes_per_step": 3 * H * W * 4, "steps": Ke,
                "note": "camera (80 B) passed by value into the kernels; rgb copied to pinned host memory"}
+    fr.close()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, scene, cams)
-    fr.close()
-    serving = training = None
+
+    city = city_res = city_cams = None
+    if rank == 0 and args.config == "room" and not (args.no_city and args.no_serving):
+        city_scene, city_cams = synth.load_config("city")
+        with torch.cuda.stream(stream):
+            city = gs.Scene.from_numpy(ctx, city_scene, stream=stream)
+        stream.synchronize()
+        if not args.no_city:
+            res, cfr, _ = time_frames(gs, ctx, city, city_scene.P, city_cams, args.city_steps, 3, stream, flush,
+                                      pair_capacity("city"), args, rank, sample_clocks=True)
+            cfr.close()
+            city_res = dict(workload="city-scale 10M Gaussians @3840x2160, 16 aerial + 16 street cameras "
+                                     "(synthetic, seed 2)", **res)
+        del city_scene
+    training = serving = None
     if rank == 0 and not args.no_training and args.config == "room":
         training = run_training(args, gs, ctx, scene, cams)
     if rank == 0 and not args.no_serving and args.config == "room":
-        serving = run_serving(args, gs, ctx, scene, cams)
+        serving = run_serving(args, gs, ctx, scene, cams, city, city_cams)
 
     if rank == 0:
-        line = {"metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": ws, "steps": K,
-                "warmup": args.warmup, "ms_per_step": tot_ms / K, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        line = {"metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": desc, "l2": "flushed (256 MiB write) before every step",
-                           "camera_cycle": ncam, "graph": True, "parallelism": f"replicas x{ws}",
-                           "tuning": tuning},
-                "clocks": clocks, "gpu_launches": kernels,
-                "roofline": roofline, "stages": per_stage,
-                "frame": {"pairs": N, "visible": V, "culled_in": Pc, "evaluations": E, "contributions": Ec,
-                          "sort_passes": passes,
-                          "pairs_per_s": N * value / ws},
-                "wall_s": wall, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
-                "differentiable": training}
+                           "camera_cycle": len(cams), "graph": True, "parallelism": f"replicas x{ws}",
+                           "tuning": main["tuning"]},
+                "clocks": main["clocks"], "gpu_launches": main["gpu_launches"],
+                "roofline": main["roofline"], "stages": main["stages"], "frame": main["frame"],
+                "wall_s": main["wall_s"], "e2e": e2e, "cpu_baseline": cpu, "city_4k": city_res,
+                "serving": serving, "differentiable": training}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
