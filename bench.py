@@ -337,7 +337,19 @@ def run_training(args, gs, ctx, room_scene, room_cams, steps=10):
 
 
 # ------------------------------------------------------------------------------------ timed frames
-def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, args, rank=0, sample_clocks=True):
+def measure_alu(gs, dev):
+    """FP32 FMA and ex2 rates from the library's probe kernels, with the SM clock they ran at."""
+    clk = ClockSampler(dev)
+    clk.start()
+    r = gs.gs_measure_alu_peaks(dev, 300.0)
+    c = clk.stop()
+    r["sm_mhz"] = c.get("sm_mhz")
+    r["reasons"] = c.get("reasons")
+    return r
+
+
+def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, args, rank=0, sample_clocks=True,
+                alu=None):
     """Render `steps` frames (camera cycle), L2 flushed before each, graph replay; per-step CUDA events
     on the launching stream, per-stage event nodes inside the graph, then the same frames again with
     the instrumented blend for the evaluation counts.  Returns (result dict, frame, camera of step i)."""
@@ -394,7 +406,9 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks = clk.stop() if clk else None
-    tot_ms = float(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)))
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    tot_ms = float(sum(step_ms))
+    med_ms = float(statistics.median(step_ms))
     # evaluation counts of the same cameras from the instrumented blend (outside the timed region)
     fr.gs_frame_set_counting(True)
     evals = contrib = 0
@@ -414,7 +428,15 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
     peaks = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
-    alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T lane-ops/s
+    if alu and alu.get("fma_tops"):
+        # measured FMA rate, scaled to the SM clock of this timed region when the probe ran at another
+        probe_mhz = alu.get("sm_mhz") or sm_mhz
+        alu_peak = alu["fma_tops"] * (sm_mhz / probe_mhz)
+        alu_src = (f"measured FP32 FMA probe: {alu['fma_tops']:.2f} T lane-ops/s at {probe_mhz:.0f} MHz, "
+                   f"scaled to the {sm_mhz:.0f} MHz median SM clock of this run")
+    else:
+        alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T lane-ops/s
+        alu_src = f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz median SM clock sampled in this run"
     pre_bytes = 16 * P + 32 * Pc + 192 * V + 48 * V + 12 * N
     if tuning.get("sort_mode", 0) == 1:
         sort_bytes = 4 * N + passes * 16 * N + V * (4 + 4 * 16)     # tile sort (32-bit keys) + depth sort
@@ -448,10 +470,10 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
                      f"E = {E:.4g} walked per frame)"}[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": None, "kernel": kernel, "stage": dom,
-                "peak_source": ("measured HBM copy (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
-                                f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz median SM clock sampled in this run"),
+                "peak_source": ("measured HBM copy (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else alu_src),
                 "algorithmic": algo}
     res = {"frames": K, "ms_total": tot_ms, "frames_per_s": K / (tot_ms / 1000.0), "ms_per_frame": tot_ms / K,
+           "ms_median": med_ms, "frames_per_s_median": 1000.0 / med_ms,
            "wall_s": wall, "clocks": clocks, "gpu_launches": kernels, "tuning": tuning, "roofline": roofline,
            "stages": per_stage, "frame": {"pairs": N, "visible": V, "culled_in": Pc, "evaluations": E,
                                           "contributions": Ec, "sort_passes": passes,
@@ -483,8 +505,9 @@ def run_ours(args):
         sc = gs.Scene.from_numpy(ctx, scene, stream=stream)
     stream.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    alu = measure_alu(gs, dev)
     main, fr, cam_of = time_frames(gs, ctx, sc, scene.P, cams, args.steps, args.warmup, stream, flush,
-                                   pair_capacity(args.config), args, rank)
+                                   pair_capacity(args.config), args, rank, alu=alu)
     tot_ms = max_over_ranks(main["ms_total"])
     if ws > 1:
         torch.distributed.barrier()
@@ -519,7 +542,7 @@ def run_ours(args):
         stream.synchronize()
         if not args.no_city:
             res, cfr, _ = time_frames(gs, ctx, city, city_scene.P, city_cams, args.city_steps, 3, stream, flush,
-                                      pair_capacity("city"), args, rank, sample_clocks=True)
+                                      pair_capacity("city"), args, rank, alu=alu)
             cfr.close()
             city_res = dict(workload="city-scale 10M Gaussians @3840x2160, 16 aerial + 16 street cameras "
                                      "(synthetic, seed 2)", **res)
@@ -537,7 +560,7 @@ def run_ours(args):
                 "config": {"workload": desc, "l2": "flushed (256 MiB write) before every step",
                            "camera_cycle": len(cams), "graph": True, "parallelism": f"replicas x{ws}",
                            "tuning": main["tuning"]},
-                "clocks": main["clocks"], "gpu_launches": main["gpu_launches"],
+                "clocks": main["clocks"], "gpu_launches": main["gpu_launches"], "alu_peaks": alu,
                 "roofline": main["roofline"], "stages": main["stages"], "frame": main["frame"],
                 "wall_s": main["wall_s"], "e2e": e2e, "cpu_baseline": cpu, "city_4k": city_res,
                 "serving": serving, "differentiable": training}

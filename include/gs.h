@@ -116,8 +116,9 @@ gs_status gs_context_create(int32_t device, gs_context **out);
 gs_status gs_context_destroy(gs_context *ctx);
 
 /* Device-resident scene: copies the canonical arrays in `g` into the library's internal
-   structure-of-arrays layout (16-byte vectors per Gaussian: position+opacity, scale,
-   quaternion, and twelve SH planes), enqueued on `stream`.  The input arrays may be freed
+   layout (272 bytes per Gaussian: a dense plane of position+opacity, read by the cull of every
+   Gaussian, and a 256-byte body of scale, quaternion and the 48 SH floats, read only for
+   Gaussians that pass the cull or are paired), enqueued on `stream`.  The input arrays may be freed
    once the stream has passed this call.  Section 5.3.1 (per-scene work done once).
    Errors: GS_ERR_INVALID_ARG (NULL pointers, P <= 0, P >= 2^31, bad degree), GS_ERR_OOM. */
 gs_status gs_scene_create(gs_context *ctx, const gs_gaussians *g, gs_stream stream, gs_scene **out);
@@ -239,6 +240,25 @@ gs_status gs_frame_get_tuning(const gs_frame *frame, gs_tuning *tuning);
    unreadable or unwritable cache file is ignored. */
 gs_status gs_autotune(gs_frame *frame, const gs_scene *scene, const gs_camera *cams, int32_t ncams,
                       const gs_render_opts *opts, const char *cache_path, gs_tuning *out, gs_stream stream);
+
+/* Measured arithmetic throughput of a device, the denominator of the blend stage's roofline (the
+   blend is bound by FP32 and special-function work, and neither rate is a published measured
+   figure).  Two probe kernels run on every SM at full occupancy: one issues independent chains of
+   FP32 fused multiply-adds (one lane-operation each), the other independent chains of ex2.approx.
+   Each runs about `target_ms` milliseconds (<= 0: 200 ms) after a warm-up, timed with CUDA events
+   on a private stream; the result is lane-operations per second / 1e12 and the elapsed time of each
+   probe.  The paper has no counterpart (it reports no roofline).  Synchronous; allocates a 4 KiB
+   buffer for the probes' sinks.  Errors: GS_ERR_INVALID_ARG (NULL out), GS_ERR_NO_DEVICE,
+   GS_ERR_CUDA. */
+typedef struct {
+    double fma_tops;     /* FP32 FMA lane-operations per second / 1e12 */
+    double ex2_tops;     /* ex2.approx.ftz.f32 results per second / 1e12 */
+    double fma_ms;       /* duration of the timed FMA probe */
+    double ex2_ms;       /* duration of the timed ex2 probe */
+    int32_t sm_count;
+    int32_t pad;
+} gs_alu_peaks;
+gs_status gs_measure_alu_peaks(int32_t device, double target_ms, gs_alu_peaks *out);
 
 /* Enables (1) or disables (0) the instrumented blend that counts, per frame, the (pixel, entry)
    pairs walked before early stop and those passing q <= t (gs_frame_stats.evaluations /

@@ -106,7 +106,7 @@ class Context:
 
 
 class Scene:
-    """gs_scene: device-resident Gaussians (packed into the library's SoA layout)."""
+    """gs_scene: device-resident Gaussians (packed into a position plane and 256-byte bodies)."""
 
     def __init__(self, ctx: Context, means, scales, quats, opacity, sh, sh_degree=3, activated=True, stream=None):
         self.ctx = ctx
@@ -369,6 +369,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def gs_measure_alu_peaks(device: int = 0, target_ms: float = 200.0) -> dict:
+    """Measured FP32 FMA and ex2.approx throughput (lane-operations/s / 1e12) of a device."""
+    out = _native.gs_alu_peaks()
+    _check(lib().gs_measure_alu_peaks(int(device), float(target_ms), C.byref(out)))
+    return {"fma_tops": out.fma_tops, "ex2_tops": out.ex2_tops, "fma_ms": out.fma_ms, "ex2_ms": out.ex2_ms,
+            "sm_count": out.sm_count}
 
 
 def gs_sort_pairs(ctx: Context, keys, vals, end_bit: int = 64, stream=None):

@@ -59,6 +59,11 @@ class gs_tuning(C.Structure):
     _fields_ = [("blend_variant", C.c_int32), ("sort_mode", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
+class gs_alu_peaks(C.Structure):
+    _fields_ = [("fma_tops", C.c_double), ("ex2_tops", C.c_double), ("fma_ms", C.c_double), ("ex2_ms", C.c_double),
+                ("sm_count", C.c_int32), ("pad", C.c_int32)]
+
+
 _vp = C.c_void_p
 _pp = C.POINTER(C.c_void_p)
 _st = C.c_int32
@@ -92,6 +97,7 @@ PROTOTYPES = {
     "gs_autotune": (_st, [_vp, _vp, _vp, C.c_int32, C.POINTER(gs_render_opts), C.c_char_p, C.POINTER(gs_tuning),
                           _vp]),
     "gs_frame_stage_ms": (_st, [_vp, C.POINTER(C.c_float)]),
+    "gs_measure_alu_peaks": (_st, [C.c_int32, C.c_double, C.POINTER(gs_alu_peaks)]),
     "gs_render_host": (_st, [_vp, _vp, C.POINTER(gs_camera), C.POINTER(gs_render_opts), _vp, _vp, _vp, _vp]),
     "gs_frame_get_stats": (_st, [_vp, C.POINTER(gs_frame_stats), _vp]),
     "gs_frame_pairs": (_st, [_vp, C.c_int32, _vp, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),

@@ -100,7 +100,7 @@ struct gs_scene {
     int sh_degree = 3;
     int activated = 1;
     void *mem = nullptr;
-    float4 *pos_opa = nullptr, *scale = nullptr, *quat = nullptr, *sh = nullptr;
+    float4 *pos_opa = nullptr, *body = nullptr;
 };
 
 struct gs_frame {
@@ -227,17 +227,15 @@ gs_status gs_scene_create(gs_context *ctx, const gs_gaussians *g, gs_stream stre
     s->ctx = ctx;
     s->device = ctx->device;
     s->P = g->P;
-    size_t planes = 3 + kShPlanes;
-    cudaError_t e = cudaMalloc(&s->mem, planes * (size_t)g->P * sizeof(float4));
+    // bodies first (256-byte aligned by cudaMalloc), then the position plane
+    cudaError_t e = cudaMalloc(&s->mem, (size_t)(kBody + 1) * (size_t)g->P * sizeof(float4));
     if (e != cudaSuccess) {
         delete s;
         return cuda_fail(e, "cudaMalloc(scene)");
     }
     float4 *base = (float4 *)s->mem;
-    s->pos_opa = base;
-    s->scale = base + g->P;
-    s->quat = base + 2 * g->P;
-    s->sh = base + 3 * g->P;
+    s->body = base;
+    s->pos_opa = base + (size_t)kBody * g->P;
     st = gs_scene_update(s, g, stream);
     if (st) {
         cudaFree(s->mem);
@@ -255,7 +253,7 @@ gs_status gs_scene_update(gs_scene *s, const gs_gaussians *g, gs_stream stream) 
     if (g->P != s->P) return fail(GS_ERR_INVALID_ARG, "P changed (%lld != %lld)", (long long)g->P, s->P);
     s->sh_degree = g->sh_degree;
     s->activated = g->activated ? 1 : 0;
-    launch_pack_scene(*g, s->pos_opa, s->scale, s->quat, s->sh, (cudaStream_t)stream);
+    launch_pack_scene(*g, s->pos_opa, s->body, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -463,9 +461,7 @@ static gs_status make_cam(const gs_camera *cam, Cam &c) {
 static SceneView view_of(const gs_scene *s) {
     SceneView v;
     v.pos_opa = s->pos_opa;
-    v.scale = s->scale;
-    v.quat = s->quat;
-    v.sh = s->sh;
+    v.body = s->body;
     v.P = s->P;
     v.sh_degree = s->sh_degree;
     v.activated = s->activated;
@@ -998,9 +994,7 @@ extern "C" gs_status gs_render_backward(gs_frame *f, const gs_scene *s, const fl
     a.opt = f->opt;
     a.cam = f->cam;
     a.scene.pos_opa = s->pos_opa;
-    a.scene.scale = s->scale;
-    a.scene.quat = s->quat;
-    a.scene.sh = s->sh;
+    a.scene.body = s->body;
     a.scene.P = s->P;
     a.scene.sh_degree = s->sh_degree;
     a.scene.activated = s->activated;

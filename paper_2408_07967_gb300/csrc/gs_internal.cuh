@@ -15,7 +15,7 @@
 namespace gs {
 
 constexpr int kTile = 16;            // 16x16-pixel tiles (Section 2.2)
-constexpr int kShPlanes = 12;        // 48 SH floats as twelve float4 planes
+constexpr int kShPlanes = 12;        // 48 SH floats as twelve float4
 
 // device-side status bits, collected in FrameCounters::status
 enum : unsigned { kStPairOverflow = 1u, kStTimeout = 2u };
@@ -40,16 +40,21 @@ struct Opts {
     int cap_3sigma, clamp_fov;
 };
 
-// Internal structure-of-arrays scene, one 16-byte vector per Gaussian per plane.
+// Internal scene layout.  pos_opa is a dense plane (one float4 per Gaussian) read by the cull of
+// every Gaussian; everything else of Gaussian i is one 256-byte body at body[kBody * i]:
+//   [0] (sx, sy, sz, 0) or log-scales   [1] quaternion (w, x, y, z)
+//   [2 + k] SH floats 4k .. 4k+3, k < kShPlanes   [14], [15] zero padding
+// so a Gaussian that passes the cull costs one 64-byte DRAM burst for its scale and rotation, and
+// one that is paired three more for its colour, however sparse the visible set is.
+constexpr int kBody = 16;
 struct SceneView {
     const float4 *pos_opa;   // (x, y, z, opacity or logit)
-    const float4 *scale;     // (sx, sy, sz, 0) or log-scales
-    const float4 *quat;      // (w, x, y, z)
-    const float4 *sh;        // kShPlanes planes of P float4: plane k = SH floats 4k .. 4k+3
+    const float4 *body;      // P bodies of kBody float4, 256-byte aligned
     int64_t P;
     int sh_degree;
     int activated;
 };
+__device__ __forceinline__ const float4 *body_of(const SceneView &S, long long gid) { return S.body + gid * kBody; }
 
 // Render record of a paired Gaussian (48 bytes, three float4):
 //   r0 = (u, v, a, b2)   centre and conic, b2 = 2 b
@@ -225,6 +230,62 @@ __device__ __forceinline__ bool tile_hits(float u, float v, float a, float b, fl
     return false;
 }
 
+// The exact test of a run of n <= 32 consecutive tiles tx_begin .. tx_begin+n-1 of tile row ty,
+// bit j of the result for tile tx_begin + j.  Every sub-test evaluates the same binary32
+// operations on the same operands as tile_hits, so each bit equals tile_hits of that tile; the
+// quantities that depend only on the row (the top and bottom edge chords) are formed once, and the
+// side chord at x = 16 (tx + 1) is shared by the right edge of tile tx and the left edge of tile
+// tx + 1.
+__device__ __forceinline__ bool chord_eval(float A, float B, float D, float lo, float hi) {
+    float e1 = fadd(fmul(A, lo), B);
+    float e2 = fadd(fmul(A, hi), B);
+    bool left = (e1 <= 0.0f) || (fmul(e1, e1) <= D);
+    bool right = (e2 >= 0.0f) || (fmul(e2, e2) <= D);
+    return left && right;
+}
+
+__device__ __forceinline__ bool side_hits(float u, float a, float b, float c, float t, float x, float loy,
+                                          float hiy) {
+    const float dx = fsub(x, u);
+    const float B = fmul(b, dx);
+    const float C = fsub(fmul(fmul(a, dx), dx), t);
+    const float D = fsub(fmul(B, B), fmul(c, C));
+    if (!(D >= 0.0f)) return false;
+    return chord_eval(c, B, D, loy, hiy);
+}
+
+__device__ __forceinline__ unsigned run_hits(int W, int H, float u, float v, float a, float b, float c, float t,
+                                             int tx_begin, int n, int ty) {
+    const float y0 = (float)(16 * ty), y1 = (float)min(16 * ty + 16, H);
+    const bool cy = y0 <= v && v <= y1;
+    const float dyt = fsub(y0, v), dyb = fsub(y1, v);
+    const float Bt = fmul(b, dyt), Ct = fsub(fmul(fmul(c, dyt), dyt), t);
+    const float Bb = fmul(b, dyb), Cb = fsub(fmul(fmul(c, dyb), dyb), t);
+    const float Dt = fsub(fmul(Bt, Bt), fmul(a, Ct));
+    const float Db = fsub(fmul(Bb, Bb), fmul(a, Cb));
+    const bool top = Dt >= 0.0f, bot = Db >= 0.0f;
+    const float loy = dyt, hiy = dyb;
+    unsigned mask = 0;
+    bool have = false, cached = false;        // side chord at the current tile's left edge
+    for (int j = 0; j < n; ++j) {
+        const int tx = tx_begin + j;
+        const float x0 = (float)(16 * tx), x1 = (float)min(16 * tx + 16, W);
+        bool h = cy && x0 <= u && u <= x1;
+        const float lo = fsub(x0, u), hi = fsub(x1, u);
+        if (!h && top) h = chord_eval(a, Bt, Dt, lo, hi);
+        if (!h && bot) h = chord_eval(a, Bb, Db, lo, hi);
+        if (!h) h = have ? cached : side_hits(u, a, b, c, t, x0, loy, hiy);
+        have = false;
+        if (!h) {
+            cached = side_hits(u, a, b, c, t, x1, loy, hiy);
+            have = true;
+            h = cached;
+        }
+        mask |= (unsigned)h << j;
+    }
+    return mask;
+}
+
 // Pixel-area rectangle of tile (tx, ty), clipped to the image.
 __device__ __forceinline__ void tile_rect(const Cam &cam, int tx, int ty, float &x0, float &x1,
                                           float &y0, float &y1) {
@@ -269,8 +330,7 @@ struct PreprocessArgs {
     long long n_chunks;
 };
 
-void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *scale, float4 *quat, float4 *sh,
-                       cudaStream_t s);
+void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *body, cudaStream_t s);
 void launch_pre_count(const PreprocessArgs &a, cudaStream_t s);
 void launch_req_pairs(const PreprocessArgs &a, unsigned long long *out, cudaStream_t s);
 void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted);

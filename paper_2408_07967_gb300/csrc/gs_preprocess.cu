@@ -2,20 +2,24 @@
 // (Algorithm 4 of FlashGS, with the exact tile test of Algorithm 3 and Eq. 9, the opacity-aware
 // threshold of Eq. 2-3 and the tight bounding box of Section 4.1).
 //
-// Three kernels over chunks of 256 consecutive Gaussians:
+// Kernels over chunks of 256 consecutive Gaussians:
 //   k_pre_count  each thread culls and projects its Gaussian and finds its candidate tiles (tight
-//                box); then the exact tile tests run load-balanced over the whole CTA: a block
-//                scan of the candidate counts numbers every (Gaussian, candidate tile) slot, and
-//                each step the 256 threads test 256 consecutive slots, whatever Gaussians they
-//                belong to.  This generalises the paper's size-aware remapping of a large ellipse
-//                onto a warp (Section 5.1.2) to any mix of sizes.  It writes the chunk's hit
-//                count, the geometry of paired Gaussians, and their render records with the SH
-//                colour (Algorithm 4, last step: colour only for Gaussians that are used);
-//   k_pre_scan   exclusive scan of the chunk hit counts (one CTA);
-//   k_pre_emit   repeats the tests and writes every hit at its chunk's base + its rank in slot
+//                box); then the exact tile tests run load-balanced over the whole CTA: the
+//                candidate box of every Gaussian is cut into units (runs of up to 8 tiles of one
+//                tile row), a block scan numbers the units of the chunk, and each step the 256
+//                threads take 256 consecutive units, whatever Gaussians they belong to, testing a
+//                unit's tiles with the row's shared terms formed once (run_hits).  This
+//                generalises the paper's size-aware remapping of a large ellipse onto a warp
+//                (Section 5.1.2) to any mix of sizes.  It writes the chunk's hit count, the
+//                geometry of paired Gaussians, and their render records with the SH colour
+//                (Algorithm 4, last step: colour only for Gaussians that are used);
+//   k_chunk_scan exclusive scan of the chunk hit counts (one CTA);
+//   k_pre_emit   repeats the tests and writes every hit at its chunk's base + its rank in unit
 //                order, so pairs land in (Gaussian id, tile row-major) order -- deterministic,
 //                unlike the paper's atomicAdd slots, and without any inter-CTA waiting, so a
 //                chunk holding a huge Gaussian delays nobody else.
+// The depth-ordered variant (k_vis_compact, k_emit_sum, k_pre_emit<true>, k_emit_big) emits the
+// same pairs Gaussian by Gaussian in depth order for the two-level sort.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -26,35 +30,38 @@ constexpr int kPackBlock = 128;
 int preprocess_chunk() { return kPreBlock; }
 
 // ------------------------------------------------------------------------------------------ pack
-// Canonical AoS arrays -> internal SoA float4 planes.  The SH block of a CTA is staged through
-// shared memory so that both the AoS reads and the plane writes are coalesced.
-__global__ void __launch_bounds__(kPackBlock) k_pack_scene(gs_gaussians g, float4 *pos_opa, float4 *scale,
-                                                           float4 *quat, float4 *sh) {
-    __shared__ float s_sh[kPackBlock * 48];
+// Canonical AoS arrays -> the internal position plane and 256-byte bodies.  A CTA assembles its
+// 128 bodies in shared memory (the SH block read coalesced) and writes them as one contiguous,
+// coalesced 32 KiB run.
+__global__ void __launch_bounds__(kPackBlock) k_pack_scene(gs_gaussians g, float4 *pos_opa, float4 *body) {
+    __shared__ float4 s_body[kPackBlock * kBody];
+    float *sb = reinterpret_cast<float *>(s_body);
     const long long base = (long long)blockIdx.x * kPackBlock;
     const int n = (int)min((long long)kPackBlock, g.P - base);
     const float *src = g.sh + base * 48;
-    for (int k = threadIdx.x; k < n * 48; k += kPackBlock) s_sh[k] = src[k];
-    __syncthreads();
+    for (int k = threadIdx.x; k < n * 48; k += kPackBlock) {
+        const int gi = k / 48, r = k - gi * 48;
+        sb[gi * 4 * kBody + 8 + r] = src[k];
+    }
     const long long i = base + threadIdx.x;
     if (threadIdx.x < n) {
         const float *m = g.means + 3 * i;
         const float *s = g.scales + 3 * i;
         const float *q = g.quats + 4 * i;
         pos_opa[i] = make_float4(m[0], m[1], m[2], g.opacity[i]);
-        scale[i] = make_float4(s[0], s[1], s[2], 0.0f);
-        quat[i] = make_float4(q[0], q[1], q[2], q[3]);
-        const float *c = s_sh + threadIdx.x * 48;
-#pragma unroll
-        for (int k = 0; k < kShPlanes; ++k)
-            sh[(long long)k * g.P + i] = make_float4(c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
+        s_body[threadIdx.x * kBody] = make_float4(s[0], s[1], s[2], 0.0f);
+        s_body[threadIdx.x * kBody + 1] = make_float4(q[0], q[1], q[2], q[3]);
+        s_body[threadIdx.x * kBody + 2 + kShPlanes] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_body[threadIdx.x * kBody + 3 + kShPlanes] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    __syncthreads();
+    float4 *dst = body + base * kBody;
+    for (int k = threadIdx.x; k < n * kBody; k += kPackBlock) dst[k] = s_body[k];
 }
 
-void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *scale, float4 *quat, float4 *sh,
-                       cudaStream_t s) {
+void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *body, cudaStream_t s) {
     long long blocks = (g.P + kPackBlock - 1) / kPackBlock;
-    k_pack_scene<<<(unsigned)blocks, kPackBlock, 0, s>>>(g, pos_opa, scale, quat, sh);
+    k_pack_scene<<<(unsigned)blocks, kPackBlock, 0, s>>>(g, pos_opa, body);
 }
 
 // ------------------------------------------------------------------------------------------ SH
@@ -91,23 +98,23 @@ __device__ __forceinline__ void sh_colour(const SceneView &S, long long gid, con
     Y[15] = -K3a * x * (xx - 3.0f * yy);
     const int deg = S.sh_degree;
     const int ncoef = (deg + 1) * (deg + 1);
-    float f[48];
     const int nplanes = (3 * ncoef + 3) / 4;
+    // SH float f = 3 i + ch belongs to coefficient i of channel ch; each channel accumulates in
+    // ascending i as the planes stream in (float4 k holds floats 4k .. 4k+3)
+    const float4 *src = body_of(S, gid) + 2;
+    float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int k = 0; k < kShPlanes; ++k) {
-        float4 v = k < nplanes ? __ldg(S.sh + (long long)k * S.P + gid) : make_float4(0.f, 0.f, 0.f, 0.f);
-        f[4 * k] = v.x;
-        f[4 * k + 1] = v.y;
-        f[4 * k + 2] = v.z;
-        f[4 * k + 3] = v.w;
+        const float4 v = k < nplanes ? __ldg(src + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int f = 4 * k + j, i = f / 3, ch = f - 3 * (f / 3);
+            acc[ch] += (i < ncoef ? Y[i] : 0.0f) * e[j];
+        }
     }
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) acc += (i < ncoef ? Y[i] : 0.0f) * f[3 * i + ch];
-        rgb[ch] = fmaxf(acc + 0.5f, 0.0f);
-    }
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch] + 0.5f, 0.0f);
 }
 
 // ------------------------------------------------------------------------------------------ geometry
@@ -139,14 +146,14 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
     float t = t_full;
     if (o.cap_3sigma && t > 9.0f) t = 9.0f;
     // Sigma = R_q diag(s^2) R_q^T
-    const float4 sc = __ldg(S.scale + gid);
+    const float4 sc = __ldg(body_of(S, gid));
     float s0 = sc.x, s1 = sc.y, s2 = sc.z;
     if (!S.activated) {
         s0 = exp_rn(s0);
         s1 = exp_rn(s1);
         s2 = exp_rn(s2);
     }
-    const float4 q4 = __ldg(S.quat + gid);
+    const float4 q4 = __ldg(body_of(S, gid) + 1);
     float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
     float n2 = fmul(qw, qw);
     n2 = fadd(n2, fmul(qx, qx));
@@ -256,13 +263,6 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
     return true;
 }
 
-__device__ __forceinline__ bool test_tile(const Cam &cam, float u, float v, float a, float b, float c, float t,
-                                          int tx, int ty) {
-    float x0, x1, y0, y1;
-    tile_rect(cam, tx, ty, x0, x1, y0, y1);
-    return tile_hits(u, v, a, b, c, t, x0, x1, y0, y1);
-}
-
 // ------------------------------------------------------------------------------------------ kernels
 struct PreSmem {
     float u[kPreBlock], v[kPreBlock], a[kPreBlock], b[kPreBlock], c[kPreBlock], t[kPreBlock];
@@ -280,9 +280,26 @@ struct PreSmem {
 // Gaussians with more candidate tiles than this are emitted by k_emit_big, one CTA each.
 constexpr int kBigCand = 1024;
 
-// Candidate slot -> (Gaussian g of the CTA, tile); slot s belongs to the last g with
-// cstart[g] <= s, and is its k-th candidate tile in row-major order.
-__device__ __forceinline__ bool slot_test(const PreSmem &S, const BatchDesc &B, int slot, int &g_out, int &tile) {
+// Work unit of the exact tests: a run of up to kSeg consecutive candidate tiles of one tile row
+// of one Gaussian (row-major), tested by one thread with the row's shared terms (run_hits).
+constexpr int kSeg = 8;
+
+// Emission stages each step's hits (tile id and Gaussian slot, in output order) in shared memory
+// and then writes them as consecutive runs, so global stores are coalesced.
+struct EmitSmem {
+    PreSmem P;
+    unsigned stile[kPreBlock * kSeg];
+    unsigned char sg[kPreBlock * kSeg];
+};
+__device__ __forceinline__ int units_of(int w, int h) { return h * ((w + kSeg - 1) / kSeg); }
+
+struct Unit {
+    int g, tx, ty, n;
+};
+
+// Unit slot -> (Gaussian g of the CTA, first tile, row, length); slot s belongs to the last g with
+// cstart[g] <= s and is its k-th unit in row-major order.
+__device__ __forceinline__ Unit unit_of(const PreSmem &S, int slot) {
     int lo = 0, hi = kPreBlock - 1;
 #pragma unroll
     for (int it = 0; it < 8; ++it) {
@@ -292,15 +309,46 @@ __device__ __forceinline__ bool slot_test(const PreSmem &S, const BatchDesc &B, 
         else
             hi = mid - 1;
     }
-    const int g = lo;
-    const int k = slot - S.cstart[g];
-    const int w = S.w[g];
-    const int dy = k / w;
-    const int tx = S.tx0[g] + (k - dy * w), ty = S.ty0[g] + dy;
-    const ReqDesc &R = B.r[S.req[g]];
-    g_out = g;
-    tile = R.tile0 + ty * R.cam.tiles_x + tx;     // global tile id of the batch
-    return test_tile(R.cam, S.u[g], S.v[g], S.a[g], S.b[g], S.c[g], S.t[g], tx, ty);
+    Unit U;
+    U.g = lo;
+    const int k = slot - S.cstart[lo];
+    const int w = S.w[lo];
+    const int segs = (w + kSeg - 1) / kSeg;
+    const int dy = k / segs;
+    const int seg = k - dy * segs;
+    U.tx = S.tx0[lo] + seg * kSeg;
+    U.ty = S.ty0[lo] + dy;
+    U.n = min(kSeg, w - seg * kSeg);
+    return U;
+}
+
+__device__ __forceinline__ unsigned unit_hits(const PreSmem &S, const BatchDesc &B, const Unit &U) {
+    const Cam &cam = B.r[S.req[U.g]].cam;
+    return run_hits(cam.W, cam.H, S.u[U.g], S.v[U.g], S.a[U.g], S.b[U.g], S.c[U.g], S.t[U.g], U.tx, U.n, U.ty);
+}
+
+// Block exclusive scan of one unsigned per thread (uses S.wsum); returns the exclusive prefix and
+// writes the block total to *total.
+__device__ __forceinline__ unsigned block_excl(PreSmem &S, unsigned x, unsigned *total) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) S.wsum[warp] = incl;
+    __syncthreads();
+    unsigned wex = 0, tot = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
+        const unsigned y = S.wsum[w2];
+        wex += w2 < warp ? y : 0u;
+        tot += y;
+    }
+    __syncthreads();
+    *total = tot;
+    return wex + incl - x;
 }
 
 // Block exclusive scan of one int per thread into S.cstart; returns the block total.
@@ -330,7 +378,7 @@ __device__ __forceinline__ int block_scan_cand(PreSmem &S, int ncand) {
 // Pass 1: geometry, exact tests counted over all candidate tiles of the chunk (load-balanced),
 // render records of paired Gaussians, the chunk's pair count, and each paired Gaussian's
 // geometry for pass 3.
-__global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constant__ PreprocessArgs A) {
+__global__ void __launch_bounds__(kPreBlock, 4) k_pre_count(const __grid_constant__ PreprocessArgs A) {
     __shared__ PreSmem S;
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned FULL = 0xffffffffu;
@@ -349,7 +397,6 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constan
     if (lane == 0 && n_in) atomicAdd(&A.ctr->n_culled_in, n_in);
     const int w = valid ? G.tx1 - G.tx0 + 1 : 0;
     const int h = valid ? G.ty1 - G.ty0 + 1 : 0;
-    const int ncand = w * h;
     if (valid) {
         S.u[tid] = G.u;
         S.v[tid] = G.v;
@@ -362,23 +409,19 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constan
     }
     S.w[tid] = w > 0 ? w : 1;
     S.cnt[tid] = 0;
-    const int ctotal = block_scan_cand(S, ncand);
+    const int ctotal = block_scan_cand(S, valid ? units_of(w, h) : 0);
 
-    unsigned hits = 0;
     for (int base = 0; base < ctotal; base += kPreBlock) {
         const int slot = base + tid;
-        bool hit = false;
-        int g = -1;
         if (slot < ctotal) {
-            int tile;
-            hit = slot_test(S, A.B, slot, g, tile);
+            const Unit U = unit_of(S, slot);
+            const unsigned m = unit_hits(S, A.B, U);
+            if (m) atomicAdd(&S.cnt[U.g], (unsigned)__popc(m));
         }
-        // consecutive slots share Gaussians: one shared-memory add per (warp, Gaussian)
-        const unsigned peers = __match_any_sync(FULL, g);
-        const unsigned hm = __ballot_sync(FULL, hit) & peers;
-        if (g >= 0 && hm && lane == __ffs(peers) - 1) atomicAdd(&S.cnt[g], (unsigned)__popc(hm));
-        hits += (unsigned)__syncthreads_count(hit);
     }
+    __syncthreads();
+    unsigned hits = 0;
+    block_excl(S, S.cnt[tid], &hits);
     const bool vis = S.cnt[tid] != 0;
     const unsigned nvis_block = (unsigned)__syncthreads_count(vis);
     if (tid == 0) {
@@ -387,8 +430,8 @@ __global__ void __launch_bounds__(kPreBlock, 3) k_pre_count(const __grid_constan
         if (nvis_block) atomicAdd(&A.ctr->n_visible, nvis_block);
     }
     if (gid < R.scene.P) A.counts[rec] = S.cnt[tid];
-    if (gid < R.scene.P) A.geo2[rec] = vis ? make_int4(G.tx0, G.ty0, w, h) : make_int4(0, 0, 0, 0);
     if (vis) {
+        A.geo2[rec] = make_int4(G.tx0, G.ty0, w, h);
         A.geo0[rec] = make_float4(G.u, G.v, G.a, G.b);
         A.geo1[rec] = make_float4(G.c, G.t, __uint_as_float(__float_as_uint(G.z)), 0.0f);
         const float4 po = __ldg(R.scene.pos_opa + gid);
@@ -508,7 +551,8 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_sum(const __grid_constant__ 
 // (tile, depth, id) order of the 64-bit keys.
 template <bool DEPTH>
 __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
-    __shared__ PreSmem S;
+    __shared__ EmitSmem E;
+    PreSmem &S = E.P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const long long chunk = blockIdx.x;
@@ -530,7 +574,8 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
     S.req[tid] = (unsigned char)ri;
     int ncand = 0;
     S.cnt[tid] = (unsigned)gid;
-    if (in_range) {
+    // geometry exists only for paired Gaussians (count > 0; every depth-ordered one is)
+    if (in_range && (DEPTH || A.counts[gid] != 0u)) {
         const int4 g2 = A.geo2[gid];
         ncand = g2.z * g2.w;
         if (ncand > 0) {
@@ -550,23 +595,15 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
         S.w[tid] = 1;
     }
     const long long cap = A.pair_cap;
-    const unsigned lt = (1u << lane) - 1u;
+    const int nunits = ncand > 0 ? units_of(S.w[tid], ncand / S.w[tid]) : 0;
     if (DEPTH) {
         // Each Gaussian's pairs start at the chunk base + the pairs of the Gaussians before it in
         // depth order.  Large Gaussians go to k_emit_big (one CTA each) so that a chunk of
         // consecutive depth ranks -- where large footprints cluster -- does not serialise them.
         const unsigned c = in_range ? A.counts[gid] : 0u;
-        unsigned incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) S.wsum[warp] = incl;
-        __syncthreads();
-        unsigned wex = 0;
-        for (int w2 = 0; w2 < warp; ++w2) wex += S.wsum[w2];
-        const unsigned long long pb = A.chunk_base2[chunk] + wex + incl - c;
+        unsigned tot;
+        const unsigned pre = block_excl(S, c, &tot);
+        const unsigned long long pb = A.chunk_base2[chunk] + pre;
         S.pbase[tid] = pb;
         S.run[tid] = 0;
         const bool big = ncand > kBigCand;
@@ -574,65 +611,77 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
             const unsigned k = atomicAdd(&A.ctr->n_big, 1u);
             A.big[k] = make_uint4((unsigned)gid, (unsigned)ri, (unsigned)(pb & 0xffffffffu), (unsigned)(pb >> 32));
         }
-        if (big) ncand = 0;
-        __syncthreads();
-        const int ctotal = block_scan_cand(S, ncand);
+        const int ctotal = block_scan_cand(S, big ? 0 : nunits);
         for (int base = 0; base < ctotal; base += kPreBlock) {
             const int slot = base + tid;
-            bool hit = false;
-            int g = -1, tile = 0;
-            if (slot < ctotal) hit = slot_test(S, A.B, slot, g, tile);
-            const unsigned bal = __ballot_sync(FULL, hit);
-            if (lane == 0) S.wsum[warp] = __popc(bal);
-            __syncthreads();
-            unsigned wpre = 0;
-#pragma unroll
-            for (int w2 = 0; w2 < kPreBlock / 32; ++w2) wpre += w2 < warp ? S.wsum[w2] : 0u;
-            const unsigned xr = wpre + __popc(bal & lt);      // exclusive hit rank of this slot in the step
+            unsigned m = 0;
+            Unit U{-1, 0, 0, 0};
+            if (slot < ctotal) {
+                U = unit_of(S, slot);
+                m = unit_hits(S, A.B, U);
+            }
+            unsigned step_tot;
+            const unsigned xr = block_excl(S, (unsigned)__popc(m), &step_tot);   // exclusive hit rank in the step
             S.xr[tid] = xr;
+            if (m) {
+                const ReqDesc &R = A.B.r[S.req[U.g]];
+                const unsigned trow = (unsigned)(R.tile0 + U.ty * R.cam.tiles_x);
+                unsigned i = xr;
+                for (unsigned mm = m; mm; mm &= mm - 1, ++i) {
+                    E.stile[i] = trow + (unsigned)(U.tx + __ffs(mm) - 1);
+                    E.sg[i] = (unsigned char)U.g;
+                }
+            }
             __syncthreads();
-            if (hit) {
-                const int first = max(S.cstart[g], base) - base;   // g's first slot in this step
-                const unsigned long long pos = S.pbase[g] + S.run[g] + (xr - S.xr[first]);
+            // hit i of Gaussian g lands at g's base + g's hits in earlier steps + its rank among
+            // g's hits of this step (g's first unit of the step starts at staged index xr[first])
+            for (unsigned i = tid; i < step_tot; i += kPreBlock) {
+                const int g = E.sg[i];
+                const int first = max(S.cstart[g], base) - base;
+                const unsigned long long pos = S.pbase[g] + S.run[g] + (i - S.xr[first]);
                 if ((long long)pos < cap) {
-                    A.tkeys[pos] = (unsigned)tile;
+                    A.tkeys[pos] = E.stile[i];
                     A.vals[pos] = S.cnt[g];
                 }
             }
             __syncthreads();
             // advance each Gaussian's running count by its hits in this step
-            const unsigned peers = __match_any_sync(FULL, g);
-            const unsigned hm = bal & peers;
-            if (g >= 0 && hm && lane == __ffs(peers) - 1) atomicAdd(&S.run[g], (unsigned)__popc(hm));
+            if (m) atomicAdd(&S.run[U.g], (unsigned)__popc(m));
             __syncthreads();
         }
         return;
     }
-    const int ctotal = block_scan_cand(S, ncand);
+    const int ctotal = block_scan_cand(S, nunits);
     unsigned long long run = A.chunk_base[chunk];
     for (int base = 0; base < ctotal; base += kPreBlock) {
         const int slot = base + tid;
-        bool hit = false;
-        int g = 0, tile = 0;
-        if (slot < ctotal) hit = slot_test(S, A.B, slot, g, tile);
-        const unsigned bal = __ballot_sync(FULL, hit);
-        if (lane == 0) S.wsum[warp] = __popc(bal);
-        __syncthreads();
-        unsigned wpre = 0, tot = 0;
-#pragma unroll
-        for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
-            const unsigned x = S.wsum[w2];
-            wpre += w2 < warp ? x : 0u;
-            tot += x;
+        unsigned m = 0;
+        Unit U{0, 0, 0, 0};
+        if (slot < ctotal) {
+            U = unit_of(S, slot);
+            m = unit_hits(S, A.B, U);
         }
-        if (hit) {
-            const unsigned long long pos = run + wpre + __popc(bal & lt);
-            if ((long long)pos < cap) {
-                A.keys[pos] = ((unsigned long long)(unsigned)tile << 32) | S.zb[g];
-                A.vals[pos] = S.cnt[g];        // record index of slot g
+        unsigned step_tot;
+        const unsigned xr = block_excl(S, (unsigned)__popc(m), &step_tot);
+        if (m) {
+            const ReqDesc &R = A.B.r[S.req[U.g]];
+            const unsigned trow = (unsigned)(R.tile0 + U.ty * R.cam.tiles_x);
+            unsigned i = xr;
+            for (unsigned mm = m; mm; mm &= mm - 1, ++i) {
+                E.stile[i] = trow + (unsigned)(U.tx + __ffs(mm) - 1);
+                E.sg[i] = (unsigned char)U.g;
             }
         }
-        run += tot;
+        __syncthreads();
+        for (unsigned i = tid; i < step_tot; i += kPreBlock) {
+            const unsigned long long pos = run + i;
+            if ((long long)pos < cap) {
+                const int g = E.sg[i];
+                A.keys[pos] = ((unsigned long long)E.stile[i] << 32) | S.zb[g];
+                A.vals[pos] = S.cnt[g];        // record index of Gaussian g
+            }
+        }
+        run += step_tot;
         __syncthreads();
     }
 }
@@ -641,6 +690,7 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
 // tiles tested 256 at a time, hits written in row-major order from the Gaussian's base.
 __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ PreprocessArgs A) {
     __shared__ unsigned s_item, s_w[kPreBlock / 32];
+    __shared__ unsigned s_tile[kPreBlock * kSeg];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const unsigned nbig = *(volatile unsigned *)&A.ctr->n_big;
@@ -657,19 +707,28 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
         unsigned long long run = ((unsigned long long)it.w << 32) | it.z;
         const float4 g0 = A.geo0[rec], g1 = A.geo1[rec];
         const int4 g2 = A.geo2[rec];
-        const int ncand = g2.z * g2.w;
-        for (int base = 0; base < ncand; base += kPreBlock) {
+        const int segs = (g2.z + kSeg - 1) / kSeg;
+        const int nunits = segs * g2.w;
+        for (int base = 0; base < nunits; base += kPreBlock) {
             const int k = base + tid;
-            bool hit = false;
-            int tile = 0;
-            if (k < ncand) {
-                const int dy = k / g2.z;
-                const int tx = g2.x + (k - dy * g2.z), ty = g2.y + dy;
-                tile = R.tile0 + ty * R.cam.tiles_x + tx;
-                hit = test_tile(R.cam, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, ty);
+            unsigned m = 0;
+            int tx = 0, ty = 0;
+            if (k < nunits) {
+                const int dy = k / segs, seg = k - dy * segs;
+                tx = g2.x + seg * kSeg;
+                ty = g2.y + dy;
+                m = run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, min(kSeg, g2.z - seg * kSeg),
+                             ty);
             }
-            const unsigned bal = __ballot_sync(FULL, hit);
-            if (lane == 0) s_w[warp] = __popc(bal);
+            // block exclusive scan of the hit counts
+            const unsigned c = (unsigned)__popc(m);
+            unsigned incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_w[warp] = incl;
             __syncthreads();
             unsigned wpre = 0, tot = 0;
 #pragma unroll
@@ -678,10 +737,14 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
                 wpre += w2 < warp ? x : 0u;
                 tot += x;
             }
-            if (hit) {
-                const unsigned long long pos = run + wpre + __popc(bal & ((1u << lane) - 1u));
+            unsigned i = wpre + incl - c;
+            const unsigned trow = (unsigned)(R.tile0 + ty * R.cam.tiles_x);
+            for (unsigned mm = m; mm; mm &= mm - 1, ++i) s_tile[i] = trow + (unsigned)(tx + __ffs(mm) - 1);
+            __syncthreads();
+            for (unsigned j = tid; j < tot; j += kPreBlock) {
+                const unsigned long long pos = run + j;
                 if ((long long)pos < cap) {
-                    A.tkeys[pos] = (unsigned)tile;
+                    A.tkeys[pos] = s_tile[j];
                     A.vals[pos] = (unsigned)rec;
                 }
             }
@@ -726,7 +789,7 @@ int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cud
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        big_grid = 4 * sms;
+        big_grid = 8 * sms;
     }
     k_emit_big<<<big_grid, kPreBlock, 0, s>>>(a);
     return 4;

@@ -66,7 +66,7 @@ def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False, varia
     return out
 
 
-def check(res, ref, check_unsorted=True):
+def check(res, ref, check_unsorted=True, t_min=1e-4, alpha_max=0.99):
     st = res["stats"]
     assert st["status"] == 0, st
     assert st["pairs"] == ref.N
@@ -92,9 +92,11 @@ def check(res, ref, check_unsorted=True):
     assert np.abs(res["T"] - ref.T).max() <= RGB_MAX
     diff = res["last"] != ref.last
     assert diff.mean() <= 1e-3, diff.mean()
-    # where the index differs, the early-stop decision was a near tie
+    # where the index differs, the early-stop decision T (1 - alpha) < T_min was a near tie: the
+    # pixel's transmittance is within the stop regime T <= T_min / (1 - alpha_max) on both sides
     if diff.any():
-        assert np.all(np.abs(ref.T[diff] - 1e-4) <= 5e-5 + 0.01 * ref.T[diff])
+        stop_regime = t_min / (1.0 - alpha_max) * 1.01
+        assert np.all(ref.T[diff] <= stop_regime) and np.all(res["T"][diff] <= stop_regime)
 
 
 @pytest.mark.parametrize("sort_mode", [0, 1])
@@ -118,7 +120,7 @@ def test_ragged_images(ctx, W, H, sort_mode):
 def test_options(ctx, opts_kw, sort_mode):
     scene, cam = synth.random_small_scene(3000, 11, 128, 96, log_scale_mu=-2.4, log_scale_sigma=1.0)
     ref = oracle.Frame(scene, cam, oracle.opts(**opts_kw), mode=64)
-    check(run_gpu(ctx, scene, cam, opts_kw, sort_mode=sort_mode), ref)
+    check(run_gpu(ctx, scene, cam, opts_kw, sort_mode=sort_mode), ref, t_min=opts_kw.get("T_min", 1e-4))
 
 
 def test_raw_parameters_activated_on_device(ctx):
@@ -134,6 +136,27 @@ def test_large_gaussians_many_candidate_tiles(ctx, sort_mode):
     ref = oracle.Frame(scene, cam, mode=64)
     big = ((ref.rect[:, 1] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 2] + 1) > 256) & (ref.valid > 0)
     assert big.sum() > 10
+    check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
+
+
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_elongated_gaussians_row_runs(ctx, sort_mode):
+    """Thin rotated ellipses up to a few hundred pixels long: many tiles are hit only through a
+    side edge, box widths are not multiples of the 8-tile run, and the largest take the
+    one-CTA-per-Gaussian emission of the depth-ordered mode."""
+    scene, cam = synth.random_small_scene(700, 17, 700, 610, log_scale_mu=-2.2, log_scale_sigma=0.5)
+    rng = np.random.Generator(np.random.PCG64(5))
+    s = scene.scales.astype(np.float64)
+    axis = rng.integers(0, 3, scene.P)
+    s *= 0.08
+    s[np.arange(scene.P), axis] *= rng.uniform(10.0, 400.0, scene.P)
+    scene.scales = s.astype(np.float32)
+    # Conics this ill-conditioned carry binary32 rounding far above the image tolerance against
+    # binary64 values, so the image is compared with the oracle's binary32 blend; the pair lists
+    # are exact either way.
+    ref = oracle.Frame(scene, cam, mode=32)
+    ncand = (ref.rect[:, 1] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 2] + 1) * (ref.valid > 0)
+    assert (ncand > 1024).sum() >= 5 and ((ncand > 8) & (ncand < 200)).sum() >= 50
     check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
 
 
