@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="room", choices=["room", "city", "tiny"])
+    ap.add_argument("--gaussians", type=int, default=None,
+                    help="draw the config's scene with this many Gaussians (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -120,17 +122,26 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------ workload
-def workload(name):
+DEFAULT_P = {"room": 1_000_000, "city": 10_000_000, "tiny": 10_000}
+
+
+def workload(name, P=None):
     from paper_2408_07967_gb300 import synth
-    scene, cams = synth.load_config(name)
+    scene, cams = synth.load_config(name, P)
     desc = {"room": "room-scale 1M Gaussians @1920x1080, 32 cameras (synthetic, seed 1)",
             "city": "city-scale 10M Gaussians @3840x2160, 16 aerial + 16 street cameras (synthetic, seed 2)",
             "tiny": "tiny 10k Gaussians @256x256, 1 camera (synthetic, seed 0)"}[name]
+    if P and P != DEFAULT_P[name]:
+        desc = f"{desc}; reduced to {P} Gaussians of the same distribution (profiling case)"
     return scene, cams, desc
 
 
-def pair_capacity(name):
-    return {"room": 1 << 25, "city": (1 << 30) - 1, "tiny": 1 << 21}[name]
+def pair_capacity(name, P=None):
+    full = {"room": 1 << 25, "city": (1 << 30) - 1, "tiny": 1 << 21}[name]
+    if not P or P >= DEFAULT_P[name]:
+        return full
+    # the workloads make about 1.4 (room) and 10 (city) pairs per Gaussian: 16 per Gaussian is ample
+    return min(full, 1 << max(21, math.ceil(math.log2(16 * P))))
 
 
 def dist_info():
@@ -170,7 +181,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    scene, cams, desc = workload(args.config)
+    scene, cams, desc = workload(args.config, args.gaussians)
     cores = oracle.get_threads()
     # warm-up: at most one frame (the oracle has no caches to warm beyond the page cache)
     if args.warmup > 0:
@@ -498,7 +509,7 @@ def run_ours(args):
     import paper_2408_07967_gb300 as gs
     from paper_2408_07967_gb300 import synth
 
-    scene, cams, desc = workload(args.config)
+    scene, cams, desc = workload(args.config, args.gaussians)
     ctx = gs.Context(dev)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -507,7 +518,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     alu = measure_alu(gs, dev)
     main, fr, cam_of = time_frames(gs, ctx, sc, scene.P, cams, args.steps, args.warmup, stream, flush,
-                                   pair_capacity(args.config), args, rank, alu=alu)
+                                   pair_capacity(args.config, args.gaussians), args, rank, alu=alu)
     tot_ms = max_over_ranks(main["ms_total"])
     if ws > 1:
         torch.distributed.barrier()

@@ -1,14 +1,16 @@
-// gs_sort.cu -- device-wide LSD radix sort of (u64 key, u32 value) pairs in the onesweep
-// form, and the per-tile range search.
+// gs_sort.cu -- device-wide LSD radix sort of (key, u32 value) pairs in the onesweep form, and
+// the per-tile range search.
 //
 // Sort (the stage FlashGS inherits from 3DGS's CUB SortPairs, Section 2.2): one pass over the
 // keys builds the 256-bin histograms of every 8-bit digit at once; a tiny kernel turns them into
 // exclusive digit offsets; then one scatter pass per digit.  A scatter CTA takes tiles of 3072
 // pairs in ticket order, ranks them by digit with warp match/ballot (stable: warp-striped load
-// order equals input order), publishes its per-digit counts, and reads its predecessors'
-// counts through a decoupled look-back over epoch-tagged descriptors (no per-sort clearing;
-// waits bounded by kSpinLimit), then scatters through shared memory so that global writes are
-// runs of consecutive addresses.
+// order equals input order), publishes its per-digit counts, places the tile in (digit, rank)
+// order in shared memory, and reads its predecessors' counts through a decoupled look-back over
+// epoch-tagged descriptors (up to 16 predecessors per round trip; no per-sort clearing; waits
+// bounded by kSpinLimit); then it writes runs of consecutive addresses.  For 32-bit keys the next
+// tile's keys and values arrive by bulk copy (cp.async.bulk on an mbarrier) while the current
+// tile is written out.
 //
 // Ranges: the first position of every tile id in the sorted keys by binary search; tile t
 // spans [start[t], start[t+1]).
@@ -19,10 +21,12 @@ namespace gs {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 12;
+static_assert((kSortThreads * kSortItems * 4) % 16 == 0, "bulk copies of a full tile are whole 16-byte units");
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr unsigned kDescAgg = 1u << 30;
 constexpr unsigned kDescPrefix = 2u << 30;
 constexpr unsigned kDescCount = (1u << 30) - 1;
+constexpr int kLookWindow = 16;
 
 int sort_tile_items() { return kSortTile; }
 long long sort_max_tiles_for(long long n) { return (n + kSortTile - 1) / kSortTile; }
@@ -76,17 +80,67 @@ __global__ void __launch_bounds__(256) k_sort_offsets(unsigned *hist, unsigned *
 }
 
 // ------------------------------------------------------------------------------------------ scatter
+// Bulk-copy helpers (the TMA engine's untiled form): one elected thread posts the expected byte
+// count on an mbarrier and issues cp.async.bulk copies global -> shared that complete on it.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Waits for phase `parity` of the barrier to complete; false after kSpinLimit polls.
+__device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned parity) {
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 32-bit keys (the large tile sorts) double-buffer their tiles so that the next tile's bulk copy
+// lands while the current one is scattered; 64-bit keys keep one buffer, so that three CTAs fit
+// an SM (their sorts are small and latency-bound).
+template <class K>
+constexpr int kBufs = sizeof(K) == 4 ? 2 : 1;
+
 template <class K>
 struct ScatterSmem {
-    K keys[kSortTile];
-    unsigned vals[kSortTile];
+    K keys[kBufs<K>][kSortTile];   // tile being ranked / next tile in flight
+    unsigned vals[kBufs<K>][kSortTile];
     unsigned whist[kSortWarps][256];
     unsigned local_off[256];
     unsigned long long gbase[256];
+    unsigned long long bar[2];
     unsigned wsum[kSortWarps];
-    unsigned tile;
+    long long tile[2];
+    int bulk[2];                   // buffer b was filled by a bulk copy (else: plain loads)
 };
 
+// One pass of the onesweep scatter.  Persistent CTAs take tiles in ticket order.  As soon as a
+// tile has its global digit offsets (after the look-back), the CTA takes its next ticket and
+// starts that tile's bulk copy into the other shared-memory buffer, so the copy overlaps the
+// scatter of the current tile (full tiles of 16-byte-aligned arrays; a partial last tile or
+// unaligned arrays use plain loads).  Taking the ticket only then keeps a tile's predecessor
+// from waiting in a CTA that has not started it.  Progress: every CTA works on its tiles in
+// ticket order and a tile waits only on smaller tiles, so the smallest unfinished tile is always
+// being worked on.
 template <class K>
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__restrict__ kin,
                                                                const unsigned *__restrict__ vin,
@@ -94,52 +148,96 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
                                                                unsigned *__restrict__ vout,
                                                                const unsigned long long *n_dev, long long n_host,
                                                                long long cap, int pass, const unsigned *offs,
-                                                               unsigned long long *desc, FrameCounters *ctr) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                               unsigned long long *desc, FrameCounters *ctr,
+                                                               int bulk_ok) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const int shift = 8 * pass;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
+    const long long nfull = n / kSortTile;
     const unsigned epoch = *(volatile unsigned *)&ctr->sort_epoch;
     const unsigned long long tag = (unsigned long long)(epoch * 8u + (unsigned)pass) << 32;
     const unsigned lt_mask = (1u << lane) - 1u;
     const unsigned goff = offs[pass * 256 + tid];
+    unsigned phases = 0u;          // bit q: parity of buffer q's next pending phase
+    bool failed = false;
 
+    // Takes the next ticket into buffer b and starts its bulk copy when it is a full tile.
+    auto fetch = [&](int b) {
+        if (tid == 0) {
+            const long long t = (long long)atomicAdd(&ctr->sort_ticket[pass], 1u);
+            S.tile[b] = t;
+            const bool bulk = kBufs<K> == 2 && bulk_ok && t < nfull;
+            S.bulk[b] = bulk;
+            if (bulk) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_expect(&S.bar[b], (unsigned)(kSortTile * (sizeof(K) + sizeof(unsigned))));
+                const int db = kBufs<K> == 2 ? b : 0;
+                bulk_g2s(S.keys[db], kin + t * kSortTile, (unsigned)(kSortTile * sizeof(K)), &S.bar[b]);
+                bulk_g2s(S.vals[db], vin + t * kSortTile, (unsigned)(kSortTile * sizeof(unsigned)), &S.bar[b]);
+            }
+        }
+    };
+
+    if (tid == 0) {
+        bar_init(&S.bar[0]);
+        bar_init(&S.bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    fetch(0);
+    int b = 0;
     while (true) {
-        if (tid == 0) S.tile = atomicAdd(&ctr->sort_ticket[pass], 1u);
         for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
         __syncthreads();
-        const long long tile = S.tile;
+        const long long tile = S.tile[b];
         if (tile >= ntiles) break;
+        const int db = kBufs<K> == 2 ? b : 0;      // data buffer of this tile
         const long long tbase = tile * kSortTile;
-        const long long wbase = tbase + (long long)warp * (32 * kSortItems);
+        const int wofs = warp * (32 * kSortItems);
 
         K k[kSortItems];
         unsigned v[kSortItems];
         unsigned rank[kSortItems];
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const long long idx = wbase + i * 32 + lane;
-            if (idx < n) {
-                k[i] = kin[idx];
-                v[i] = vin[idx];
+        if (S.bulk[b]) {
+            if (bar_wait(&S.bar[b], (phases >> b) & 1u)) {
+                phases ^= 1u << b;
             } else {
-                k[i] = (K)~(K)0;
-                v[i] = 0u;
+                if (lane == 0) atomicOr(&ctr->status, kStTimeout);
+                failed = true;
+            }
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) {
+                k[i] = S.keys[db][wofs + i * 32 + lane];
+                v[i] = S.vals[db][wofs + i * 32 + lane];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) {
+                const long long idx = tbase + wofs + i * 32 + lane;
+                if (idx < n) {
+                    k[i] = kin[idx];
+                    v[i] = vin[idx];
+                } else {
+                    k[i] = (K)~(K)0;
+                    v[i] = 0u;
+                }
             }
         }
+        if (__syncthreads_or(failed)) break;
         // stable warp-level ranking in (item, lane) order
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
             const unsigned peers = __match_any_sync(FULL, d);
             const unsigned before = __popc(peers & lt_mask);
-            const unsigned b = S.whist[warp][d];
+            const unsigned bb = S.whist[warp][d];
             __syncwarp();
-            rank[i] = b + before;
-            if (before == 0) S.whist[warp][d] = b + __popc(peers);
+            rank[i] = bb + before;
+            if (before == 0) S.whist[warp][d] = bb + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
@@ -173,46 +271,75 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
         unsigned wex = 0;
         for (int w = 0; w < warp; ++w) wex += S.wsum[w];
         S.local_off[tid] = wex + incl - cnt;
+        __syncthreads();
+        // scatter into this tile's buffer (its contents are in registers) in (digit, rank) order
+        // before the look-back, so that only the digit's registers stay live while it waits
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+            const unsigned pos = S.local_off[d] + S.whist[warp][d] + rank[i];
+            S.keys[db][pos] = k[i];
+            S.vals[db][pos] = v[i];
+        }
         unsigned long long excl = 0;
         if (tile > 0) {
+            // Look back kLookWindow predecessors per round trip (independent loads), summing
+            // aggregates in order until a prefix; a descriptor not yet published is re-read.
+            // The first round reads only the immediate predecessor, which has usually published
+            // its prefix already; later rounds read the whole window.
             long long j = tile - 1;
             unsigned spins = 0;
-            while (j >= 0) {
-                const unsigned long long d = *(const volatile unsigned long long *)(desc + j * 256 + tid);
-                const unsigned flag = (unsigned)d & ~kDescCount;
-                if ((d & 0xffffffff00000000ull) != tag || flag == 0) {
+            bool done = false;
+            int span = 1;
+            while (!done) {
+                unsigned long long d[kLookWindow];
+#pragma unroll
+                for (int w = 0; w < kLookWindow; ++w)
+                    d[w] = (w < span && j - w >= 0) ? *(const volatile unsigned long long *)(desc + (j - w) * 256 + tid)
+                                                     : 0ull;
+                span = kLookWindow;
+                int w = 0;
+#pragma unroll
+                for (int q = 0; q < kLookWindow; ++q) {
+                    if (done || w != q || j - q < 0) continue;
+                    const unsigned flag = (unsigned)d[q] & ~kDescCount;
+                    if ((d[q] & 0xffffffff00000000ull) != tag || flag == 0) continue;   // not published yet
+                    excl += (unsigned)d[q] & kDescCount;
+                    if (flag == kDescPrefix) done = true;
+                    w = q + 1;
+                }
+                if (done) break;
+                j -= w;
+                if (w == 0) {
                     if (++spins > kSpinLimit) {
                         atomicOr(&ctr->status, kStTimeout);
                         break;
                     }
                     __nanosleep(20);
-                    continue;
                 }
-                excl += (unsigned)d & kDescCount;
-                if (flag == kDescPrefix) break;
-                --j;
             }
             *(volatile unsigned long long *)my = tag | kDescPrefix | (unsigned)(excl + cnt_valid);
         }
         S.gbase[tid] = (unsigned long long)goff + excl;
-        __syncthreads();
-        // scatter into shared memory in (digit, rank) order
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-            const unsigned pos = S.local_off[d] + S.whist[warp][d] + rank[i];
-            S.keys[pos] = k[i];
-            S.vals[pos] = v[i];
-        }
+        // this tile has published its prefix: take the next ticket now, so its copy overlaps the
+        // scatter below while no later tile waits on a ticket that is not being worked on
+        fetch(b ^ 1);
         __syncthreads();
         for (int s = tid; s < valid_here; s += kSortThreads) {
-            const K key = S.keys[s];
+            const K key = S.keys[db][s];
             const unsigned d = (unsigned)(key >> shift) & 0xffu;
             const unsigned long long dst = S.gbase[d] + (unsigned long long)(s - S.local_off[d]);
             kout[dst] = key;
-            vout[dst] = S.vals[s];
+            vout[dst] = S.vals[db][s];
         }
         __syncthreads();
+        b ^= 1;
+    }
+    // a failed wait leaves copies possibly in flight: give them a bounded chance to land (the
+    // phase of a buffer is advanced only by a successful wait, so it names the pending one)
+    if (failed && tid == 0) {
+        for (int q = 0; q < 2; ++q)
+            if (S.bulk[q]) bar_wait(&S.bar[q], (phases >> q) & 1u);
     }
 }
 
@@ -245,11 +372,14 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
     k_sort_offsets<<<passes, 256, 0, s>>>(scr.hist, scr.offs, ctr);
     long long max_tiles = sort_max_tiles_for(cap);
     int grid = (int)min((long long)sgrid, max_tiles > 0 ? max_tiles : 1);
+    // full tiles start at multiples of kSortTile elements, so 16-byte-aligned arrays keep every
+    // bulk copy 16-byte aligned
+    const int bulk_ok = (((uintptr_t)keys | (uintptr_t)vals | (uintptr_t)keys_tmp | (uintptr_t)vals_tmp) & 15u) == 0;
     K *ka = keys, *kb = keys_tmp;
     unsigned *va = vals, *vb = vals_tmp;
     for (int p = 0; p < passes; ++p) {
         k_sort_scatter<K><<<grid, kSortThreads, sizeof(ScatterSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
-                                                                             scr.offs, scr.desc, ctr);
+                                                                             scr.offs, scr.desc, ctr, bulk_ok);
         K *tk = ka;
         ka = kb;
         kb = tk;
