@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-training", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--serving-requests", type=int, default=600)
     ap.add_argument("--no-city", action="store_true")
     ap.add_argument("--city-steps", type=int, default=64)
     ap.add_argument("--sort-mode", type=int, default=None, help="force gs_tuning.sort_mode (skips the autotuner)")

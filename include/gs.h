@@ -116,9 +116,10 @@ gs_status gs_context_create(int32_t device, gs_context **out);
 gs_status gs_context_destroy(gs_context *ctx);
 
 /* Device-resident scene: copies the canonical arrays in `g` into the library's internal
-   layout (272 bytes per Gaussian: a dense plane of position+opacity, read by the cull of every
-   Gaussian, and a 256-byte body of scale, quaternion and the 48 SH floats, read only for
-   Gaussians that pass the cull or are paired), enqueued on `stream`.  The input arrays may be freed
+   layout (240 bytes per Gaussian: a plane of position+opacity, read by the cull of every
+   Gaussian; a plane of scale and quaternion, read for Gaussians that pass the cull; and each
+   Gaussian's 48 SH floats as one contiguous 192-byte block, read only for paired Gaussians),
+   enqueued on `stream`.  The input arrays may be freed
    once the stream has passed this call.  Section 5.3.1 (per-scene work done once).
    Errors: GS_ERR_INVALID_ARG (NULL pointers, P <= 0, P >= 2^31, bad degree), GS_ERR_OOM. */
 gs_status gs_scene_create(gs_context *ctx, const gs_gaussians *g, gs_stream stream, gs_scene **out);
@@ -317,8 +318,12 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys_dev, uint32_t *vals_dev,
    at most max_gaussians Gaussians together) are admitted by pair-buffer memory: one count pass
    (geometry + exact pair counts) gives each request's pairs, and the oldest requests whose
    pairs fit pair_capacity run as one batch through gs_render_batch's single pass per stage with
-   per-request tile ranges; the rest wait for the next free slot.  Images are copied to the
-   callers' host buffers (asynchronous when page-locked).  Every request's image is
+   per-request tile ranges; the rest wait for the next free slot.  A lone request skips the
+   admission round trip (it has nothing to defer; if it alone exceeds pair_capacity it completes
+   with GS_ERR_PAIR_OVERFLOW).  Batches run on streams prioritised by age: a batch launched while
+   k others are in flight gets the k-th highest stream priority, so the oldest batch keeps the
+   SMs it needs and younger ones fill the rest.  Images are copied to the callers' host buffers
+   (asynchronous when page-locked).  Every request's image is
    bit-identical to rendering it alone.  plain = 1 is the baseline loop: one request at a time,
    synchronously, no count pass.  The paper describes single frames only; batching requests is
    this library's extension (Section 5.3.1's static allocation carries over: all buffers are
@@ -333,7 +338,10 @@ typedef struct {
     int32_t sort_mode;        /* gs_tuning.sort_mode of the slots' frames, -1 for the default */
     int32_t blend_variant;    /* gs_tuning.blend_variant, -1 for the default */
     int32_t plain;            /* 1: one request at a time (the baseline loop) */
-    int32_t reserved;
+    int32_t batch_pixels;     /* image pixels per batch, summed over its requests (0: 2 x 1920 x 1080);
+                                 a larger request runs alone -- batching amortises launches and
+                                 small kernels, while a request that fills the GPU by itself only
+                                 waits longer in a batch */
 } gs_server_cfg;
 typedef struct {
     int32_t status;           /* GS_OK, GS_ERR_PAIR_OVERFLOW (alone over the pair capacity), ... */
@@ -366,6 +374,10 @@ gs_status gs_server_submit(gs_server *server, const gs_scene *scene, const gs_ca
    when the limit passes first (the request stays queued).  *out (nullable) gets its times. */
 gs_status gs_server_wait(gs_server *server, uint64_t ticket, int32_t timeout_ms, gs_request_stats *out);
 gs_status gs_server_get_stats(gs_server *server, gs_server_stats *out);
+/* hold = 1: stop admitting requests (they keep queueing) and wait until no batch is in flight,
+   e.g. before gs_scene_update of a scene the server renders, or to let a burst queue up and run
+   in full batches; hold = 0: resume.  Errors: GS_ERR_INVALID_ARG (NULL server). */
+gs_status gs_server_hold(gs_server *server, int32_t hold);
 
 /* gs_sort_pairs without any allocation.  The paper has no counterpart: this entry point exists
    for callers that must not allocate device memory -- code handed its buffers by a host

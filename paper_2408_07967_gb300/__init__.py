@@ -106,7 +106,7 @@ class Context:
 
 
 class Scene:
-    """gs_scene: device-resident Gaussians (packed into a position plane and 256-byte bodies)."""
+    """gs_scene: device-resident Gaussians (position plane, scale/rotation plane, SH blocks)."""
 
     def __init__(self, ctx: Context, means, scales, quats, opacity, sh, sh_degree=3, activated=True, stream=None):
         self.ctx = ctx
@@ -335,6 +335,10 @@ class Server:
     @staticmethod
     def clock() -> float:
         return float(lib().gs_clock_s())
+
+    def gs_server_hold(self, hold: bool = True):
+        """Stop admitting (and wait for the batches in flight), or resume."""
+        _check(lib().gs_server_hold(self.h, int(bool(hold))))
 
     def gs_server_submit(self, scene: Scene, cam, rgb_host, opts=None, arrival_s=0.0) -> int:
         """rgb_host: a CPU float32 tensor [3,H,W] (page-locked for asynchronous copies)."""

@@ -42,7 +42,7 @@ class gs_gaussian_grads(C.Structure):
 class gs_server_cfg(C.Structure):
     _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("pair_capacity", C.c_int64),
                 ("max_gaussians", C.c_int64), ("max_width", C.c_int32), ("max_height", C.c_int32),
-                ("sort_mode", C.c_int32), ("blend_variant", C.c_int32), ("plain", C.c_int32), ("reserved", C.c_int32)]
+                ("sort_mode", C.c_int32), ("blend_variant", C.c_int32), ("plain", C.c_int32), ("batch_pixels", C.c_int32)]
 
 
 class gs_request_stats(C.Structure):
@@ -104,6 +104,7 @@ PROTOTYPES = {
     "gs_frame_ranges": (_st, [_vp, _vp, C.c_int64, _vp]),
     "gs_sort_pairs": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _vp]),
     "gs_clock_s": (C.c_double, []),
+    "gs_server_hold": (_st, [_vp, C.c_int32]),
     "gs_default_server_cfg": (_st, [C.POINTER(gs_server_cfg)]),
     "gs_server_create": (_st, [_vp, C.POINTER(gs_server_cfg), _pp]),
     "gs_server_destroy": (_st, [_vp]),

@@ -100,7 +100,7 @@ struct gs_scene {
     int sh_degree = 3;
     int activated = 1;
     void *mem = nullptr;
-    float4 *pos_opa = nullptr, *body = nullptr;
+    float4 *pos_opa = nullptr, *rs = nullptr, *sh = nullptr;
 };
 
 struct gs_frame {
@@ -227,15 +227,17 @@ gs_status gs_scene_create(gs_context *ctx, const gs_gaussians *g, gs_stream stre
     s->ctx = ctx;
     s->device = ctx->device;
     s->P = g->P;
-    // bodies first (256-byte aligned by cudaMalloc), then the position plane
-    cudaError_t e = cudaMalloc(&s->mem, (size_t)(kBody + 1) * (size_t)g->P * sizeof(float4));
+    // SH blocks first (256-byte aligned by cudaMalloc, so every 192-byte block starts on a
+    // 64-byte boundary), then scale/rotation, then positions
+    cudaError_t e = cudaMalloc(&s->mem, (size_t)(kShPlanes + 3) * (size_t)g->P * sizeof(float4));
     if (e != cudaSuccess) {
         delete s;
         return cuda_fail(e, "cudaMalloc(scene)");
     }
     float4 *base = (float4 *)s->mem;
-    s->body = base;
-    s->pos_opa = base + (size_t)kBody * g->P;
+    s->sh = base;
+    s->rs = base + (size_t)kShPlanes * g->P;
+    s->pos_opa = base + (size_t)(kShPlanes + 2) * g->P;
     st = gs_scene_update(s, g, stream);
     if (st) {
         cudaFree(s->mem);
@@ -253,7 +255,7 @@ gs_status gs_scene_update(gs_scene *s, const gs_gaussians *g, gs_stream stream) 
     if (g->P != s->P) return fail(GS_ERR_INVALID_ARG, "P changed (%lld != %lld)", (long long)g->P, s->P);
     s->sh_degree = g->sh_degree;
     s->activated = g->activated ? 1 : 0;
-    launch_pack_scene(*g, s->pos_opa, s->body, (cudaStream_t)stream);
+    launch_pack_scene(*g, s->pos_opa, s->rs, s->sh, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -461,7 +463,8 @@ static gs_status make_cam(const gs_camera *cam, Cam &c) {
 static SceneView view_of(const gs_scene *s) {
     SceneView v;
     v.pos_opa = s->pos_opa;
-    v.body = s->body;
+    v.rs = s->rs;
+    v.sh = s->sh;
     v.P = s->P;
     v.sh_degree = s->sh_degree;
     v.activated = s->activated;
@@ -994,7 +997,8 @@ extern "C" gs_status gs_render_backward(gs_frame *f, const gs_scene *s, const fl
     a.opt = f->opt;
     a.cam = f->cam;
     a.scene.pos_opa = s->pos_opa;
-    a.scene.body = s->body;
+    a.scene.rs = s->rs;
+    a.scene.sh = s->sh;
     a.scene.P = s->P;
     a.scene.sh_degree = s->sh_degree;
     a.scene.activated = s->activated;

@@ -208,14 +208,14 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
 #pragma unroll
         for (int i = 0; i < 3; ++i) p[i] = Rc[3 * i] * po.x + Rc[3 * i + 1] * po.y + Rc[3 * i + 2] * po.z + cam.t[i];
         const float alpha0 = S.activated ? po.w : 1.0f / (1.0f + __expf(-po.w));
-        const float4 sc4 = body_of(S, gid)[0];
+        const float4 sc4 = rs_of(S, gid)[0];
         float s[3] = {sc4.x, sc4.y, sc4.z};
         if (!S.activated) {
             s[0] = __expf(s[0]);
             s[1] = __expf(s[1]);
             s[2] = __expf(s[2]);
         }
-        const float4 q4 = body_of(S, gid)[1];
+        const float4 q4 = rs_of(S, gid)[1];
         const float qlen = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
         const float w = q4.x / qlen, x = q4.y / qlen, y = q4.z / qlen, z = q4.w / qlen;
         float R[9];
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
         float f[48];
 #pragma unroll
         for (int k = 0; k < kShPlanes; ++k) {
-            const float4 v4 = body_of(S, gid)[2 + k];
+            const float4 v4 = sh_of(S, gid)[k];
             f[4 * k] = v4.x;
             f[4 * k + 1] = v4.y;
             f[4 * k + 2] = v4.z;

@@ -40,21 +40,23 @@ struct Opts {
     int cap_3sigma, clamp_fov;
 };
 
-// Internal scene layout.  pos_opa is a dense plane (one float4 per Gaussian) read by the cull of
-// every Gaussian; everything else of Gaussian i is one 256-byte body at body[kBody * i]:
-//   [0] (sx, sy, sz, 0) or log-scales   [1] quaternion (w, x, y, z)
-//   [2 + k] SH floats 4k .. 4k+3, k < kShPlanes   [14], [15] zero padding
-// so a Gaussian that passes the cull costs one 64-byte DRAM burst for its scale and rotation, and
-// one that is paired three more for its colour, however sparse the visible set is.
-constexpr int kBody = 16;
+// Internal scene layout, three arrays sized by how sparsely each is read:
+//   pos_opa[i]          (x, y, z, opacity or logit): read by the cull of every Gaussian;
+//   rs[2 i], rs[2 i+1]  (sx, sy, sz, 0) or log-scales, and the quaternion (w, x, y, z): read by
+//                       every Gaussian that passes the cull (most of them), so a dense plane;
+//   sh[kShPlanes i + k] SH floats 4k .. 4k+3: read only for paired Gaussians, which are scattered
+//                       over the id range, so each Gaussian's 192 bytes are contiguous (three
+//                       64-byte bursts) instead of twelve planes with one burst each.
 struct SceneView {
-    const float4 *pos_opa;   // (x, y, z, opacity or logit)
-    const float4 *body;      // P bodies of kBody float4, 256-byte aligned
+    const float4 *pos_opa;
+    const float4 *rs;
+    const float4 *sh;
     int64_t P;
     int sh_degree;
     int activated;
 };
-__device__ __forceinline__ const float4 *body_of(const SceneView &S, long long gid) { return S.body + gid * kBody; }
+__device__ __forceinline__ const float4 *rs_of(const SceneView &S, long long gid) { return S.rs + 2 * gid; }
+__device__ __forceinline__ const float4 *sh_of(const SceneView &S, long long gid) { return S.sh + kShPlanes * gid; }
 
 // Render record of a paired Gaussian (48 bytes, three float4):
 //   r0 = (u, v, a, b2)   centre and conic, b2 = 2 b
@@ -330,7 +332,7 @@ struct PreprocessArgs {
     long long n_chunks;
 };
 
-void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *body, cudaStream_t s);
+void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *rs, float4 *sh, cudaStream_t s);
 void launch_pre_count(const PreprocessArgs &a, cudaStream_t s);
 void launch_req_pairs(const PreprocessArgs &a, unsigned long long *out, cudaStream_t s);
 void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted);

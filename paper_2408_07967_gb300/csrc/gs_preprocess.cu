@@ -30,38 +30,29 @@ constexpr int kPackBlock = 128;
 int preprocess_chunk() { return kPreBlock; }
 
 // ------------------------------------------------------------------------------------------ pack
-// Canonical AoS arrays -> the internal position plane and 256-byte bodies.  A CTA assembles its
-// 128 bodies in shared memory (the SH block read coalesced) and writes them as one contiguous,
-// coalesced 32 KiB run.
-__global__ void __launch_bounds__(kPackBlock) k_pack_scene(gs_gaussians g, float4 *pos_opa, float4 *body) {
-    __shared__ float4 s_body[kPackBlock * kBody];
-    float *sb = reinterpret_cast<float *>(s_body);
+// Canonical AoS arrays -> the internal position, scale/rotation and SH arrays.  The SH block of
+// a CTA is contiguous in both layouts (48 floats per Gaussian), so it is copied as float4s.
+__global__ void __launch_bounds__(kPackBlock) k_pack_scene(gs_gaussians g, float4 *pos_opa, float4 *rs, float4 *sh) {
     const long long base = (long long)blockIdx.x * kPackBlock;
     const int n = (int)min((long long)kPackBlock, g.P - base);
     const float *src = g.sh + base * 48;
-    for (int k = threadIdx.x; k < n * 48; k += kPackBlock) {
-        const int gi = k / 48, r = k - gi * 48;
-        sb[gi * 4 * kBody + 8 + r] = src[k];
-    }
+    float4 *dst = sh + base * kShPlanes;
+    for (int k = threadIdx.x; k < n * kShPlanes; k += kPackBlock)
+        dst[k] = make_float4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
     const long long i = base + threadIdx.x;
     if (threadIdx.x < n) {
         const float *m = g.means + 3 * i;
         const float *s = g.scales + 3 * i;
         const float *q = g.quats + 4 * i;
         pos_opa[i] = make_float4(m[0], m[1], m[2], g.opacity[i]);
-        s_body[threadIdx.x * kBody] = make_float4(s[0], s[1], s[2], 0.0f);
-        s_body[threadIdx.x * kBody + 1] = make_float4(q[0], q[1], q[2], q[3]);
-        s_body[threadIdx.x * kBody + 2 + kShPlanes] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_body[threadIdx.x * kBody + 3 + kShPlanes] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rs[2 * i] = make_float4(s[0], s[1], s[2], 0.0f);
+        rs[2 * i + 1] = make_float4(q[0], q[1], q[2], q[3]);
     }
-    __syncthreads();
-    float4 *dst = body + base * kBody;
-    for (int k = threadIdx.x; k < n * kBody; k += kPackBlock) dst[k] = s_body[k];
 }
 
-void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *body, cudaStream_t s) {
+void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *rs, float4 *sh, cudaStream_t s) {
     long long blocks = (g.P + kPackBlock - 1) / kPackBlock;
-    k_pack_scene<<<(unsigned)blocks, kPackBlock, 0, s>>>(g, pos_opa, body);
+    k_pack_scene<<<(unsigned)blocks, kPackBlock, 0, s>>>(g, pos_opa, rs, sh);
 }
 
 // ------------------------------------------------------------------------------------------ SH
@@ -101,7 +92,7 @@ __device__ __forceinline__ void sh_colour(const SceneView &S, long long gid, con
     const int nplanes = (3 * ncoef + 3) / 4;
     // SH float f = 3 i + ch belongs to coefficient i of channel ch; each channel accumulates in
     // ascending i as the planes stream in (float4 k holds floats 4k .. 4k+3)
-    const float4 *src = body_of(S, gid) + 2;
+    const float4 *src = sh_of(S, gid);
     float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int k = 0; k < kShPlanes; ++k) {
@@ -146,14 +137,44 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
     float t = t_full;
     if (o.cap_3sigma && t > 9.0f) t = 9.0f;
     // Sigma = R_q diag(s^2) R_q^T
-    const float4 sc = __ldg(body_of(S, gid));
+    const float4 sc = __ldg(rs_of(S, gid));
     float s0 = sc.x, s1 = sc.y, s2 = sc.z;
     if (!S.activated) {
         s0 = exp_rn(s0);
         s1 = exp_rn(s1);
         s2 = exp_rn(s2);
     }
-    const float4 q4 = __ldg(body_of(S, gid) + 1);
+    {
+        // Conservative screen-extent test.  Sigma <= s_max^2 I, so Sigma'00 <= s_max^2 |M0|^2 +
+        // dilation (M0 = first row of J W) and {q <= t} lies within u +- sqrt(t Sigma'00); a
+        // Gaussian whose bound, padded by 2% and two pixels for rounding, misses the image can
+        // have no candidate tile, and skipping its covariance changes no result.  (NaN bounds
+        // compare false and keep the Gaussian.)
+        const float smax = fmaxf(fmaxf(s0, s1), s2);
+        const float iz = 1.0f / p[2];
+        float rx = p[0] * iz, ry = p[1] * iz;
+        if (o.clamp_fov) {
+            rx = fminf(fmaxf(rx, -cam.limx), cam.limx);
+            ry = fminf(fmaxf(ry, -cam.limy), cam.limy);
+        }
+        const float a00 = cam.fx * iz, a02 = -cam.fx * rx * iz;
+        const float a11 = cam.fy * iz, a12 = -cam.fy * ry * iz;
+        float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float e0 = a00 * R[k] + a02 * R[6 + k];
+            const float e1 = a11 * R[3 + k] + a12 * R[6 + k];
+            m0 += e0 * e0;
+            m1 += e1 * e1;
+        }
+        const float hxb = sqrtf(t * (smax * smax * m0 + o.dilation)) * 1.02f + 2.0f;
+        const float hyb = sqrtf(t * (smax * smax * m1 + o.dilation)) * 1.02f + 2.0f;
+        const float uu = cam.fx * p[0] * iz + cam.cx, vv = cam.fy * p[1] * iz + cam.cy;
+        if (uu + hxb < 0.0f || uu - hxb >= (float)(kTile * cam.tiles_x) || vv + hyb < 0.0f ||
+            vv - hyb >= (float)(kTile * cam.tiles_y))
+            return false;
+    }
+    const float4 q4 = __ldg(rs_of(S, gid) + 1);
     float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
     float n2 = fmul(qw, qw);
     n2 = fadd(n2, fmul(qx, qx));

@@ -14,7 +14,9 @@
 //      ranges, gs_render_batch), then each image is copied to its host buffer and a host
 //      callback marks the batch complete.
 // Batches on different slots overlap on the device, and a request arriving while others run is
-// admitted as soon as a slot frees -- continuous batching rather than a queue alone.  Each
+// admitted as soon as a slot frees -- continuous batching rather than a queue alone.  Streams are
+// prioritised by batch age (the oldest batch in flight runs at the highest priority), and a lone
+// request runs without the admission round trip.  Each
 // request's image is bit-identical to rendering it alone.  `plain` mode is the baseline: one
 // request at a time, synchronously, no count pass.
 #include <chrono>
@@ -62,8 +64,12 @@ struct Request {
     bool finished = false;
 };
 
+constexpr int kPrioLevels = 3;
+
 struct Slot {
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;              // the stream of the batch in flight
+    cudaStream_t streams[kPrioLevels] = {};     // by priority, highest first
+    bool single = false;                        // the batch in flight is one unadmitted request
     gs_frame *frame = nullptr;
     float *out = nullptr;                       // max_batch images of max_width x max_height
     unsigned long long *pairs_dev = nullptr;    // per-request pair counts of the count pass
@@ -88,6 +94,7 @@ struct gs_server {
     std::vector<Slot> slots;
     std::thread worker;
     bool stop = false;
+    bool hold = false;
     uint64_t next_ticket = 1;
     long long completed = 0, batches = 0, batched_requests = 0;
     gs_status fatal = GS_OK;
@@ -113,6 +120,12 @@ void reap(gs_server *sv) {
         for (uint64_t t : s.inflight) {
             auto it = sv->reqs.find(t);
             if (it == sv->reqs.end()) continue;
+            if (s.single) {
+                // a lone request ran without the admission pass: its count arrived with the image
+                const long long p = (long long)s.pairs_host[0];
+                it->second.pairs = p;
+                if (p > sv->cfg.pair_capacity) it->second.status = GS_ERR_PAIR_OVERFLOW;
+            }
             it->second.done = s.done_time;
             it->second.finished = true;
             ++sv->completed;
@@ -149,7 +162,26 @@ std::vector<uint64_t> launch_batch(gs_server *sv, Slot &s, std::vector<uint64_t>
     std::vector<float *> rgb(n);
     for (int i = 0; i < n; ++i) rgb[i] = s.out + (size_t)i * image_floats(cfg);
     gs_status st = GS_OK;
-    if (!cfg.plain) {
+    // Priority by age: a batch launched while k others are in flight runs at the k-th highest
+    // stream priority, so the oldest batch keeps the SMs it needs (its latency stays that of a
+    // lone render) and younger ones fill what it leaves idle.
+    int level = 0;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (const Slot &o : sv->slots) level += (&o != &s && o.busy) ? 1 : 0;
+    }
+    s.stream = s.streams[level < kPrioLevels ? level : kPrioLevels - 1];
+    s.single = !cfg.plain && n == 1;
+    if (s.single) {
+        // One request: nothing to admit or defer, so the count pass runs without a host round
+        // trip; a request that alone exceeds the pair capacity is failed when it completes.
+        st = frame_batch_count(s.frame, 1, scenes.data(), cams.data(), opts.data(), s.pairs_dev, s.stream);
+        if (!st)
+            if (cudaMemcpyAsync(s.pairs_host, s.pairs_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                s.stream) != cudaSuccess)
+                st = GS_ERR_CUDA;
+        if (!st) st = frame_batch_finish(s.frame, rgb.data(), nullptr, nullptr, s.stream);
+    } else if (!cfg.plain) {
         // admission: exact pair counts of the candidates
         st = frame_batch_count(s.frame, n, scenes.data(), cams.data(), opts.data(), s.pairs_dev, s.stream);
         if (!st) {
@@ -236,20 +268,24 @@ void worker_main(gs_server *sv) {
                 free_slot = &s;
                 break;
             }
-        if (!free_slot || sv->pending.empty()) {
+        if (!free_slot || sv->pending.empty() || sv->hold) {
             sv->cv.notify_all();
             sv->cv.wait_for(lk, std::chrono::microseconds(200));
             continue;
         }
         // candidates: oldest requests, bounded by max_batch and the frame's Gaussian capacity
         std::vector<uint64_t> cand;
-        long long g = 0;
+        long long g = 0, px = 0;
         const int maxb = sv->cfg.plain ? 1 : sv->cfg.max_batch;
+        const long long max_px = sv->cfg.batch_pixels > 0 ? sv->cfg.batch_pixels : 2ll * 1920 * 1080;
         while (!sv->pending.empty() && (int)cand.size() < maxb) {
             const uint64_t t = sv->pending.front();
-            const long long P = gs_scene_size(sv->reqs[t].scene);
-            if (!cand.empty() && g + P > sv->cfg.max_gaussians) break;
+            const Request &r = sv->reqs[t];
+            const long long P = gs_scene_size(r.scene);
+            const long long npx = (long long)r.cam.width * r.cam.height;
+            if (!cand.empty() && (g + P > sv->cfg.max_gaussians || px + npx > max_px)) break;
             g += P;
+            px += npx;
             cand.push_back(t);
             sv->pending.pop_front();
         }
@@ -279,6 +315,7 @@ gs_status gs_default_server_cfg(gs_server_cfg *c) {
     c->sort_mode = -1;
     c->blend_variant = -1;
     c->plain = 0;
+    c->batch_pixels = 2 * 1920 * 1080;
     return GS_OK;
 }
 
@@ -291,7 +328,8 @@ gs_status gs_server_create(gs_context *ctx, const gs_server_cfg *cfg, gs_server 
         c.max_batch = 1;
     }
     if (c.slots < 1 || c.slots > 8 || c.max_batch < 1 || c.max_batch > gs::kMaxBatch || c.pair_capacity <= 0 ||
-        c.pair_capacity >= (1ll << 30) || c.max_gaussians <= 0 || c.max_width <= 0 || c.max_height <= 0)
+        c.pair_capacity >= (1ll << 30) || c.max_gaussians <= 0 || c.max_width <= 0 || c.max_height <= 0 ||
+        c.batch_pixels < 0)
         return err(GS_ERR_INVALID_ARG, "server configuration out of range");
     gs_server *sv = new (std::nothrow) gs_server();
     if (!sv) return err(GS_ERR_OOM, "host allocation failed");
@@ -311,7 +349,14 @@ gs_status gs_server_create(gs_context *ctx, const gs_server_cfg *cfg, gs_server 
             if (c.blend_variant >= 0) t.blend_variant = c.blend_variant;
             st = gs_frame_set_tuning(s.frame, &t);
         }
-        if (!st && cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) st = GS_ERR_CUDA;
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        for (int k = 0; k < kPrioLevels && !st; ++k) {
+            const int prio = greatest + k < least ? greatest + k : least;
+            if (cudaStreamCreateWithPriority(&s.streams[k], cudaStreamNonBlocking, prio) != cudaSuccess)
+                st = GS_ERR_CUDA;
+        }
+        s.stream = s.streams[0];
         if (!st && cudaMalloc(&s.out, sizeof(float) * image_floats(c) * c.max_batch) != cudaSuccess) st = GS_ERR_OOM;
         if (!st && cudaMalloc(&s.pairs_dev, sizeof(unsigned long long) * gs::kMaxBatch) != cudaSuccess) st = GS_ERR_OOM;
         if (!st && cudaMallocHost(&s.pairs_host, sizeof(unsigned long long) * gs::kMaxBatch) != cudaSuccess)
@@ -336,9 +381,11 @@ gs_status gs_server_destroy(gs_server *sv) {
     sv->cv.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     for (Slot &s : sv->slots) {
-        if (s.stream) cudaStreamSynchronize(s.stream);
+        for (cudaStream_t q : s.streams)
+            if (q) cudaStreamSynchronize(q);
         if (s.frame) gs_frame_destroy(s.frame);
-        if (s.stream) cudaStreamDestroy(s.stream);
+        for (cudaStream_t q : s.streams)
+            if (q) cudaStreamDestroy(q);
         cudaFree(s.out);
         cudaFree(s.pairs_dev);
         cudaFreeHost(s.pairs_host);
@@ -400,6 +447,23 @@ gs_status gs_server_wait(gs_server *sv, uint64_t ticket, int32_t timeout_ms, gs_
         out->pairs = r.pairs;
     }
     return r.status;
+}
+
+gs_status gs_server_hold(gs_server *sv, int32_t hold) {
+    if (!sv) return err(GS_ERR_INVALID_ARG, "server is NULL");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    sv->hold = hold != 0;
+    sv->cv.notify_all();
+    if (sv->hold) {
+        // the worker admits nothing more; wait for the batches in flight to be reaped
+        auto idle = [&] {
+            for (const Slot &s : sv->slots)
+                if (s.busy) return false;
+            return true;
+        };
+        while (!idle() && !sv->stop) sv->cv.wait_for(lk, std::chrono::milliseconds(1));
+    }
+    return GS_OK;
 }
 
 gs_status gs_server_get_stats(gs_server *sv, gs_server_stats *out) {

@@ -160,6 +160,31 @@ def test_elongated_gaussians_row_runs(ctx, sort_mode):
     check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
 
 
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_offscreen_centres_reaching_in(ctx, sort_mode):
+    """Centres projected just outside every image edge, footprints from a few pixels to far
+    across the border: the off-screen early-out must keep every Gaussian whose ellipse reaches a
+    tile, and only those."""
+    W, H = 240, 180
+    scene, cam = synth.random_small_scene(1500, 23, W, H, log_scale_mu=-2.0, log_scale_sigma=1.0)
+    rng = np.random.Generator(np.random.PCG64(29))
+    m = scene.means.astype(np.float64)
+    z = m[:, 2]
+    fx, cx, cy = cam.fx, cam.cx, cam.cy
+    side = rng.integers(0, 4, scene.P)
+    off = rng.uniform(0.0, 120.0, scene.P)                  # pixels beyond the edge
+    u = rng.uniform(-20.0, W + 20.0, scene.P)
+    v = rng.uniform(-20.0, H + 20.0, scene.P)
+    u = np.where(side == 0, -off, np.where(side == 1, W + off, u))
+    v = np.where(side == 2, -off, np.where(side == 3, H + off, v))
+    m[:, 0] = (u - cx) * z / fx
+    m[:, 1] = (v - cy) * z / cam.fy
+    scene.means = m.astype(np.float32)
+    ref = oracle.Frame(scene, cam, mode=32)
+    assert ref.visible > 100 and ref.N > 1000
+    check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
+
+
 def test_empty_view(ctx):
     scene, cam = synth.random_small_scene(1000, 14, 64, 48)
     cam.R = (-np.eye(3)).astype(np.float32)        # looking the other way

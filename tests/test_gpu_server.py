@@ -41,12 +41,15 @@ def setup():
     return ctx, A, B, reqs, alone
 
 
-def run(server, reqs):
+def run(server, reqs, release=None):
     outs, tickets = [], []
     for sc, cam in reqs:
         buf = torch.empty((3, cam.height, cam.width), dtype=torch.float32).pin_memory()
         outs.append(buf)
         tickets.append(server.gs_server_submit(sc, cam, buf))
+    if release is not None:
+        assert release.stats()["pending"] == len(reqs)      # held: nothing admitted yet
+        release.gs_server_hold(False)
     stats = [server.gs_server_wait(t, 60000) for t in tickets]
     return outs, stats
 
@@ -56,7 +59,8 @@ def test_batched_results_equal_alone(setup, sort_mode):
     ctx, A, B, reqs, alone = setup
     sv = gs.Server(ctx, slots=3, max_batch=8, pair_capacity=1 << 22, max_gaussians=1 << 20, max_width=256,
                    max_height=256, sort_mode=sort_mode)
-    outs, stats = run(sv, reqs)
+    sv.gs_server_hold(True)          # let the whole burst queue, so that it runs in full batches
+    outs, stats = run(sv, reqs, release=sv)
     assert all(s["status"] == 0 for s in stats)
     for o, a in zip(outs, alone):
         assert torch.equal(o, a)
