@@ -281,7 +281,9 @@ def run_serving(args, gs, ctx, room_scene, room_cams, city, city_cams):
     stream.synchronize()
     scenes, poses = [room, city], [room_cams, city_cams]
     ring = [torch.empty(3 * 3840 * 2160, dtype=torch.float32).pin_memory() for _ in range(16)]
-    batched = dict(slots=3, max_batch=8, pair_capacity=(1 << 28), max_gaussians=32_000_000, max_width=3840,
+    # batches are bounded by two 1080p images of pixels (the server's default), so two city
+    # requests at most: 2^27 pairs and 21M Gaussians cover them
+    batched = dict(slots=3, max_batch=8, pair_capacity=(1 << 27), max_gaussians=21_000_000, max_width=3840,
                    max_height=2160)
     plain = dict(plain=True, pair_capacity=(1 << 27), max_gaussians=11_000_000, max_width=3840, max_height=2160)
     out = {"workload": "resident room 1M + city 10M scenes, requests 50/50 over scenes, random pose of the "

@@ -314,7 +314,8 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys_dev, uint32_t *vals_dev,
    inside the library).  Requests -- a scene, a camera of any size up to the configured maximum,
    options and a HOST output buffer -- are queued by gs_server_submit.  Up to `slots` batches are
    in flight at once, each on its own stream with its own frame and output pool, so batches
-   overlap on the device.  When a slot is free the oldest waiting requests (at most max_batch,
+   overlap on the device; a batch starts beside a running one only once two or more requests
+   are waiting (overlap costs the older batch latency, so it is spent only on a backlog).  When a slot is free the oldest waiting requests (at most max_batch,
    at most max_gaussians Gaussians together) are admitted by pair-buffer memory: one count pass
    (geometry + exact pair counts) gives each request's pairs, and the oldest requests whose
    pairs fit pair_capacity run as one batch through gs_render_batch's single pass per stage with

@@ -65,6 +65,7 @@ struct Request {
 };
 
 constexpr int kPrioLevels = 3;
+constexpr long long kBacklog = 2;        // pending requests that justify overlapping batches
 
 struct Slot {
     cudaStream_t stream = nullptr;              // the stream of the batch in flight
@@ -263,12 +264,16 @@ void worker_main(gs_server *sv) {
     while (!sv->stop) {
         reap(sv);
         Slot *free_slot = nullptr;
-        for (Slot &s : sv->slots)
-            if (!s.busy) {
-                free_slot = &s;
-                break;
-            }
-        if (!free_slot || sv->pending.empty() || sv->hold) {
+        int busy = 0;
+        for (Slot &s : sv->slots) {
+            if (!s.busy && !free_slot) free_slot = &s;
+            busy += s.busy ? 1 : 0;
+        }
+        // Overlapping batches buy throughput at the price of the older batch's latency (younger
+        // kernels, persistent ones in particular, hold SMs it needs).  So a second batch starts
+        // beside a running one only when a backlog has formed.
+        const bool backlog = (long long)sv->pending.size() >= kBacklog;
+        if (!free_slot || sv->pending.empty() || sv->hold || (busy > 0 && !backlog)) {
             sv->cv.notify_all();
             sv->cv.wait_for(lk, std::chrono::microseconds(200));
             continue;
