@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-training", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=600)
     ap.add_argument("--no-city", action="store_true")
+    ap.add_argument("--no-pair-study", action="store_true")
     ap.add_argument("--city-steps", type=int, default=64)
     ap.add_argument("--sort-mode", type=int, default=None, help="force gs_tuning.sort_mode (skips the autotuner)")
     ap.add_argument("--blend-variant", type=int, default=None, help="force gs_tuning.blend_variant")
@@ -494,6 +495,49 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
     return res, fr, cam_of
 
 
+# ------------------------------------------------------------------------------------ pair study
+def pair_study(gs, ctx, dev_scene, P, cams, cap, stream, flush, tuning, ncams=8):
+    """The paper's comparison on the same kernels: pairs per frame with the exact tile test
+    (uncapped, and with the paper's min(3 sigma, Eq. 3) rule) against the 3DGS 3-sigma square
+    (Eq. 1, Alg. 1-2), and the frame time of the capped exact pairs against the square's (equal
+    images under the cap)."""
+    import numpy as np
+    import torch
+    W, H = cams[0].width, cams[0].height
+    fr = gs.Frame(ctx, P, cap, W, H)
+    fr.gs_frame_set_tuning(blend_variant=tuning["blend_variant"], sort_mode=tuning["sort_mode"])
+    fr.gs_frame_use_graph(True)
+    rgb = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
+    T = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    last = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    modes = {"exact": dict(), "exact_3sigma_cap": dict(cap_3sigma=True),
+             "square_3sigma": dict(cap_3sigma=True, intersect=1)}
+    out = {}
+    for name, kw in modes.items():
+        o = gs.gs_opts(**kw)
+        pairs, ms = [], []
+        with torch.cuda.stream(stream):
+            fr.gs_render(dev_scene, cams[0], rgb, T, last, o, stream=stream)     # warm-up / capture
+            for i in range(ncams):
+                flush.fill_(i & 0xff)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fr.gs_render(dev_scene, cams[i % len(cams)], rgb, T, last, o, stream=stream)
+                e1.record(stream)
+                st = fr.stats(stream)
+                if st["status"] != 0:
+                    raise RuntimeError(f"pair study {name}: status {st['status']}")
+                pairs.append(st["pairs"])
+                ms.append(e0.elapsed_time(e1))
+        out[name] = {"pairs_per_frame": float(np.mean(pairs)), "ms_per_frame": float(np.mean(ms))}
+    fr.close()
+    sq, ex = out["square_3sigma"], out["exact_3sigma_cap"]
+    out["pair_reduction_vs_square"] = 1.0 - ex["pairs_per_frame"] / sq["pairs_per_frame"]
+    out["speedup_vs_square"] = sq["ms_per_frame"] / ex["ms_per_frame"]
+    out["cameras"] = ncams
+    return out
+
+
 # ------------------------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -542,6 +586,11 @@ def run_ours(args):
                "d2h_bytes_per_step": 3 * H * W * 4, "steps": Ke,
                "note": "camera (80 B) passed by value into the kernels; rgb copied to pinned host memory"}
     fr.close()
+    study = None
+    if rank == 0 and not args.no_pair_study:
+        study = {"room" if args.config == "room" else args.config:
+                 pair_study(gs, ctx, sc, scene.P, cams, pair_capacity(args.config, args.gaussians), stream, flush,
+                            main["tuning"])}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -559,6 +608,9 @@ def run_ours(args):
             cfr.close()
             city_res = dict(workload="city-scale 10M Gaussians @3840x2160, 16 aerial + 16 street cameras "
                                      "(synthetic, seed 2)", **res)
+            if study is not None:
+                study["city"] = pair_study(gs, ctx, city, city_scene.P, city_cams, pair_capacity("city"), stream,
+                                           flush, res["tuning"])
         del city_scene
     training = serving = None
     if rank == 0 and not args.no_training and args.config == "room":
@@ -576,7 +628,7 @@ def run_ours(args):
                 "clocks": main["clocks"], "gpu_launches": main["gpu_launches"], "alu_peaks": alu,
                 "roofline": main["roofline"], "stages": main["stages"], "frame": main["frame"],
                 "wall_s": main["wall_s"], "e2e": e2e, "cpu_baseline": cpu, "city_4k": city_res,
-                "serving": serving, "differentiable": training}
+                "serving": serving, "differentiable": training, "pair_study": study}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

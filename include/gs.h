@@ -83,6 +83,10 @@ typedef struct {
     float dilation;     /* low-pass added to the 2D covariance diagonal, 0.3 px^2 */
     int32_t cap_3sigma; /* 0: t = 2 ln(alpha0/tau) (Eq. 3); 1: t = min(9, Eq. 3) (Section 4.1) */
     int32_t clamp_fov;  /* 1: clamp x/z, y/z to 1.3 tan(half fov) in the EWA Jacobian */
+    int32_t intersect;  /* 0: exact tile pairs (Alg. 3, the default); 1: the 3DGS pairs the paper
+                           compares against -- every tile of the square of radius
+                           ceil(3 sqrt(max eigenvalue of Sigma')) about the mean (Eq. 1, Alg. 1-2).
+                           Same blend; under cap_3sigma both give the same image. */
 } gs_render_opts;
 
 typedef struct {

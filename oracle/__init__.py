@@ -43,7 +43,8 @@ class OrCamera(C.Structure):
 
 class OrOpts(C.Structure):
     _fields_ = [("bg", C.c_float * 3), ("tau", C.c_float), ("alpha_max", C.c_float), ("T_min", C.c_float),
-                ("dilation", C.c_float), ("cap_3sigma", C.c_int32), ("clamp_fov", C.c_int32)]
+                ("dilation", C.c_float), ("cap_3sigma", C.c_int32), ("clamp_fov", C.c_int32),
+                ("intersect", C.c_int32)]
 
 
 REC32 = 16
@@ -137,12 +138,13 @@ def camera(cam) -> OrCamera:
 
 
 def opts(bg=(0.0, 0.0, 0.0), tau=1.0 / 255.0, alpha_max=0.99, T_min=1e-4, dilation=0.3, cap_3sigma=False,
-         clamp_fov=True) -> OrOpts:
+         clamp_fov=True, intersect=0) -> OrOpts:
+    """intersect 0: exact tile pairs (Alg. 3); 1: every tile of the 3DGS 3-sigma square (Eq. 1, Alg. 2)."""
     o = OrOpts()
     for i in range(3):
         o.bg[i] = float(bg[i])
     o.tau, o.alpha_max, o.T_min, o.dilation = float(tau), float(alpha_max), float(T_min), float(dilation)
-    o.cap_3sigma, o.clamp_fov = int(bool(cap_3sigma)), int(bool(clamp_fov))
+    o.cap_3sigma, o.clamp_fov, o.intersect = int(bool(cap_3sigma)), int(bool(clamp_fov)), int(intersect)
     return o
 
 

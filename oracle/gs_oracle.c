@@ -63,10 +63,12 @@ typedef struct {
     float dilation;         /* 0.3 px^2 low-pass */
     int32_t cap_3sigma;     /* 1: t = min(9, 2 ln(alpha0/tau)) */
     int32_t clamp_fov;      /* 1: clamp x/z, y/z to 1.3 tan(half fov) in the Jacobian */
+    int32_t intersect;      /* 0: exact tiles (Alg. 3); 1: every tile of the 3DGS square (Eq. 1, Alg. 2) */
 } OrOpts;
 
 /* FP32 per-Gaussian record (floats). */
-enum { F_U, F_V, F_A, F_B, F_C, F_T, F_Z, F_S00, F_S01, F_S11, F_ALPHA, F_R, F_G, F_BL, F_TFULL, F_PAD, REC32 };
+/* F_ALL = 1: every tile of the rectangle is paired (3DGS square); 0: the exact test decides. */
+enum { F_U, F_V, F_A, F_B, F_C, F_T, F_Z, F_S00, F_S01, F_S11, F_ALPHA, F_R, F_G, F_BL, F_TFULL, F_ALL, REC32 };
 /* FP64 per-Gaussian record (doubles). */
 enum { D_U, D_V, D_A, D_B, D_C, D_ALPHA, D_R, D_G, D_BL, D_S00, D_S01, D_S11, D_Z, D_PAD0, D_PAD1, D_PAD2, REC64 };
 
@@ -485,6 +487,19 @@ static int preprocess_one(const OrGauss *G, int64_t g, const OrCamera *cam, cons
     int tiles_x = (cam->width + TILE - 1) / TILE, tiles_y = (cam->height + TILE - 1) / TILE;
     float fx0 = floorf(((u - hx) - 1.0f) * 0.0625f), fx1 = floorf(((u + hx) + 1.0f) * 0.0625f);
     float fy0 = floorf(((v - hy) - 1.0f) * 0.0625f), fy1 = floorf(((v + hy) + 1.0f) * 0.0625f);
+    rec[F_ALL] = 0.0f;
+    if (o->intersect == 1) {
+        /* 3DGS pairs (Eq. 1; Alg. 1 radii, Alg. 2): radius r = ceil(3 sqrt(lambda_max)) of
+           Sigma' (lambda_max = mid + sqrt(mid^2 - det), the discriminant clamped at 0 against
+           rounding), and every tile of the square [u - r, u + r] x [v - r, v + r] */
+        float mid = 0.5f * (s00 + s11);
+        float disc = mid * mid - det;
+        float lam = mid + sqrtf(disc > 0.0f ? disc : 0.0f);
+        float rad = ceilf(3.0f * sqrtf(lam));
+        fx0 = floorf((u - rad) * 0.0625f); fx1 = floorf((u + rad) * 0.0625f);
+        fy0 = floorf((v - rad) * 0.0625f); fy1 = floorf((v + rad) * 0.0625f);
+        rec[F_ALL] = 1.0f;
+    }
     rec[F_U] = u; rec[F_V] = v; rec[F_A] = a; rec[F_B] = b; rec[F_C] = c; rec[F_T] = t;
     rec[F_Z] = p[2]; rec[F_S00] = s00; rec[F_S01] = s01; rec[F_S11] = s11; rec[F_ALPHA] = alpha0;
     rec[F_TFULL] = t_full;
@@ -613,6 +628,7 @@ static void tile_rect(const OrCamera *cam, int tx, int ty, float r[4])
 
 static int32_t count_one(const float *rec, const int32_t *rc, const OrCamera *cam)
 {
+    if (rec[F_ALL] != 0.0f) return (rc[1] - rc[0] + 1) * (rc[3] - rc[2] + 1);
     int32_t n = 0;
     for (int ty = rc[2]; ty <= rc[3]; ++ty)
         for (int tx = rc[0]; tx <= rc[1]; ++tx) {
@@ -647,7 +663,8 @@ int64_t or_emit_pairs(int64_t P, const float *rec32, const int32_t *rect, const 
             for (int tx = rc[0]; tx <= rc[1]; ++tx) {
                 float r[4];
                 tile_rect(cam, tx, ty, r);
-                if (or_tile_hit(rec[F_U], rec[F_V], rec[F_A], rec[F_B], rec[F_C], rec[F_T], r[0], r[1], r[2], r[3])) {
+                if (rec[F_ALL] != 0.0f ||
+                    or_tile_hit(rec[F_U], rec[F_V], rec[F_A], rec[F_B], rec[F_C], rec[F_T], r[0], r[1], r[2], r[3])) {
                     keys[o] = ((uint64_t)(ty * tiles_x + tx) << 32) | zb;
                     vals[o] = (uint32_t)g;
                     ++o;

@@ -35,6 +35,7 @@ typedef struct {
     float dilation;
     int32_t cap_3sigma;
     int32_t clamp_fov;
+    int32_t intersect;      /* pair rule of the forward; the gradient does not depend on it */
 } OrOpts;
 
 void or_sh_basis(const double d[3], double Y[16]);

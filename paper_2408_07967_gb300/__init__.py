@@ -66,7 +66,7 @@ def gs_camera_from(cam) -> _native.gs_camera:
 
 
 def gs_opts(bg=(0.0, 0.0, 0.0), tau=None, alpha_max=None, T_min=None, dilation=None, cap_3sigma=False,
-            clamp_fov=True) -> _native.gs_render_opts:
+            clamp_fov=True, intersect=0) -> _native.gs_render_opts:
     o = _native.gs_render_opts()
     _check(lib().gs_default_opts(C.byref(o)))
     for i in range(3):
@@ -81,6 +81,7 @@ def gs_opts(bg=(0.0, 0.0, 0.0), tau=None, alpha_max=None, T_min=None, dilation=N
         o.dilation = float(dilation)
     o.cap_3sigma = int(bool(cap_3sigma))
     o.clamp_fov = int(bool(clamp_fov))
+    o.intersect = int(intersect)    # 0 exact tile pairs; 1 the 3DGS 3-sigma square (the paper's baseline)
     return o
 
 

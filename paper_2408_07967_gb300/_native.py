@@ -24,7 +24,8 @@ class gs_gaussians(C.Structure):
 
 class gs_render_opts(C.Structure):
     _fields_ = [("bg", C.c_float * 3), ("tau", C.c_float), ("alpha_max", C.c_float), ("T_min", C.c_float),
-                ("dilation", C.c_float), ("cap_3sigma", C.c_int32), ("clamp_fov", C.c_int32)]
+                ("dilation", C.c_float), ("cap_3sigma", C.c_int32), ("clamp_fov", C.c_int32),
+                ("intersect", C.c_int32)]
 
 
 class gs_frame_stats(C.Structure):

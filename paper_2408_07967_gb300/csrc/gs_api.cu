@@ -78,6 +78,7 @@ Opts make_opts(const gs_render_opts *o) {
     r.dilation = o->dilation;
     r.cap_3sigma = o->cap_3sigma;
     r.clamp_fov = o->clamp_fov;
+    r.intersect = o->intersect;
     return r;
 }
 
@@ -162,6 +163,7 @@ gs_status gs_default_opts(gs_render_opts *o) {
     o->dilation = 0.3f;
     o->cap_3sigma = 0;
     o->clamp_fov = 1;
+    o->intersect = 0;
     return GS_OK;
 }
 

@@ -38,6 +38,7 @@ struct Opts {
     float bg[3];
     float tau, alpha_max, T_min, dilation;
     int cap_3sigma, clamp_fov;
+    int intersect;           // 0 exact tiles, 1 every tile of the 3DGS 3-sigma square
 };
 
 // Internal scene layout, three arrays sized by how sparsely each is read:

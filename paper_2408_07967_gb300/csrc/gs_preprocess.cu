@@ -167,8 +167,14 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
             m0 += e0 * e0;
             m1 += e1 * e1;
         }
-        const float hxb = sqrtf(t * (smax * smax * m0 + o.dilation)) * 1.02f + 2.0f;
-        const float hyb = sqrtf(t * (smax * smax * m1 + o.dilation)) * 1.02f + 2.0f;
+        float hxb = sqrtf(t * (smax * smax * m0 + o.dilation)) * 1.02f + 2.0f;
+        float hyb = sqrtf(t * (smax * smax * m1 + o.dilation)) * 1.02f + 2.0f;
+        if (o.intersect == 1) {
+            // 3DGS square: r <= ceil(3 sqrt(trace Sigma')), trace <= s_max^2 (|M0|^2 + |M1|^2) + 2 dilation
+            const float rb = 3.0f * sqrtf(smax * smax * (m0 + m1) + 2.0f * o.dilation) * 1.02f + 3.0f;
+            hxb = rb;
+            hyb = rb;
+        }
         const float uu = cam.fx * p[0] * iz + cam.cx, vv = cam.fy * p[1] * iz + cam.cy;
         if (uu + hxb < 0.0f || uu - hxb >= (float)(kTile * cam.tiles_x) || vv + hyb < 0.0f ||
             vv - hyb >= (float)(kTile * cam.tiles_y))
@@ -263,10 +269,22 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
     // tight box of {q <= t}: half extents sqrt(t Sigma'00), sqrt(t Sigma'11), padded by 1 px
     const float hx = fsqrt(fmul(t, s00));
     const float hy = fsqrt(fmul(t, s11));
-    const float fx0 = floorf(fmul(fsub(fsub(u, hx), 1.0f), 0.0625f));
-    const float fx1 = floorf(fmul(fadd(fadd(u, hx), 1.0f), 0.0625f));
-    const float fy0 = floorf(fmul(fsub(fsub(v, hy), 1.0f), 0.0625f));
-    const float fy1 = floorf(fmul(fadd(fadd(v, hy), 1.0f), 0.0625f));
+    float fx0 = floorf(fmul(fsub(fsub(u, hx), 1.0f), 0.0625f));
+    float fx1 = floorf(fmul(fadd(fadd(u, hx), 1.0f), 0.0625f));
+    float fy0 = floorf(fmul(fsub(fsub(v, hy), 1.0f), 0.0625f));
+    float fy1 = floorf(fmul(fadd(fadd(v, hy), 1.0f), 0.0625f));
+    if (o.intersect == 1) {
+        // 3DGS pairs (Eq. 1; Alg. 1 radii; Alg. 2): r = ceil(3 sqrt(lambda_max)) of Sigma', every
+        // tile of [u - r, u + r] x [v - r, v + r] (the discriminant clamped at 0 against rounding)
+        const float mid = fmul(0.5f, fadd(s00, s11));
+        const float disc = fsub(fmul(mid, mid), det);
+        const float lam = fadd(mid, fsqrt(disc > 0.0f ? disc : 0.0f));
+        const float rad = ceilf(fmul(3.0f, fsqrt(lam)));
+        fx0 = floorf(fmul(fsub(u, rad), 0.0625f));
+        fx1 = floorf(fmul(fadd(u, rad), 0.0625f));
+        fy0 = floorf(fmul(fsub(v, rad), 0.0625f));
+        fy1 = floorf(fmul(fadd(v, rad), 0.0625f));
+    }
     const float mxx = (float)(cam.tiles_x - 1), mxy = (float)(cam.tiles_y - 1);
     if (!(fx1 >= 0.0f) || !(fy1 >= 0.0f) || !(fx0 <= mxx) || !(fy0 <= mxy)) return false;
     G.tx0 = fx0 < 0.0f ? 0 : (int)fx0;
@@ -344,6 +362,7 @@ __device__ __forceinline__ Unit unit_of(const PreSmem &S, int slot) {
 }
 
 __device__ __forceinline__ unsigned unit_hits(const PreSmem &S, const BatchDesc &B, const Unit &U) {
+    if (B.r[S.req[U.g]].opt.intersect == 1) return (1u << U.n) - 1u;    // 3DGS square: every tile
     const Cam &cam = B.r[S.req[U.g]].cam;
     return run_hits(cam.W, cam.H, S.u[U.g], S.v[U.g], S.a[U.g], S.b[U.g], S.c[U.g], S.t[U.g], U.tx, U.n, U.ty);
 }
@@ -738,8 +757,9 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
                 const int dy = k / segs, seg = k - dy * segs;
                 tx = g2.x + seg * kSeg;
                 ty = g2.y + dy;
-                m = run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, min(kSeg, g2.z - seg * kSeg),
-                             ty);
+                const int nrun = min(kSeg, g2.z - seg * kSeg);
+                m = R.opt.intersect == 1 ? (1u << nrun) - 1u
+                                         : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, nrun, ty);
             }
             // block exclusive scan of the hit counts
             const unsigned c = (unsigned)__popc(m);

@@ -185,6 +185,23 @@ def test_offscreen_centres_reaching_in(ctx, sort_mode):
     check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
 
 
+@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("cap", [False, True])
+def test_3dgs_square_pairs(ctx, sort_mode, cap):
+    """The paper's baseline pairs (every tile of the 3-sigma square, Eq. 1, Alg. 1-2): pair lists
+    bit-exact against the oracle; under the 3-sigma cap the image equals the exact pairs' image
+    bit for bit, with fewer pairs for the exact test."""
+    scene, cam = synth.random_small_scene(3000, 41, 200, 150, log_scale_mu=-2.4, log_scale_sigma=1.0)
+    kw = dict(cap_3sigma=cap)
+    ref = oracle.Frame(scene, cam, oracle.opts(intersect=1, **kw), mode=64)
+    res = run_gpu(ctx, scene, cam, dict(intersect=1, **kw), sort_mode=sort_mode)
+    check(res, ref)
+    ex = run_gpu(ctx, scene, cam, dict(intersect=0, **kw), sort_mode=sort_mode)
+    assert ex["stats"]["pairs"] < res["stats"]["pairs"]
+    if cap:
+        assert np.array_equal(ex["rgb"], res["rgb"]) and np.array_equal(ex["T"], res["T"])
+
+
 def test_empty_view(ctx):
     scene, cam = synth.random_small_scene(1000, 14, 64, 48)
     cam.R = (-np.eye(3)).astype(np.float32)        # looking the other way

@@ -435,6 +435,78 @@ def test_exact_pairs_subset_of_3dgs_aabb(oracle_lib):
     assert f.N < total_aabb
 
 
+def last_gaussian(fr, cam):
+    """Gaussian id of each pixel's last contributor (-1 for none) from the list positions."""
+    tx_n, _ = oracle.tiles_of(cam)
+    ty = np.arange(cam.height)[:, None] // 16
+    tx = np.arange(cam.width)[None, :] // 16
+    start = fr.ranges[ty * tx_n + tx, 0]
+    last = fr.last.astype(np.int64)
+    idx = np.where(last > 0, start + last - 1, 0)
+    return np.where(last > 0, fr.vals[idx].astype(np.int64), -1)
+
+
+def test_aabb_mode_is_the_3sigma_square_closed_form(oracle_lib):
+    """3DGS pairs (Eq. 1; Alg. 1 radii = ceil(3 sqrt(max eigenvalue)); Alg. 2): an isotropic
+    Gaussian of scale s at depth z has Sigma' = ((f s / z)^2 + 0.3) I at the image centre, so
+    r = ceil(3 sqrt((f s / z)^2 + 0.3)) and the pairs are every tile of [u - r, u + r]^2 --
+    counted here from the closed form alone (offsets small enough that the Jacobian's x/z term
+    changes no radius)."""
+    W = H = 256
+    f, z = 100.0, 4.0
+    for s_ in (0.05, 0.13, 0.31, 0.62):
+        for du in (0.0, 5.3, -9.7):
+            cam = cam_simple(W, H, f=f)
+            sc = scene_of([[du * z / f, 0.0, z]], [[s_, s_, s_]], opac=[0.9])
+            fr = oracle.Frame(sc, cam, oracle.opts(intersect=1), mode=32)
+            sig2 = (f * s_ / z) ** 2 + 0.3
+            r = math.ceil(3.0 * math.sqrt(sig2))
+            u, v = W / 2 + du, H / 2
+            tx = range(max(0, math.floor((u - r) / 16)), min(W // 16 - 1, math.floor((u + r) / 16)) + 1)
+            ty = range(max(0, math.floor((v - r) / 16)), min(H // 16 - 1, math.floor((v + r) / 16)) + 1)
+            expect = sorted(y * (W // 16) + x for y in ty for x in tx)
+            got = sorted((fr.keys >> np.uint64(32)).astype(np.int64).tolist())
+            assert got == expect, (s_, du, r)
+
+
+def test_aabb_mode_superset_same_image_under_3sigma_cap(oracle_lib):
+    """Under the paper's min(3 sigma, Eq. 3) rule every contribution (q <= t <= 9) lies in the
+    3-sigma ellipse, which the 3DGS square contains: the exact pairs are a subset of the square's,
+    fewer, and the image is the same bit for bit (both precisions).  Brute force: every pixel with
+    q <= 9 of a Gaussian falls in one of its square's tiles."""
+    sc, cam = synth.random_small_scene(500, 31, 176, 144, log_scale_mu=-2.3, log_scale_sigma=0.9)
+    for mode in (32, 64):
+        fe = oracle.Frame(sc, cam, oracle.opts(cap_3sigma=True), mode=mode)
+        fa = oracle.Frame(sc, cam, oracle.opts(cap_3sigma=True, intersect=1), mode=mode)
+        assert fe.N < fa.N
+        assert np.array_equal(fe.rgb, fa.rgb) and np.array_equal(fe.T, fa.T)
+        # `last` is a position in the tile's list: compare the Gaussians it names
+        assert np.array_equal(last_gaussian(fe, cam), last_gaussian(fa, cam))
+    tx_n, _ = oracle.tiles_of(cam)
+    pe = {}
+    for k, v in zip(fe.keys_unsorted >> np.uint64(32), fe.vals_unsorted):
+        pe.setdefault(int(v), set()).add(int(k))
+    pa = {}
+    for k, v in zip(fa.keys_unsorted >> np.uint64(32), fa.vals_unsorted):
+        pa.setdefault(int(v), set()).add(int(k))
+    for g, tiles in pe.items():
+        assert tiles <= pa.get(g, set()), g
+    D = oracle.D
+    px = np.arange(cam.width) + 0.5
+    py = np.arange(cam.height) + 0.5
+    tiles_of_px = (py[:, None] // 16).astype(int) * tx_n + (px[None, :] // 16).astype(int)
+    checked = 0
+    for g in list(pa)[:150]:
+        r = fa.rec64[g]
+        dx = px[None, :] - r[D["U"]]
+        dy = py[:, None] - r[D["V"]]
+        q = r[D["A"]] * dx * dx + 2 * r[D["B"]] * dx * dy + r[D["C"]] * dy * dy
+        inside = set(np.unique(tiles_of_px[q <= 9.0 * (1 - 1e-4)]).tolist())
+        assert inside <= pa[g], g
+        checked += len(inside)
+    assert checked > 100
+
+
 # ------------------------------------------------------------------ activation
 
 def test_raw_parameters_activate_with_own_exp(oracle_lib):
