@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--city-steps", type=int, default=64)
     ap.add_argument("--sort-mode", type=int, default=None, help="force gs_tuning.sort_mode (skips the autotuner)")
     ap.add_argument("--blend-variant", type=int, default=None, help="force gs_tuning.blend_variant")
+    ap.add_argument("--sort-algo", type=int, default=None, help="force gs_tuning.sort_algo")
     return ap.parse_args()
 
 
@@ -372,8 +373,8 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
     W, H = cams[0].width, cams[0].height
     fr = gs.Frame(ctx, P, cap, W, H)
     fr.gs_frame_use_graph(True)
-    if args.sort_mode is not None or args.blend_variant is not None:
-        fr.gs_frame_set_tuning(blend_variant=args.blend_variant, sort_mode=args.sort_mode)
+    if args.sort_mode is not None or args.blend_variant is not None or args.sort_algo is not None:
+        fr.gs_frame_set_tuning(blend_variant=args.blend_variant, sort_mode=args.sort_mode, sort_algo=args.sort_algo)
         tuning = fr.gs_frame_get_tuning()
         tuning["source"] = "forced"
     else:
@@ -505,7 +506,8 @@ def pair_study(gs, ctx, dev_scene, P, cams, cap, stream, flush, tuning, ncams=8)
     import torch
     W, H = cams[0].width, cams[0].height
     fr = gs.Frame(ctx, P, cap, W, H)
-    fr.gs_frame_set_tuning(blend_variant=tuning["blend_variant"], sort_mode=tuning["sort_mode"])
+    fr.gs_frame_set_tuning(blend_variant=tuning["blend_variant"], sort_mode=tuning["sort_mode"],
+                           sort_algo=tuning["sort_algo"])
     fr.gs_frame_use_graph(True)
     rgb = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
     T = torch.empty((H, W), dtype=torch.float32, device="cuda")

@@ -224,20 +224,25 @@ gs_status gs_frame_use_graph(gs_frame *frame, int32_t enable);
    keys and sorted over 32 + ceil(log2 tiles) bits; sort_mode 1 (two-level): the paired
    Gaussians are sorted once by depth (32-bit keys), pairs are emitted in that order with the
    tile id alone as a 32-bit key, and a stable sort over ceil(log2 tiles) bits finishes -- the
-   same (tile, depth, id) order with far fewer bytes moved.  Results are bit-identical across
-   all choices.  GS_ERR_INVALID_ARG for out-of-range values. */
+   same (tile, depth, id) order with far fewer bytes moved.  sort_algo picks how each radix pass
+   is carried out (below).  Results are bit-identical across all choices.  GS_ERR_INVALID_ARG for
+   out-of-range values. */
 typedef struct {
     int32_t blend_variant;
     int32_t sort_mode;
-    int32_t reserved[6];
+    int32_t sort_algo;     /* 0: onesweep passes (decoupled look-back between tiles); 1: reduce-then-
+                              scan passes (per-tile digit counts, a scan across tiles, then the
+                              scatter: keys read twice, no tile waits on another) */
+    int32_t reserved[5];
 } gs_tuning;
 gs_status gs_frame_set_tuning(gs_frame *frame, const gs_tuning *tuning);
 gs_status gs_frame_get_tuning(const gs_frame *frame, gs_tuning *tuning);
 
 /* Autotuner: picks the frame's gs_tuning for rendering `scene` at the size of cams[0].  With
-   cache_path non-NULL, a line "gs-autotune-v1 <device> <P> <W> <H> <blend_variant> <sort_mode>"
-   matching this device, scene size and image size is reused when present; otherwise both sort
-   modes are timed (preprocess + sort + ranges) and then every blend_variant (blend), each over the
+   cache_path non-NULL, a line "gs-autotune-v2 <device> <P> <W> <H> <blend_variant> <sort_mode>
+   <sort_algo>" matching this device, scene size and image size is reused when present; otherwise
+   every (sort_mode, sort_algo) is timed (preprocess + sort + ranges) and then every blend_variant
+   (blend), each over the
    ncams cameras after one warm-up render with CUDA-event stage times, and the fastest choices are
    kept and appended to the cache file.  The frame
    is left with the chosen tuning, which is also written to *out (nullable).  Synchronises

@@ -227,19 +227,22 @@ class Frame:
     def gs_frame_use_graph(self, enable: bool):
         _check(lib().gs_frame_use_graph(self.h, int(bool(enable))))
 
-    def gs_frame_set_tuning(self, blend_variant: int | None = None, sort_mode: int | None = None):
+    def gs_frame_set_tuning(self, blend_variant: int | None = None, sort_mode: int | None = None,
+                            sort_algo: int | None = None):
         t = _native.gs_tuning()
         _check(lib().gs_frame_get_tuning(self.h, C.byref(t)))
         if blend_variant is not None:
             t.blend_variant = int(blend_variant)
         if sort_mode is not None:
             t.sort_mode = int(sort_mode)
+        if sort_algo is not None:
+            t.sort_algo = int(sort_algo)
         _check(lib().gs_frame_set_tuning(self.h, C.byref(t)))
 
     def gs_frame_get_tuning(self) -> dict:
         t = _native.gs_tuning()
         _check(lib().gs_frame_get_tuning(self.h, C.byref(t)))
-        return {"blend_variant": t.blend_variant, "sort_mode": t.sort_mode}
+        return {"blend_variant": t.blend_variant, "sort_mode": t.sort_mode, "sort_algo": t.sort_algo}
 
     def gs_autotune(self, scene: Scene, cams, opts=None, cache_path=None, stream=None) -> dict:
         """Pick the fastest launch shape for this scene and image size (cached per device, P, W, H)."""
@@ -248,7 +251,7 @@ class Frame:
         t = _native.gs_tuning()
         path = None if cache_path is None else str(cache_path).encode()
         _check(lib().gs_autotune(self.h, scene.h, arr, len(cams), C.byref(o), path, C.byref(t), _stream(stream)))
-        return {"blend_variant": t.blend_variant, "sort_mode": t.sort_mode}
+        return {"blend_variant": t.blend_variant, "sort_mode": t.sort_mode, "sort_algo": t.sort_algo}
 
     def gs_frame_set_counting(self, enable: bool):
         _check(lib().gs_frame_set_counting(self.h, int(bool(enable))))

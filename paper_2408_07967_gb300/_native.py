@@ -57,7 +57,8 @@ class gs_server_stats(C.Structure):
 
 
 class gs_tuning(C.Structure):
-    _fields_ = [("blend_variant", C.c_int32), ("sort_mode", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("blend_variant", C.c_int32), ("sort_mode", C.c_int32), ("sort_algo", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class gs_alu_peaks(C.Structure):

@@ -136,7 +136,7 @@ struct gs_frame {
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // frame-owned outputs for gs_render_host (allocated on first use)
     void *out_mem = nullptr;
-    gs_tuning tuning{1, 1, {0, 0, 0, 0, 0, 0}};
+    gs_tuning tuning{1, 1, 0, {0, 0, 0, 0, 0}};
     int counting = 0;
     // camera and options of the last preprocess (used by the backward)
     Cam cam{};
@@ -312,6 +312,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     size_t o_geo0 = cv.take<float4>(max_g), o_geo1 = cv.take<float4>(max_g), o_geo2 = cv.take<int4>(max_g);
     size_t o_hist = cv.take<unsigned>(8 * 256), o_offs = cv.take<unsigned>(8 * 256);
     size_t o_desc = cv.take<unsigned long long>(f->sort.max_tiles * 256);
+    size_t o_rts = cv.take<unsigned>(f->sort.max_tiles * 256);
     size_t o_ctr = cv.take<FrameCounters>(1);
     f->bytes = align_up(cv.off, 256);
     cudaError_t e = cudaMalloc(&f->mem, f->bytes);
@@ -345,6 +346,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     f->sort.hist = (unsigned *)(b + o_hist);
     f->sort.offs = (unsigned *)(b + o_offs);
     f->sort.desc = (unsigned long long *)(b + o_desc);
+    f->sort.counts = (unsigned *)(b + o_rts);
     f->ctr = (FrameCounters *)(b + o_ctr);
     // zero scratch that must start cleared (histograms, descriptors, counters, tile starts)
     cudaMemset(b + o_starts, 0, f->bytes - o_starts);
@@ -386,11 +388,15 @@ gs_status gs_frame_set_tuning(gs_frame *f, const gs_tuning *t) {
     if (t->blend_variant < 0 || t->blend_variant >= blend_variant_count())
         return fail(GS_ERR_INVALID_ARG, "blend_variant %d out of range", t->blend_variant);
     if (t->sort_mode < 0 || t->sort_mode > 1) return fail(GS_ERR_INVALID_ARG, "sort_mode %d not 0 or 1", t->sort_mode);
-    if ((t->blend_variant != f->tuning.blend_variant || t->sort_mode != f->tuning.sort_mode) && f->exec) {
+    if (t->sort_algo < 0 || t->sort_algo > 1) return fail(GS_ERR_INVALID_ARG, "sort_algo %d not 0 or 1", t->sort_algo);
+    if ((t->blend_variant != f->tuning.blend_variant || t->sort_mode != f->tuning.sort_mode ||
+         t->sort_algo != f->tuning.sort_algo) &&
+        f->exec) {
         cudaGraphExecDestroy(f->exec);
         f->exec = nullptr;
     }
     f->tuning = *t;
+    f->sort.algo = t->sort_algo;
     return GS_OK;
 }
 
@@ -888,20 +894,23 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
     for (char &ch : dev)
         if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
     char key[256];
-    snprintf(key, sizeof(key), "gs-autotune-v1 %s %lld %d %d", dev.c_str(), s->P, cams[0].width, cams[0].height);
+    snprintf(key, sizeof(key), "gs-autotune-v2 %s %lld %d %d", dev.c_str(), s->P, cams[0].width, cams[0].height);
     if (cache_path) {
         FILE *fp = fopen(cache_path, "r");
         if (fp) {
             char line[512];
-            int found_v = -1, found_m = -1;
+            int found_v = -1, found_m = -1, found_a = -1;
             const size_t kl = strlen(key);
             while (fgets(line, sizeof(line), fp))
-                if (strncmp(line, key, kl) == 0 && line[kl] == ' ') sscanf(line + kl + 1, "%d %d", &found_v, &found_m);
+                if (strncmp(line, key, kl) == 0 && line[kl] == ' ')
+                    sscanf(line + kl + 1, "%d %d %d", &found_v, &found_m, &found_a);
             fclose(fp);
-            if (found_v >= 0 && found_v < blend_variant_count() && (found_m == 0 || found_m == 1)) {
+            if (found_v >= 0 && found_v < blend_variant_count() && (found_m == 0 || found_m == 1) &&
+                (found_a == 0 || found_a == 1)) {
                 gs_tuning t = f->tuning;
                 t.blend_variant = found_v;
                 t.sort_mode = found_m;
+                t.sort_algo = found_a;
                 gs_status st = gs_frame_set_tuning(f, &t);
                 if (st) return st;
                 if (out) *out = f->tuning;
@@ -929,26 +938,30 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
         }
         return GS_OK;
     };
-    // 1) ordering: preprocess + sort + ranges time of each sort mode
-    int best_mode = f->tuning.sort_mode;
+    // 1) ordering: preprocess + sort + ranges time of each sort mode and sort algorithm
+    int best_mode = f->tuning.sort_mode, best_algo = f->tuning.sort_algo;
     float best_ms = 1e30f;
-    for (int m = 0; m <= 1; ++m) {
-        gs_tuning t = f->tuning;
-        t.sort_mode = m;
-        if ((st = gs_frame_set_tuning(f, &t))) return st;
-        float ms[4];
-        if ((st = timed(ms))) return st;
-        if (ms[0] + ms[1] + ms[2] < best_ms) {
-            best_ms = ms[0] + ms[1] + ms[2];
-            best_mode = m;
+    for (int m = 0; m <= 1; ++m)
+        for (int a = 0; a <= 1; ++a) {
+            gs_tuning t = f->tuning;
+            t.sort_mode = m;
+            t.sort_algo = a;
+            if ((st = gs_frame_set_tuning(f, &t))) return st;
+            float ms[4];
+            if ((st = timed(ms))) return st;
+            if (ms[0] + ms[1] + ms[2] < best_ms) {
+                best_ms = ms[0] + ms[1] + ms[2];
+                best_mode = m;
+                best_algo = a;
+            }
         }
-    }
     // 2) blend launch shape
     int best = f->tuning.blend_variant;
     best_ms = 1e30f;
     for (int v = 0; v < blend_variant_count(); ++v) {
         gs_tuning t = f->tuning;
         t.sort_mode = best_mode;
+        t.sort_algo = best_algo;
         t.blend_variant = v;
         if ((st = gs_frame_set_tuning(f, &t))) return st;
         float ms[4];
@@ -962,12 +975,13 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
     gs_tuning t = f->tuning;
     t.blend_variant = best;
     t.sort_mode = best_mode;
+    t.sort_algo = best_algo;
     if ((st = gs_frame_set_tuning(f, &t))) return st;
     if ((st = gs_frame_enable_timing(f, timing_before))) return st;
     if (cache_path) {
         FILE *fp = fopen(cache_path, "a");
         if (fp) {
-            fprintf(fp, "%s %d %d\n", key, best, best_mode);
+            fprintf(fp, "%s %d %d %d\n", key, best, best_mode, best_algo);
             fclose(fp);
         }
     }

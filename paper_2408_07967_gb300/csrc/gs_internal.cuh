@@ -348,6 +348,8 @@ struct SortScratch {
     unsigned *offs;                  // [8][256] exclusive digit offsets
     unsigned long long *desc;        // [max_tiles * 256] epoch-tagged look-back descriptors
     long long max_tiles;
+    unsigned *counts = nullptr;      // [256][max_tiles] per-tile digit counts (reduce-then-scan)
+    int algo = 0;                    // 0 onesweep (decoupled look-back), 1 reduce-then-scan
 };
 
 int sort_tile_items();

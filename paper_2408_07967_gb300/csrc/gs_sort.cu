@@ -36,6 +36,19 @@ __device__ __forceinline__ long long pair_count(const unsigned long long *n_dev,
     return n < cap ? n : cap;
 }
 
+// Lanes of the warp holding the same 8-bit digit, from eight ballots (one per digit bit): plain
+// ALU work at full rate, where a hardware match over 32-bit values is a long-latency operation.
+__device__ __forceinline__ unsigned match_digit(unsigned d) {
+    unsigned m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const unsigned bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bal : ~bal;
+    }
+    return m;
+}
+
 // ------------------------------------------------------------------------------------------ histogram
 template <class K>
 __global__ void __launch_bounds__(512) k_sort_hist(const K *keys, const unsigned long long *n_dev,
@@ -45,7 +58,20 @@ __global__ void __launch_bounds__(512) k_sort_hist(const K *keys, const unsigned
     __syncthreads();
     const long long n = pair_count(n_dev, n_host, cap);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    // four keys per thread and step, loaded before any is counted (keys are 16-byte aligned
+    // whenever the base is; a misaligned base falls back to single keys)
+    constexpr int V = 4;
+    const bool vec = ((uintptr_t)keys & 15u) == 0;
+    const long long nv = vec ? n / V : 0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nv; c += stride) {
+        K k[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) k[j] = __ldg(keys + c * V + j);
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+            for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k[j] >> (8 * p)) & 0xffu)], 1u);
+    }
+    for (long long i = nv * V + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const K k = keys[i];
         for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k >> (8 * p)) & 0xffu)], 1u);
     }
@@ -232,7 +258,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-            const unsigned peers = __match_any_sync(FULL, d);
+            const unsigned peers = __match_any_sync(FULL, d);   // latency: it precedes the publish
             const unsigned before = __popc(peers & lt_mask);
             const unsigned bb = S.whist[warp][d];
             __syncwarp();
@@ -359,6 +385,220 @@ static int scatter_grid() {
     return grid;
 }
 
+// ------------------------------------------------------------------------------------------ reduce-then-scan
+// The same stable LSD passes without any inter-CTA waiting: per pass, k_rts_count writes every
+// tile's 256 digit counts (digit-major, so that k_rts_scan reads rows), k_rts_scan turns each
+// digit's row into exclusive offsets across tiles plus the digit's global offset, and
+// k_rts_scatter ranks each tile exactly as the onesweep CTA does and writes it at those offsets.
+// It reads the keys twice per pass, but no tile ever waits on a predecessor, so large sorts run at
+// the memory system's pace instead of the look-back's.
+template <class K>
+__global__ void __launch_bounds__(kSortThreads) k_rts_count(const K *__restrict__ kin, const unsigned long long *n_dev,
+                                                            long long n_host, long long cap, int pass,
+                                                            unsigned *counts, long long stride) {
+    __shared__ unsigned s_h[256];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int shift = 8 * pass;
+    const long long n = pair_count(n_dev, n_host, cap);
+    const long long ntiles = (n + kSortTile - 1) / kSortTile;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        s_h[tid] = 0;
+        __syncthreads();
+        const long long base = tile * kSortTile;
+        unsigned dg[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {        // all loads in flight before any ranking
+            const long long idx = base + i * kSortThreads + tid;
+            dg[i] = idx < n ? (unsigned)(__ldg(kin + idx) >> shift) & 0xffu : 256u;
+        }
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i)
+            if (dg[i] < 256u) atomicAdd(&s_h[dg[i]], 1u);
+        __syncthreads();
+        counts[(long long)tid * stride + tile] = s_h[tid];
+        __syncthreads();
+    }
+}
+
+// One CTA per digit: counts[d][t] becomes the sum of counts[d][t'] over t' < t, and the row's total
+// goes to tot[d] (the scatter turns the 256 totals into the digits' global offsets).
+constexpr int kRtsScanThreads = 1024;
+constexpr int kRtsScanRun = 8;
+__global__ void __launch_bounds__(kRtsScanThreads) k_rts_scan(unsigned *counts, long long stride,
+                                                              const unsigned long long *n_dev, long long n_host,
+                                                              long long cap, unsigned *tot_out) {
+    __shared__ unsigned s_w[kRtsScanThreads / 32];
+    __shared__ unsigned s_carry;
+    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long n = pair_count(n_dev, n_host, cap);
+    const long long ntiles = (n + kSortTile - 1) / kSortTile;
+    unsigned *row = counts + (long long)d * stride;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (long long b0 = 0; b0 < ntiles; b0 += (long long)kRtsScanThreads * kRtsScanRun) {
+        const long long my0 = b0 + (long long)tid * kRtsScanRun;
+        unsigned v[kRtsScanRun];
+        unsigned sum = 0;
+#pragma unroll
+        for (int r = 0; r < kRtsScanRun; ++r) {
+            v[r] = my0 + r < ntiles ? row[my0 + r] : 0u;
+            sum += v[r];
+        }
+        unsigned incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        unsigned wex = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kRtsScanThreads / 32; ++w) {
+            const unsigned x = s_w[w];
+            wex += w < warp ? x : 0u;
+            tot += x;
+        }
+        unsigned run = s_carry + wex + incl - sum;
+#pragma unroll
+        for (int r = 0; r < kRtsScanRun; ++r) {
+            if (my0 + r < ntiles) row[my0 + r] = run;
+            run += v[r];
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += tot;
+        __syncthreads();
+    }
+    if (tid == 0) tot_out[d] = s_carry;
+}
+
+template <class K>
+struct RtsSmem {
+    K keys[kSortTile];
+    unsigned vals[kSortTile];
+    unsigned whist[kSortWarps][256];
+    unsigned local_off[256];
+    unsigned gbase[256];
+    unsigned wsum[kSortWarps];
+};
+
+template <class K>
+__global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__restrict__ kin,
+                                                              const unsigned *__restrict__ vin, K *__restrict__ kout,
+                                                              unsigned *__restrict__ vout,
+                                                              const unsigned long long *n_dev, long long n_host,
+                                                              long long cap, int pass, const unsigned *offs_t,
+                                                              long long stride, const unsigned *tot) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RtsSmem<K> &S = *reinterpret_cast<RtsSmem<K> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned FULL = 0xffffffffu;
+    const int shift = 8 * pass;
+    const long long n = pair_count(n_dev, n_host, cap);
+    const long long ntiles = (n + kSortTile - 1) / kSortTile;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // global offset of digit tid: exclusive scan of the digit totals
+    unsigned dbase;
+    {
+        const unsigned c = tot[tid];
+        unsigned incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) S.wsum[warp] = incl;
+        __syncthreads();
+        unsigned wex = 0;
+        for (int w = 0; w < warp; ++w) wex += S.wsum[w];
+        dbase = wex + incl - c;
+        __syncthreads();
+    }
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+        S.gbase[tid] = dbase + offs_t[(long long)tid * stride + tile];
+        __syncthreads();
+        const long long tbase = tile * kSortTile;
+        const long long wbase = tbase + (long long)warp * (32 * kSortItems);
+        K k[kSortItems];
+        unsigned v[kSortItems];
+        unsigned rank[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const long long idx = wbase + i * 32 + lane;
+            if (idx < n) {
+                k[i] = kin[idx];
+                v[i] = vin[idx];
+            } else {
+                k[i] = (K)~(K)0;
+                v[i] = 0u;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+            const unsigned peers = match_digit(d);
+            const unsigned before = __popc(peers & lt_mask);
+            const unsigned bb = S.whist[warp][d];
+            __syncwarp();
+            rank[i] = bb + before;
+            if (before == 0) S.whist[warp][d] = bb + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        unsigned cnt = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const unsigned c = S.whist[w][tid];
+            S.whist[w][tid] = cnt;
+            cnt += c;
+        }
+        unsigned incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) S.wsum[warp] = incl;
+        __syncthreads();
+        unsigned wex = 0;
+        for (int w = 0; w < warp; ++w) wex += S.wsum[w];
+        S.local_off[tid] = wex + incl - cnt;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+            const unsigned pos = S.local_off[d] + S.whist[warp][d] + rank[i];
+            S.keys[pos] = k[i];
+            S.vals[pos] = v[i];
+        }
+        __syncthreads();
+        const long long valid_here = min((long long)kSortTile, n - tbase);
+        for (int s = tid; s < valid_here; s += kSortThreads) {
+            const K key = S.keys[s];
+            const unsigned d = (unsigned)(key >> shift) & 0xffu;
+            const unsigned long long dst = (unsigned long long)S.gbase[d] + (unsigned long long)(s - S.local_off[d]);
+            kout[dst] = key;
+            vout[dst] = S.vals[s];
+        }
+        __syncthreads();
+    }
+}
+
+template <class K>
+static int rts_scatter_grid() {
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_rts_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RtsSmem<K>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rts_scatter<K>, kSortThreads, sizeof(RtsSmem<K>));
+        grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    return grid;
+}
+
 template <class K>
 static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tmp, const unsigned long long *n_dev,
                          long long n_host, long long cap, int end_bit, const SortScratch &scr, FrameCounters *ctr,
@@ -368,9 +608,30 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long max_tiles = sort_max_tiles_for(cap);
+    if (scr.algo == 1 && scr.counts && max_tiles <= scr.max_tiles) {
+        const int cgrid = (int)min((long long)sms * 8, max_tiles > 0 ? max_tiles : 1);
+        const int rgrid = (int)min((long long)rts_scatter_grid<K>(), max_tiles > 0 ? max_tiles : 1);
+        K *ka = keys, *kb = keys_tmp;
+        unsigned *va = vals, *vb = vals_tmp;
+        for (int p = 0; p < passes; ++p) {
+            k_rts_count<K><<<cgrid, kSortThreads, 0, s>>>(ka, n_dev, n_host, cap, p, scr.counts, scr.max_tiles);
+            k_rts_scan<<<256, kRtsScanThreads, 0, s>>>(scr.counts, scr.max_tiles, n_dev, n_host, cap,
+                                                       scr.offs + p * 256);
+            k_rts_scatter<K><<<rgrid, kSortThreads, sizeof(RtsSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
+                                                                           scr.counts, scr.max_tiles,
+                                                                           scr.offs + p * 256);
+            K *tk = ka;
+            ka = kb;
+            kb = tk;
+            unsigned *tv = va;
+            va = vb;
+            vb = tv;
+        }
+        return passes;
+    }
     k_sort_hist<K><<<sms * 2, 512, 0, s>>>(keys, n_dev, n_host, cap, passes, scr.hist);
     k_sort_offsets<<<passes, 256, 0, s>>>(scr.hist, scr.offs, ctr);
-    long long max_tiles = sort_max_tiles_for(cap);
     int grid = (int)min((long long)sgrid, max_tiles > 0 ? max_tiles : 1);
     // full tiles start at multiples of kSortTile elements, so 16-byte-aligned arrays keep every
     // bulk copy 16-byte aligned

@@ -29,10 +29,11 @@ def ctx():
     return gs.Context(0)
 
 
-def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False, variant=None, sort_mode=None):
+def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False, variant=None, sort_mode=None,
+            sort_algo=None):
     sc = gs.Scene.from_numpy(ctx, scene)
     fr = gs.Frame(ctx, scene.P, max_pairs, cam.width, cam.height)
-    fr.gs_frame_set_tuning(blend_variant=variant, sort_mode=sort_mode)
+    fr.gs_frame_set_tuning(blend_variant=variant, sort_mode=sort_mode, sort_algo=sort_algo)
     o = gs.gs_opts(**(opts_kw or {}))
     H, W = cam.height, cam.width
     rgb = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
@@ -99,11 +100,12 @@ def check(res, ref, check_unsorted=True, t_min=1e-4, alpha_max=0.99):
         assert np.all(ref.T[diff] <= stop_regime) and np.all(res["T"][diff] <= stop_regime)
 
 
+@pytest.mark.parametrize("sort_algo", [0, 1])
 @pytest.mark.parametrize("sort_mode", [0, 1])
-def test_tiny_config_parity(ctx, sort_mode):
+def test_tiny_config_parity(ctx, sort_mode, sort_algo):
     scene, cams = synth.load_config("tiny")
     ref = oracle.Frame(scene, cams[0], mode=64)
-    check(run_gpu(ctx, scene, cams[0], sort_mode=sort_mode), ref)
+    check(run_gpu(ctx, scene, cams[0], sort_mode=sort_mode, sort_algo=sort_algo), ref)
 
 
 @pytest.mark.parametrize("sort_mode", [0, 1])
@@ -129,18 +131,20 @@ def test_raw_parameters_activated_on_device(ctx):
     check(run_gpu(ctx, scene, cam), ref)
 
 
+@pytest.mark.parametrize("sort_algo", [0, 1])
 @pytest.mark.parametrize("sort_mode", [0, 1])
-def test_large_gaussians_many_candidate_tiles(ctx, sort_mode):
+def test_large_gaussians_many_candidate_tiles(ctx, sort_mode, sort_algo):
     """Gaussians with hundreds of candidate tiles spread over many load-balanced steps."""
     scene, cam = synth.random_small_scene(400, 13, 320, 240, log_scale_mu=-1.2, log_scale_sigma=0.5)
     ref = oracle.Frame(scene, cam, mode=64)
     big = ((ref.rect[:, 1] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 2] + 1) > 256) & (ref.valid > 0)
     assert big.sum() > 10
-    check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
+    check(run_gpu(ctx, scene, cam, sort_mode=sort_mode, sort_algo=sort_algo), ref)
 
 
+@pytest.mark.parametrize("sort_algo", [0, 1])
 @pytest.mark.parametrize("sort_mode", [0, 1])
-def test_elongated_gaussians_row_runs(ctx, sort_mode):
+def test_elongated_gaussians_row_runs(ctx, sort_mode, sort_algo):
     """Thin rotated ellipses up to a few hundred pixels long: many tiles are hit only through a
     side edge, box widths are not multiples of the 8-tile run, and the largest take the
     one-CTA-per-Gaussian emission of the depth-ordered mode."""
@@ -157,7 +161,7 @@ def test_elongated_gaussians_row_runs(ctx, sort_mode):
     ref = oracle.Frame(scene, cam, mode=32)
     ncand = (ref.rect[:, 1] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 2] + 1) * (ref.valid > 0)
     assert (ncand > 1024).sum() >= 5 and ((ncand > 8) & (ncand < 200)).sum() >= 50
-    check(run_gpu(ctx, scene, cam, sort_mode=sort_mode), ref)
+    check(run_gpu(ctx, scene, cam, sort_mode=sort_mode, sort_algo=sort_algo), ref)
 
 
 @pytest.mark.parametrize("sort_mode", [0, 1])
@@ -279,10 +283,11 @@ def test_autotune_picks_a_shape_and_caches_it(ctx, tmp_path):
     ref, _, _ = fr.render(sc, cams[0])
     cache = tmp_path / "tune.txt"
     t1 = fr.gs_autotune(sc, cams, cache_path=cache)
-    assert 0 <= t1["blend_variant"] < 6 and t1["sort_mode"] in (0, 1)
+    assert 0 <= t1["blend_variant"] < 6 and t1["sort_mode"] in (0, 1) and t1["sort_algo"] in (0, 1)
     assert fr.gs_frame_get_tuning() == t1
     line = cache.read_text().strip().split()
-    assert line[0] == "gs-autotune-v1" and int(line[-2]) == t1["blend_variant"] and int(line[-1]) == t1["sort_mode"]
+    assert line[0] == "gs-autotune-v2"
+    assert [int(x) for x in line[-3:]] == [t1["blend_variant"], t1["sort_mode"], t1["sort_algo"]]
     fr2 = gs.Frame(ctx, scene.P, 1 << 20, 256, 256)
     assert fr2.gs_autotune(sc, cams, cache_path=cache) == t1          # served from the cache
     out, _, _ = fr2.render(sc, cams[0])
