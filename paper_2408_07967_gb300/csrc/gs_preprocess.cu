@@ -132,26 +132,19 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
     if (!(p[2] > cam.near_z)) return false;
     if (!(alpha0 > o.tau)) return false;
     passed_cull = true;
-    // Eq. 3: alpha0 exp(-q/2) >= tau  <=>  q <= 2 ln(alpha0 / tau)
-    const float t_full = fmul(2.0f, log_rn(fdiv(alpha0, o.tau)));
-    float t = t_full;
-    if (o.cap_3sigma && t > 9.0f) t = 9.0f;
-    // Sigma = R_q diag(s^2) R_q^T
     const float4 sc = __ldg(rs_of(S, gid));
-    float s0 = sc.x, s1 = sc.y, s2 = sc.z;
-    if (!S.activated) {
-        s0 = exp_rn(s0);
-        s1 = exp_rn(s1);
-        s2 = exp_rn(s2);
-    }
     {
-        // Conservative screen-extent test.  Sigma <= s_max^2 I, so Sigma'00 <= s_max^2 |M0|^2 +
-        // dilation (M0 = first row of J W) and {q <= t} lies within u +- sqrt(t Sigma'00); a
-        // Gaussian whose bound, padded by 2% and two pixels for rounding, misses the image can
-        // have no candidate tile, and skipping its covariance changes no result.  (NaN bounds
-        // compare false and keep the Gaussian.)
-        const float smax = fmaxf(fmaxf(s0, s1), s2);
-        const float iz = 1.0f / p[2];
+        // Conservative screen-extent test, before any exact arithmetic of the covariance.
+        // Sigma <= s_max^2 I, so Sigma'00 <= s_max^2 |M0|^2 + dilation (M0 = first row of J W) and
+        // {q <= t} lies within u +- sqrt(t Sigma'00).  Every factor here is an upper estimate from
+        // the fast approximate unit (relative errors near 1e-6), padded by 2% and two pixels: a
+        // Gaussian whose bound misses the image can have no candidate tile, and skipping it
+        // changes no result.  (NaN bounds compare false and keep the Gaussian.)
+        float tb = 2.0f * __logf(__fdividef(alpha0, o.tau)) * 1.01f + 0.01f;
+        if (o.cap_3sigma && tb > 9.01f) tb = 9.01f;
+        const float sraw = fmaxf(fmaxf(sc.x, sc.y), sc.z);
+        const float smax = S.activated ? sraw : __expf(sraw) * 1.01f;
+        const float iz = __fdividef(1.0f, p[2]);
         float rx = p[0] * iz, ry = p[1] * iz;
         if (o.clamp_fov) {
             rx = fminf(fmaxf(rx, -cam.limx), cam.limx);
@@ -167,11 +160,13 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
             m0 += e0 * e0;
             m1 += e1 * e1;
         }
-        float hxb = sqrtf(t * (smax * smax * m0 + o.dilation)) * 1.02f + 2.0f;
-        float hyb = sqrtf(t * (smax * smax * m1 + o.dilation)) * 1.02f + 2.0f;
+        const float x2 = tb * (smax * smax * m0 + o.dilation), y2 = tb * (smax * smax * m1 + o.dilation);
+        float hxb = (x2 > 0.0f ? x2 * rsqrtf(x2) : 0.0f) * 1.02f + 2.0f;
+        float hyb = (y2 > 0.0f ? y2 * rsqrtf(y2) : 0.0f) * 1.02f + 2.0f;
         if (o.intersect == 1) {
             // 3DGS square: r <= ceil(3 sqrt(trace Sigma')), trace <= s_max^2 (|M0|^2 + |M1|^2) + 2 dilation
-            const float rb = 3.0f * sqrtf(smax * smax * (m0 + m1) + 2.0f * o.dilation) * 1.02f + 3.0f;
+            const float r2 = smax * smax * (m0 + m1) + 2.0f * o.dilation;
+            const float rb = 3.0f * (r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f) * 1.02f + 3.0f;
             hxb = rb;
             hyb = rb;
         }
@@ -179,6 +174,17 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
         if (uu + hxb < 0.0f || uu - hxb >= (float)(kTile * cam.tiles_x) || vv + hyb < 0.0f ||
             vv - hyb >= (float)(kTile * cam.tiles_y))
             return false;
+    }
+    // Eq. 3: alpha0 exp(-q/2) >= tau  <=>  q <= 2 ln(alpha0 / tau)
+    const float t_full = fmul(2.0f, log_rn(fdiv(alpha0, o.tau)));
+    float t = t_full;
+    if (o.cap_3sigma && t > 9.0f) t = 9.0f;
+    // Sigma = R_q diag(s^2) R_q^T
+    float s0 = sc.x, s1 = sc.y, s2 = sc.z;
+    if (!S.activated) {
+        s0 = exp_rn(s0);
+        s1 = exp_rn(s1);
+        s2 = exp_rn(s2);
     }
     const float4 q4 = __ldg(rs_of(S, gid) + 1);
     float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
@@ -433,8 +439,7 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_count(const __grid_constan
     Geom G;
     bool valid = false, passed_cull = false;
     if (gid < R.scene.P) valid = gaussian_geometry(R.scene, gid, cam, R.opt, G, passed_cull);
-    const unsigned n_in = __popc(__ballot_sync(FULL, passed_cull));
-    if (lane == 0 && n_in) atomicAdd(&A.ctr->n_culled_in, n_in);
+    const unsigned n_in_block = (unsigned)__syncthreads_count(passed_cull);   // one atomic per CTA below
     const int w = valid ? G.tx1 - G.tx0 + 1 : 0;
     const int h = valid ? G.ty1 - G.ty0 + 1 : 0;
     if (valid) {
@@ -468,6 +473,7 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_count(const __grid_constan
         A.chunk_hits[chunk] = hits;
         A.chunk_vis[chunk] = nvis_block;
         if (nvis_block) atomicAdd(&A.ctr->n_visible, nvis_block);
+        if (n_in_block) atomicAdd(&A.ctr->n_culled_in, n_in_block);
     }
     if (gid < R.scene.P) A.counts[rec] = S.cnt[tid];
     if (vis) {
@@ -647,10 +653,16 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
         S.pbase[tid] = pb;
         S.run[tid] = 0;
         const bool big = ncand > kBigCand;
+        // this CTA's large Gaussians take consecutive slots of the list: one atomic per CTA
+        unsigned nbig_blk;
+        const unsigned bslot = block_excl(S, (big && c > 0) ? 1u : 0u, &nbig_blk);
+        if (tid == 0 && nbig_blk) S.xr[0] = atomicAdd(&A.ctr->n_big, nbig_blk);
+        __syncthreads();
         if (big && c > 0) {
-            const unsigned k = atomicAdd(&A.ctr->n_big, 1u);
+            const unsigned k = S.xr[0] + bslot;
             A.big[k] = make_uint4((unsigned)gid, (unsigned)ri, (unsigned)(pb & 0xffffffffu), (unsigned)(pb >> 32));
         }
+        __syncthreads();
         const int ctotal = block_scan_cand(S, big ? 0 : nunits);
         for (int base = 0; base < ctotal; base += kPreBlock) {
             const int slot = base + tid;
@@ -735,6 +747,7 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
     const unsigned FULL = 0xffffffffu;
     const unsigned nbig = *(volatile unsigned *)&A.ctr->n_big;
     const long long cap = A.pair_cap;
+    // items in ticket order, so that CTAs that drew small Gaussians take more of them
     while (true) {
         if (tid == 0) s_item = atomicAdd(&A.ctr->big_ticket, 1u);
         __syncthreads();
