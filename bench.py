@@ -59,6 +59,28 @@ def parse():
     return ap.parse_args()
 
 
+def traffic_for(config, stage, tuning=None):
+    """DRAM bytes per launch of the stage's kernel from an ncu capture recorded in
+    profiles/traffic.json, or None when the kernel's sources changed since the capture (their
+    sha256 is stored with the figure) or the run uses another launch shape."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    e = json.load(open(p)).get(config, {}).get(stage)
+    if not e:
+        return None
+    if any((tuning or {}).get(k) != v for k, v in e.get("tuning", {}).items()):
+        return None
+    h = hashlib.sha256()
+    for f in e["sources"]:
+        fp = os.path.join(ROOT, f)
+        if not os.path.exists(fp):
+            return None
+        h.update(open(fp, "rb").read())
+    return e["dram_bytes_per_launch"] if h.hexdigest() == e["sha256"] else None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -364,7 +386,7 @@ def measure_alu(gs, dev):
 
 
 def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, args, rank=0, sample_clocks=True,
-                alu=None):
+                alu=None, config=None):
     """Render `steps` frames (camera cycle), L2 flushed before each, graph replay; per-step CUDA events
     on the launching stream, per-stage event nodes inside the graph, then the same frames again with
     the instrumented blend for the evaluation counts.  Returns (result dict, frame, camera of step i)."""
@@ -484,7 +506,8 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
             "blend": f"{BLEND_OPS_PER_CONTRIB} FP32 ops x contributing evaluations (E_c = {Ec:.4g} of "
                      f"E = {E:.4g} walked per frame)"}[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": None, "kernel": kernel, "stage": dom,
+                "frac": d["frac"], "traffic": traffic_for(config, dom, tuning) if config else None, "kernel": kernel,
+                "stage": dom,
                 "peak_source": ("measured HBM copy (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else alu_src),
                 "algorithmic": algo}
     res = {"frames": K, "ms_total": tot_ms, "frames_per_s": K / (tot_ms / 1000.0), "ms_per_frame": tot_ms / K,
@@ -566,7 +589,8 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     alu = measure_alu(gs, dev)
     main, fr, cam_of = time_frames(gs, ctx, sc, scene.P, cams, args.steps, args.warmup, stream, flush,
-                                   pair_capacity(args.config, args.gaussians), args, rank, alu=alu)
+                                   pair_capacity(args.config, args.gaussians), args, rank, alu=alu,
+                                   config=None if args.gaussians else args.config)
     tot_ms = max_over_ranks(main["ms_total"])
     if ws > 1:
         torch.distributed.barrier()

@@ -752,7 +752,14 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     out->culled_in = c.n_culled_in;
     out->evaluations = (int64_t)c.evals[0];
     out->contributions = (int64_t)c.evals[1];
-    out->kernels = f->mode_used == 1 ? 17 + f->passes : 7 + f->passes;
+    // count + scan + emit, sort, ranges, blend; the depth-ordered mode adds the visible-list
+    // compaction, the 4-pass depth sort, the rank-chunk sums and scan and the large-Gaussian
+    // emission.  A sort runs histogram + offsets + one scatter per pass (onesweep) or count +
+    // scan + scatter per pass (reduce-then-scan).
+    const bool rts = f->tuning.sort_algo == 1;
+    const int sort_k = rts ? 3 * f->passes : 2 + f->passes;
+    const int depth_k = rts ? 12 : 6;
+    out->kernels = f->mode_used == 1 ? 3 + 4 + depth_k + sort_k + 2 : 3 + sort_k + 2;
     return GS_OK;
 }
 
