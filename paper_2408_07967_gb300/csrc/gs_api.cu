@@ -119,7 +119,7 @@ struct gs_frame {
     unsigned long long *chunk_base = nullptr, *vis_base = nullptr, *chunk_base2 = nullptr;
     unsigned *chunk_hits = nullptr, *chunk_vis = nullptr, *chunk_hits2 = nullptr, *counts = nullptr;
     unsigned *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
-    uint4 *big = nullptr;
+    uint4 *big = nullptr, *mid = nullptr;
     int mode_used = 0;
     float4 *geo0 = nullptr, *geo1 = nullptr;
     int4 *geo2 = nullptr;
@@ -308,7 +308,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     size_t o_counts = cv.take<unsigned>(max_g);
     size_t o_dk0 = cv.take<unsigned>(max_g), o_dk1 = cv.take<unsigned>(max_g);
     size_t o_dv0 = cv.take<unsigned>(max_g), o_dv1 = cv.take<unsigned>(max_g);
-    size_t o_big = cv.take<uint4>(max_g);
+    size_t o_big = cv.take<uint4>(max_g), o_mid = cv.take<uint4>(max_g);
     size_t o_geo0 = cv.take<float4>(max_g), o_geo1 = cv.take<float4>(max_g), o_geo2 = cv.take<int4>(max_g);
     size_t o_hist = cv.take<unsigned>(8 * 256), o_offs = cv.take<unsigned>(8 * 256);
     size_t o_desc = cv.take<unsigned long long>(f->sort.max_tiles * 256);
@@ -340,6 +340,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     f->dval[0] = (unsigned *)(b + o_dv0);
     f->dval[1] = (unsigned *)(b + o_dv1);
     f->big = (uint4 *)(b + o_big);
+    f->mid = (uint4 *)(b + o_mid);
     f->geo0 = (float4 *)(b + o_geo0);
     f->geo1 = (float4 *)(b + o_geo1);
     f->geo2 = (int4 *)(b + o_geo2);
@@ -536,6 +537,7 @@ static PreprocessArgs pre_args(gs_frame *f) {
     a.chunk_hits2 = f->chunk_hits2;
     a.chunk_base2 = f->chunk_base2;
     a.big = f->big;
+    a.mid = f->mid;
     a.ctr = f->ctr;
     a.pair_cap = f->max_pairs;
     a.n_chunks = f->batch.total_chunks;
@@ -753,13 +755,13 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     out->evaluations = (int64_t)c.evals[0];
     out->contributions = (int64_t)c.evals[1];
     // count + scan + emit, sort, ranges, blend; the depth-ordered mode adds the visible-list
-    // compaction, the 4-pass depth sort, the rank-chunk sums and scan and the large-Gaussian
-    // emission.  A sort runs histogram + offsets + one scatter per pass (onesweep) or count +
+    // compaction, the 4-pass depth sort, the rank-chunk sums and scan and the medium- and
+    // large-Gaussian emission.  A sort runs histogram + offsets + one scatter per pass (onesweep) or count +
     // scan + scatter per pass (reduce-then-scan).
     const bool rts = f->tuning.sort_algo == 1;
     const int sort_k = rts ? 3 * f->passes : 2 + f->passes;
     const int depth_k = rts ? 12 : 6;
-    out->kernels = f->mode_used == 1 ? 3 + 4 + depth_k + sort_k + 2 : 3 + sort_k + 2;
+    out->kernels = f->mode_used == 1 ? 3 + 5 + depth_k + sort_k + 2 : 3 + sort_k + 2;
     return GS_OK;
 }
 

@@ -123,9 +123,11 @@ struct FrameCounters {
     unsigned long long scratch64;    // unused scan total
     unsigned int n_big;              // two-level order: Gaussians left to k_emit_big
     unsigned int big_ticket;
+    unsigned int n_mid;              // two-level order: Gaussians left to k_emit_mid (one warp each)
+    unsigned int mid_ticket;
     unsigned int sort_ticket[8];     // scatter-pass tickets
     unsigned int sort_epoch;         // bumped once per sort; tags look-back descriptors
-    unsigned int pad1[7];
+    unsigned int pad1[5];
 };
 
 // ----------------------------------------------------------------------------------------------
@@ -328,6 +330,7 @@ struct PreprocessArgs {
     unsigned *chunk_hits2;           // pairs per chunk of 256 depth-sorted Gaussians
     unsigned long long *chunk_base2; // exclusive scan of chunk_hits2
     uint4 *big;                      // (record, request, output base lo, hi) of large Gaussians
+    uint4 *mid;                      // the same for medium Gaussians
     FrameCounters *ctr;
     long long pair_cap;
     long long n_chunks;

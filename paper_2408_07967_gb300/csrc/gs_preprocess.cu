@@ -322,8 +322,12 @@ struct PreSmem {
     unsigned xr[kPreBlock];                // depth order: exclusive hit rank of each slot of a step
 };
 
-// Gaussians with more candidate tiles than this are emitted by k_emit_big, one CTA each.
-constexpr int kBigCand = 1024;
+// Depth-ordered emission by footprint: Gaussians with more candidate tiles than kBigCand are
+// emitted by k_emit_big (a CTA each), those above kMidCand by k_emit_mid (a warp each), the rest
+// by their rank chunk in k_pre_emit.  Near Gaussians are large and neighbours in depth order, so a
+// rank chunk full of them would otherwise hold up the whole pass.
+constexpr int kBigCand = 4096;
+constexpr int kMidCand = 64;
 
 // Work unit of the exact tests: a run of up to kSeg consecutive candidate tiles of one tile row
 // of one Gaussian (row-major), tested by one thread with the row's shared terms (run_hits).
@@ -652,18 +656,20 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
         const unsigned long long pb = A.chunk_base2[chunk] + pre;
         S.pbase[tid] = pb;
         S.run[tid] = 0;
-        const bool big = ncand > kBigCand;
-        // this CTA's large Gaussians take consecutive slots of the list: one atomic per CTA
-        unsigned nbig_blk;
+        const bool big = ncand > kBigCand, mid = !big && ncand > kMidCand;
+        // this CTA's large and medium Gaussians take consecutive slots of their lists: one atomic
+        // per CTA and list
+        unsigned nbig_blk, nmid_blk;
         const unsigned bslot = block_excl(S, (big && c > 0) ? 1u : 0u, &nbig_blk);
+        const unsigned mslot = block_excl(S, (mid && c > 0) ? 1u : 0u, &nmid_blk);
         if (tid == 0 && nbig_blk) S.xr[0] = atomicAdd(&A.ctr->n_big, nbig_blk);
+        if (tid == 32 && nmid_blk) S.xr[1] = atomicAdd(&A.ctr->n_mid, nmid_blk);
         __syncthreads();
-        if (big && c > 0) {
-            const unsigned k = S.xr[0] + bslot;
-            A.big[k] = make_uint4((unsigned)gid, (unsigned)ri, (unsigned)(pb & 0xffffffffu), (unsigned)(pb >> 32));
-        }
+        const uint4 item = make_uint4((unsigned)gid, (unsigned)ri, (unsigned)(pb & 0xffffffffu), (unsigned)(pb >> 32));
+        if (big && c > 0) A.big[S.xr[0] + bslot] = item;
+        if (mid && c > 0) A.mid[S.xr[1] + mslot] = item;
         __syncthreads();
-        const int ctotal = block_scan_cand(S, big ? 0 : nunits);
+        const int ctotal = block_scan_cand(S, (big || mid) ? 0 : nunits);
         for (int base = 0; base < ctotal; base += kPreBlock) {
             const int slot = base + tid;
             unsigned m = 0;
@@ -735,6 +741,66 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant
         }
         run += step_tot;
         __syncthreads();
+    }
+}
+
+// Depth order, medium Gaussians: one warp per Gaussian (warps take items in ticket order), its
+// units tested 32 at a time, hits staged per warp and written as coalesced runs from the
+// Gaussian's base.
+__global__ void __launch_bounds__(kPreBlock) k_emit_mid(const __grid_constant__ PreprocessArgs A) {
+    constexpr int kWarps = kPreBlock / 32;
+    __shared__ unsigned s_tile[kWarps][32 * kSeg];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned nmid = *(volatile unsigned *)&A.ctr->n_mid;
+    const long long cap = A.pair_cap;
+    while (true) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&A.ctr->mid_ticket, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= nmid) break;
+        const uint4 it = A.mid[item];
+        const long long rec = it.x;
+        const ReqDesc &R = A.B.r[it.y];
+        unsigned long long run = ((unsigned long long)it.w << 32) | it.z;
+        const float4 g0 = A.geo0[rec], g1 = A.geo1[rec];
+        const int4 g2 = A.geo2[rec];
+        const int segs = (g2.z + kSeg - 1) / kSeg;
+        const int nunits = segs * g2.w;
+        for (int base = 0; base < nunits; base += 32) {
+            const int k = base + lane;
+            unsigned m = 0;
+            int tx = 0, ty = 0;
+            if (k < nunits) {
+                const int dy = k / segs, seg = k - dy * segs;
+                tx = g2.x + seg * kSeg;
+                ty = g2.y + dy;
+                const int nrun = min(kSeg, g2.z - seg * kSeg);
+                m = R.opt.intersect == 1 ? (1u << nrun) - 1u
+                                         : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, nrun, ty);
+            }
+            const unsigned c = (unsigned)__popc(m);
+            unsigned incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned tot = __shfl_sync(FULL, incl, 31);
+            unsigned i = incl - c;
+            const unsigned trow = (unsigned)(R.tile0 + ty * R.cam.tiles_x);
+            for (unsigned mm = m; mm; mm &= mm - 1, ++i) s_tile[warp][i] = trow + (unsigned)(tx + __ffs(mm) - 1);
+            __syncwarp();
+            for (unsigned j = lane; j < tot; j += 32) {
+                const unsigned long long pos = run + j;
+                if ((long long)pos < cap) {
+                    A.tkeys[pos] = s_tile[warp][j];
+                    A.vals[pos] = (unsigned)rec;
+                }
+            }
+            run += tot;
+            __syncwarp();
+        }
     }
 }
 
@@ -845,6 +911,7 @@ int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cud
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         big_grid = 8 * sms;
     }
+    k_emit_mid<<<big_grid, kPreBlock, 0, s>>>(a);
     k_emit_big<<<big_grid, kPreBlock, 0, s>>>(a);
     return 4;
 }
