@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kPreBlock, 4) k_pre_count(const __grid_constan
 // Exclusive scan of up to two arrays of chunk counts (one CTA; each thread sums a run of chunks).
 // Writes the totals to *tot_a / *tot_b.
 constexpr int kScanThreads = 1024;
-constexpr int kScanRun = 16;
+constexpr int kScanRun = 40;   // 40960 chunks per sweep: one sweep up to 10M Gaussians per batch
 __device__ void chunk_scan(const unsigned *in, unsigned long long *out, long long n, unsigned long long *total) {
     __shared__ unsigned long long s_w[kScanThreads / 32];
     __shared__ unsigned long long s_carry;
@@ -508,11 +508,12 @@ __device__ void chunk_scan(const unsigned *in, unsigned long long *out, long lon
     if (tid == 0) s_carry = 0;
     __syncthreads();
     for (long long base = 0; base < n; base += (long long)kScanThreads * kScanRun) {
+        // each thread sums a run of counts; the second sweep re-reads them from L1
         const long long my0 = base + (long long)tid * kScanRun;
         unsigned long long sum = 0;
-#pragma unroll
+#pragma unroll 8
         for (int r = 0; r < kScanRun; ++r)
-            if (my0 + r < n) sum += in[my0 + r];
+            if (my0 + r < n) sum += __ldg(in + my0 + r);
         unsigned long long incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -529,11 +530,11 @@ __device__ void chunk_scan(const unsigned *in, unsigned long long *out, long lon
         }
         unsigned long long run = s_carry + wex + incl - sum;
         if (out) {
-#pragma unroll
+#pragma unroll 8
             for (int r = 0; r < kScanRun; ++r)
                 if (my0 + r < n) {
                     out[my0 + r] = run;
-                    run += in[my0 + r];
+                    run += __ldg(in + my0 + r);
                 }
         }
         __syncthreads();

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rts_count(const K *__restrict_
 // One CTA per digit: counts[d][t] becomes the sum of counts[d][t'] over t' < t, and the row's total
 // goes to tot[d] (the scatter turns the 256 totals into the digits' global offsets).
 constexpr int kRtsScanThreads = 1024;
-constexpr int kRtsScanRun = 8;
+constexpr int kRtsScanRun = 24;   // 24576 tiles per sweep
 __global__ void __launch_bounds__(kRtsScanThreads) k_rts_scan(unsigned *counts, long long stride,
                                                               const unsigned long long *n_dev, long long n_host,
                                                               long long cap, unsigned *tot_out) {
@@ -437,13 +437,10 @@ __global__ void __launch_bounds__(kRtsScanThreads) k_rts_scan(unsigned *counts, 
     __syncthreads();
     for (long long b0 = 0; b0 < ntiles; b0 += (long long)kRtsScanThreads * kRtsScanRun) {
         const long long my0 = b0 + (long long)tid * kRtsScanRun;
-        unsigned v[kRtsScanRun];
         unsigned sum = 0;
-#pragma unroll
-        for (int r = 0; r < kRtsScanRun; ++r) {
-            v[r] = my0 + r < ntiles ? row[my0 + r] : 0u;
-            sum += v[r];
-        }
+#pragma unroll 8
+        for (int r = 0; r < kRtsScanRun; ++r)
+            if (my0 + r < ntiles) sum += row[my0 + r];
         unsigned incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -460,11 +457,13 @@ __global__ void __launch_bounds__(kRtsScanThreads) k_rts_scan(unsigned *counts, 
             tot += x;
         }
         unsigned run = s_carry + wex + incl - sum;
-#pragma unroll
-        for (int r = 0; r < kRtsScanRun; ++r) {
-            if (my0 + r < ntiles) row[my0 + r] = run;
-            run += v[r];
-        }
+#pragma unroll 8
+        for (int r = 0; r < kRtsScanRun; ++r)
+            if (my0 + r < ntiles) {
+                const unsigned x = row[my0 + r];    // read before this thread overwrites it
+                row[my0 + r] = run;
+                run += x;
+            }
         __syncthreads();
         if (tid == 0) s_carry += tot;
         __syncthreads();
@@ -474,12 +473,13 @@ __global__ void __launch_bounds__(kRtsScanThreads) k_rts_scan(unsigned *counts, 
 
 template <class K>
 struct RtsSmem {
-    K keys[kSortTile];
-    unsigned vals[kSortTile];
+    K keys[kBufs<K>][kSortTile];     // tile being ranked / next tile arriving (32-bit keys)
+    unsigned vals[kBufs<K>][kSortTile];
     unsigned whist[kSortWarps][256];
     unsigned local_off[256];
     unsigned gbase[256];
     unsigned wsum[kSortWarps];
+    unsigned long long bar[2];
 };
 
 template <class K>
@@ -488,8 +488,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__rest
                                                               unsigned *__restrict__ vout,
                                                               const unsigned long long *n_dev, long long n_host,
                                                               long long cap, int pass, const unsigned *offs_t,
-                                                              long long stride, const unsigned *tot) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                              long long stride, const unsigned *tot,
+                                                              int bulk_ok, FrameCounters *ctr) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     RtsSmem<K> &S = *reinterpret_cast<RtsSmem<K> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
@@ -514,26 +515,65 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__rest
         dbase = wex + incl - c;
         __syncthreads();
     }
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // Tiles are dealt round-robin, so each CTA knows its next tile: with 32-bit keys its bulk copy
+    // (full tiles of 16-byte-aligned arrays) lands in the other buffer while this one is ranked.
+    const long long nfull = n / kSortTile;
+    constexpr bool kPrefetch = kBufs<K> == 2;
+    unsigned phases = 0u;
+    bool failed = false;
+    auto issue = [&](long long t, int b) {
+        if (kPrefetch && tid == 0 && bulk_ok && t < nfull) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bar_expect(&S.bar[b], (unsigned)(kSortTile * (sizeof(K) + sizeof(unsigned))));
+            bulk_g2s(S.keys[b], kin + t * kSortTile, (unsigned)(kSortTile * sizeof(K)), &S.bar[b]);
+            bulk_g2s(S.vals[b], vin + t * kSortTile, (unsigned)(kSortTile * sizeof(unsigned)), &S.bar[b]);
+        }
+    };
+    if (kPrefetch && tid == 0) {
+        bar_init(&S.bar[0]);
+        bar_init(&S.bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    issue(blockIdx.x, 0);
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int b = kPrefetch ? (it & 1) : 0;
         for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
         S.gbase[tid] = dbase + offs_t[(long long)tid * stride + tile];
-        __syncthreads();
+        issue(tile + gridDim.x, b ^ 1);      // the other buffer was released at the end of the last tile
         const long long tbase = tile * kSortTile;
         const long long wbase = tbase + (long long)warp * (32 * kSortItems);
         K k[kSortItems];
         unsigned v[kSortItems];
         unsigned rank[kSortItems];
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const long long idx = wbase + i * 32 + lane;
-            if (idx < n) {
-                k[i] = kin[idx];
-                v[i] = vin[idx];
+        if (kPrefetch && bulk_ok && tile < nfull) {
+            if (bar_wait(&S.bar[b], (phases >> b) & 1u)) {
+                phases ^= 1u << b;
             } else {
-                k[i] = (K)~(K)0;
-                v[i] = 0u;
+                if (lane == 0) atomicOr(&ctr->status, kStTimeout);
+                failed = true;
+            }
+            const int wofs = warp * (32 * kSortItems);
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) {
+                k[i] = S.keys[b][wofs + i * 32 + lane];
+                v[i] = S.vals[b][wofs + i * 32 + lane];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) {
+                const long long idx = wbase + i * 32 + lane;
+                if (idx < n) {
+                    k[i] = kin[idx];
+                    v[i] = vin[idx];
+                } else {
+                    k[i] = (K)~(K)0;
+                    v[i] = 0u;
+                }
             }
         }
+        if (__syncthreads_or(failed)) break;
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
@@ -569,19 +609,24 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__rest
         for (int i = 0; i < kSortItems; ++i) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
             const unsigned pos = S.local_off[d] + S.whist[warp][d] + rank[i];
-            S.keys[pos] = k[i];
-            S.vals[pos] = v[i];
+            S.keys[b][pos] = k[i];
+            S.vals[b][pos] = v[i];
         }
         __syncthreads();
         const long long valid_here = min((long long)kSortTile, n - tbase);
         for (int s = tid; s < valid_here; s += kSortThreads) {
-            const K key = S.keys[s];
+            const K key = S.keys[b][s];
             const unsigned d = (unsigned)(key >> shift) & 0xffu;
             const unsigned long long dst = (unsigned long long)S.gbase[d] + (unsigned long long)(s - S.local_off[d]);
             kout[dst] = key;
-            vout[dst] = S.vals[s];
+            vout[dst] = S.vals[b][s];
         }
         __syncthreads();
+    }
+    // a failed wait leaves copies possibly in flight: give them a bounded chance to land
+    if (kPrefetch && failed && tid == 0) {
+        bar_wait(&S.bar[0], phases & 1u);
+        bar_wait(&S.bar[1], (phases >> 1) & 1u);
     }
 }
 
@@ -609,6 +654,9 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long max_tiles = sort_max_tiles_for(cap);
+    // full tiles start at multiples of kSortTile elements, so 16-byte-aligned arrays keep every
+    // bulk copy 16-byte aligned
+    const int bulk_ok = (((uintptr_t)keys | (uintptr_t)vals | (uintptr_t)keys_tmp | (uintptr_t)vals_tmp) & 15u) == 0;
     if (scr.algo == 1 && scr.counts && max_tiles <= scr.max_tiles) {
         const int cgrid = (int)min((long long)sms * 8, max_tiles > 0 ? max_tiles : 1);
         const int rgrid = (int)min((long long)rts_scatter_grid<K>(), max_tiles > 0 ? max_tiles : 1);
@@ -620,7 +668,7 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
                                                        scr.offs + p * 256);
             k_rts_scatter<K><<<rgrid, kSortThreads, sizeof(RtsSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
                                                                            scr.counts, scr.max_tiles,
-                                                                           scr.offs + p * 256);
+                                                                           scr.offs + p * 256, bulk_ok, ctr);
             K *tk = ka;
             ka = kb;
             kb = tk;
@@ -633,9 +681,6 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
     k_sort_hist<K><<<sms * 2, 512, 0, s>>>(keys, n_dev, n_host, cap, passes, scr.hist);
     k_sort_offsets<<<passes, 256, 0, s>>>(scr.hist, scr.offs, ctr);
     int grid = (int)min((long long)sgrid, max_tiles > 0 ? max_tiles : 1);
-    // full tiles start at multiples of kSortTile elements, so 16-byte-aligned arrays keep every
-    // bulk copy 16-byte aligned
-    const int bulk_ok = (((uintptr_t)keys | (uintptr_t)vals | (uintptr_t)keys_tmp | (uintptr_t)vals_tmp) & 15u) == 0;
     K *ka = keys, *kb = keys_tmp;
     unsigned *va = vals, *vb = vals_tmp;
     for (int p = 0; p < passes; ++p) {
