@@ -428,7 +428,7 @@ __device__ __forceinline__ int block_scan_cand(PreSmem &S, int ncand) {
 // Pass 1: geometry, exact tests counted over all candidate tiles of the chunk (load-balanced),
 // render records of paired Gaussians, the chunk's pair count, and each paired Gaussian's
 // geometry for pass 3.
-__global__ void __launch_bounds__(kPreBlock, 4) k_pre_count(const __grid_constant__ PreprocessArgs A) {
+__global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constant__ PreprocessArgs A) {
     __shared__ PreSmem S;
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned FULL = 0xffffffffu;
