@@ -305,11 +305,12 @@ def run_serving(args, gs, ctx, room_scene, room_cams, city, city_cams):
     stream.synchronize()
     scenes, poses = [room, city], [room_cams, city_cams]
     ring = [torch.empty(3 * 3840 * 2160, dtype=torch.float32).pin_memory() for _ in range(16)]
+    # a city view at 3840x2160 reaches ~230M pairs (street cameras), so both loops get 2^28 pairs;
     # batches are bounded by two 1080p images of pixels (the server's default), so two city
-    # requests at most: 2^27 pairs and 21M Gaussians cover them
-    batched = dict(slots=3, max_batch=8, pair_capacity=(1 << 27), max_gaussians=21_000_000, max_width=3840,
+    # requests at most: 21M Gaussians cover them
+    batched = dict(slots=3, max_batch=8, pair_capacity=(1 << 28), max_gaussians=21_000_000, max_width=3840,
                    max_height=2160)
-    plain = dict(plain=True, pair_capacity=(1 << 27), max_gaussians=11_000_000, max_width=3840, max_height=2160)
+    plain = dict(plain=True, pair_capacity=(1 << 28), max_gaussians=11_000_000, max_width=3840, max_height=2160)
     out = {"workload": "resident room 1M + city 10M scenes, requests 50/50 over scenes, random pose of the "
                        "scene's 32, resolution uniform over 1280x720 / 1920x1080 / 3840x2160",
            "requests_per_run": args.serving_requests}
@@ -322,11 +323,15 @@ def run_serving(args, gs, ctx, room_scene, room_cams, city, city_cams):
             out[f"{name}@{rate}"] = {"frames_per_s": ok / wall, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                                      "mean_batch": sst["batched_requests"] / max(1, sst["batches"]),
                                      "failed": len(st) - ok}
+            if len(st) != ok:
+                raise RuntimeError(f"serving {name}@{rate}: {len(st) - ok} requests failed")
     # saturation: every request available at once
     sched = [(0.0, si, ci, wh) for (_, si, ci, wh) in synth.poisson_requests(args.serving_requests, 1e9, seed=4)]
     for name, kw in (("plain", plain), ("batched", batched)):
         st, wall, sst = serve_run(gs, dict(kw, ctx=ctx), scenes, poses, sched, ring)
         lat = [1000.0 * (s["done_s"] - s["arrival_s"]) for s in st]
+        if any(s["status"] != 0 for s in st):
+            raise RuntimeError(f"serving {name}@saturated: requests failed")
         out[f"{name}@saturated"] = {"frames_per_s": sum(s["status"] == 0 for s in st) / wall,
                                     "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                                     "mean_batch": sst["batched_requests"] / max(1, sst["batches"])}

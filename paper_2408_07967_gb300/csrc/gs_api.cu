@@ -871,6 +871,13 @@ extern "C" gs_status gs_render_batch(gs_frame *f, int32_t n, const gs_scene *con
 }
 
 // Server path: finish a batch whose counts are already on the device (frame_batch_count).
+// Enqueues a copy of the frame's device counters (status word, pair count) to page-locked host
+// memory, so that a completion callback can judge the batch without a synchronising read.
+gs_status frame_counters_async(gs_frame *f, void *host_dst, gs_stream stream) {
+    GS_CUDA(cudaMemcpyAsync(host_dst, f->ctr, sizeof(FrameCounters), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    return GS_OK;
+}
+
 gs_status frame_batch_finish(gs_frame *f, float *const *rgb, float *const *T, uint32_t *const *last,
                              gs_stream stream) {
     gs_status st = batch_emit(f, (cudaStream_t)stream, true);

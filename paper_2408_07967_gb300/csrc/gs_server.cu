@@ -34,6 +34,7 @@
 gs_status frame_batch_count(gs_frame *f, int n, const gs_scene *const *scenes, const gs_camera *cams,
                             const gs_render_opts *opts, unsigned long long *req_pairs_dev, gs_stream stream);
 int context_device(const gs_context *ctx);
+gs_status frame_counters_async(gs_frame *f, void *host_dst, gs_stream stream);
 gs_status frame_batch_finish(gs_frame *f, float *const *rgb, float *const *T, uint32_t *const *last,
                              gs_stream stream);
 namespace gs {
@@ -75,6 +76,7 @@ struct Slot {
     float *out = nullptr;                       // max_batch images of max_width x max_height
     unsigned long long *pairs_dev = nullptr;    // per-request pair counts of the count pass
     unsigned long long *pairs_host = nullptr;   // pinned mirror
+    gs::FrameCounters *ctr_host = nullptr;      // pinned copy of the frame's counters after the batch
     std::vector<uint64_t> inflight;
     bool busy = false;
     bool done = false;
@@ -118,15 +120,18 @@ void CUDART_CB on_batch_done(void *p) {
 void reap(gs_server *sv) {
     for (Slot &s : sv->slots) {
         if (!s.busy || !s.done) continue;
+        // device-side failures of the batch (pairs over the capacity, a wait past its limit)
+        const unsigned dev = s.ctr_host ? s.ctr_host->status : 0u;
+        const gs_status dev_st = (dev & gs::kStTimeout) ? GS_ERR_DEVICE_TIMEOUT
+                                 : (dev & gs::kStPairOverflow) ? GS_ERR_PAIR_OVERFLOW
+                                                               : GS_OK;
         for (uint64_t t : s.inflight) {
             auto it = sv->reqs.find(t);
             if (it == sv->reqs.end()) continue;
-            if (s.single) {
-                // a lone request ran without the admission pass: its count arrived with the image
-                const long long p = (long long)s.pairs_host[0];
-                it->second.pairs = p;
-                if (p > sv->cfg.pair_capacity) it->second.status = GS_ERR_PAIR_OVERFLOW;
-            }
+            if (dev_st != GS_OK && it->second.status == GS_OK) it->second.status = dev_st;
+            // a lone request (or the plain loop's) ran without the admission pass: its count
+            // arrived with the frame's counters
+            if (sv->cfg.plain || s.single) it->second.pairs = (long long)s.ctr_host->n_pairs;
             it->second.done = s.done_time;
             it->second.finished = true;
             ++sv->completed;
@@ -174,14 +179,11 @@ std::vector<uint64_t> launch_batch(gs_server *sv, Slot &s, std::vector<uint64_t>
     s.stream = s.streams[level < kPrioLevels ? level : kPrioLevels - 1];
     s.single = !cfg.plain && n == 1;
     if (s.single) {
-        // One request: nothing to admit or defer, so the count pass runs without a host round
-        // trip; a request that alone exceeds the pair capacity is failed when it completes.
-        st = frame_batch_count(s.frame, 1, scenes.data(), cams.data(), opts.data(), s.pairs_dev, s.stream);
-        if (!st)
-            if (cudaMemcpyAsync(s.pairs_host, s.pairs_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                s.stream) != cudaSuccess)
-                st = GS_ERR_CUDA;
-        if (!st) st = frame_batch_finish(s.frame, rgb.data(), nullptr, nullptr, s.stream);
+        // One request: nothing to admit or defer, so it renders without the admission round trip;
+        // its pair count (and an overflow, if it alone exceeds the capacity) comes back with the
+        // frame's counters when it completes.
+        st = gs_render_batch(s.frame, 1, scenes.data(), cams.data(), opts.data(), rgb.data(), nullptr, nullptr,
+                             s.stream);
     } else if (!cfg.plain) {
         // admission: exact pair counts of the candidates
         st = frame_batch_count(s.frame, n, scenes.data(), cams.data(), opts.data(), s.pairs_dev, s.stream);
@@ -224,6 +226,7 @@ std::vector<uint64_t> launch_batch(gs_server *sv, Slot &s, std::vector<uint64_t>
         st = gs_render_batch(s.frame, n, scenes.data(), cams.data(), opts.data(), rgb.data(), nullptr, nullptr,
                              s.stream);
     }
+    if (!st) st = frame_counters_async(s.frame, s.ctr_host, (gs_stream)s.stream);
     if (!st) {
         for (int i = 0; i < n; ++i) {
             const size_t bytes = sizeof(float) * 3 * (size_t)cams[i].width * cams[i].height;
@@ -254,7 +257,9 @@ std::vector<uint64_t> launch_batch(gs_server *sv, Slot &s, std::vector<uint64_t>
     sv->batched_requests += n;
     lk.unlock();
     cudaLaunchHostFunc(s.stream, on_batch_done, &s);
-    if (cfg.plain) cudaStreamSynchronize(s.stream);   // one request at a time
+    // one request at a time (plain), or a lone request on an idle device: the worker waits for it
+    // itself, which returns the result sooner than the completion callback's thread hand-offs
+    if (cfg.plain || (s.single && level == 0)) cudaStreamSynchronize(s.stream);
     return back;
 }
 
@@ -364,6 +369,8 @@ gs_status gs_server_create(gs_context *ctx, const gs_server_cfg *cfg, gs_server 
         s.stream = s.streams[0];
         if (!st && cudaMalloc(&s.out, sizeof(float) * image_floats(c) * c.max_batch) != cudaSuccess) st = GS_ERR_OOM;
         if (!st && cudaMalloc(&s.pairs_dev, sizeof(unsigned long long) * gs::kMaxBatch) != cudaSuccess) st = GS_ERR_OOM;
+        if (!st && cudaMallocHost(&s.ctr_host, sizeof(gs::FrameCounters)) != cudaSuccess) st = GS_ERR_OOM;
+        if (!st) memset(s.ctr_host, 0, sizeof(gs::FrameCounters));
         if (!st && cudaMallocHost(&s.pairs_host, sizeof(unsigned long long) * gs::kMaxBatch) != cudaSuccess)
             st = GS_ERR_OOM;
         if (st) {
@@ -394,6 +401,7 @@ gs_status gs_server_destroy(gs_server *sv) {
         cudaFree(s.out);
         cudaFree(s.pairs_dev);
         cudaFreeHost(s.pairs_host);
+        cudaFreeHost(s.ctr_host);
     }
     cudaGetLastError();
     delete sv;
