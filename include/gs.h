@@ -389,6 +389,41 @@ gs_status gs_server_get_stats(gs_server *server, gs_server_stats *out);
    in full batches; hold = 0: resume.  Errors: GS_ERR_INVALID_ARG (NULL server). */
 gs_status gs_server_hold(gs_server *server, int32_t hold);
 
+/* ------------------------------------------------------------------------------------------
+   Routing across replicas: frames and requests are independent units, so a machine with several
+   GPUs serves them with one gs_server per GPU, each holding its own copy of the scenes it serves.
+   The router sends each request to the replica that holds its scene and has the fewest image
+   pixels outstanding (submitted, not yet waited for; ties to the lower index), and keeps the
+   (replica, ticket) behind each router ticket.  Replicas are reached through a backend: either
+   gs_router_create_on_servers (gs_server objects, scenes placed with gs_router_place_scene) or any
+   caller-supplied pair of submit/wait functions (gs_router_create).  The paper renders on one GPU
+   and has no counterpart.  Thread-safe; submit never blocks on a device. */
+typedef struct gs_router gs_router;
+typedef struct {
+    /* submit a request for scene `scene` to replica `replica`; *ticket identifies it there */
+    gs_status (*submit)(void *user, int32_t replica, int32_t scene, const gs_camera *cam,
+                        const gs_render_opts *opts, float *rgb_host, double arrival_s, uint64_t *ticket);
+    /* wait for it (timeout_ms < 0: no limit); fills *out as gs_server_wait does */
+    gs_status (*wait)(void *user, int32_t replica, uint64_t ticket, int32_t timeout_ms, gs_request_stats *out);
+    void *user;
+} gs_router_backend;
+/* replicas 1..64.  Errors: GS_ERR_INVALID_ARG, GS_ERR_OOM. */
+gs_status gs_router_create(int32_t replicas, const gs_router_backend *backend, gs_router **out);
+/* Backend over gs_server objects (servers[i] = replica i, not owned by the router). */
+gs_status gs_router_create_on_servers(int32_t replicas, gs_server *const *servers, gs_router **out);
+gs_status gs_router_destroy(gs_router *router);
+/* Declares that replica `replica` holds scene id `scene` (0 <= scene < 4096); `handle` is that
+   replica's gs_scene for the server backend (ignored, may be NULL, for a custom backend). */
+gs_status gs_router_place_scene(gs_router *router, int32_t scene, int32_t replica, const gs_scene *handle);
+/* Routes one request.  Errors: GS_ERR_INVALID_ARG (scene placed nowhere), or the backend's. */
+gs_status gs_router_submit(gs_router *router, int32_t scene, const gs_camera *cam, const gs_render_opts *opts,
+                           float *rgb_host, double arrival_s, uint64_t *ticket);
+/* Waits for a routed request; *replica (nullable) receives where it ran.  Returns its status. */
+gs_status gs_router_wait(gs_router *router, uint64_t ticket, int32_t timeout_ms, gs_request_stats *out,
+                         int32_t *replica);
+/* Requests and image pixels outstanding on one replica. */
+gs_status gs_router_outstanding(gs_router *router, int32_t replica, int64_t *requests, int64_t *pixels);
+
 /* gs_sort_pairs without any allocation.  The paper has no counterpart: this entry point exists
    for callers that must not allocate device memory -- code handed its buffers by a host
    application that owns the device-memory budget (an embedded renderer, a plugin, a real-time

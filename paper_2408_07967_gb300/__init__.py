@@ -14,7 +14,7 @@ import ctypes as C
 
 from . import _native
 
-__all__ = ["GsError", "Context", "Scene", "Frame", "Server", "gs_camera_from", "gs_opts", "gs_sort_pairs", "lib"]
+__all__ = ["GsError", "Context", "Scene", "Frame", "Server", "Router", "gs_camera_from", "gs_opts", "gs_sort_pairs", "lib"]
 
 GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_PAIR_OVERFLOW", -4: "GS_ERR_CUDA",
@@ -370,6 +370,77 @@ class Server:
     def close(self):
         if getattr(self, "h", None):
             lib().gs_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Router:
+    """gs_router: requests routed across replicas (one server per GPU) by scene placement and
+    fewest outstanding pixels.  Router.on_servers(...) drives gs_server objects; Router(replicas,
+    submit, wait) takes Python callables (submit(replica, scene, cam_ptr, opts_ptr, rgb_ptr,
+    arrival_s) -> (status, ticket); wait(replica, ticket, timeout_ms, stats) -> status)."""
+
+    def __init__(self, replicas: int, submit=None, wait=None, _servers=None):
+        h = C.c_void_p()
+        self._keep = []
+        if _servers is not None:
+            arr = (C.c_void_p * replicas)(*[sv.h.value for sv in _servers])
+            self._keep.append((arr, _servers))
+            _check(lib().gs_router_create_on_servers(int(replicas), arr, C.byref(h)))
+        else:
+            def c_submit(user, replica, scene, cam, opts, rgb, arrival, ticket):
+                st, t = submit(replica, scene, cam, opts, rgb, arrival)
+                ticket[0] = t
+                return st
+
+            def c_wait(user, replica, ticket, timeout_ms, out):
+                return wait(replica, ticket, timeout_ms, _native.gs_request_stats.from_address(out))
+
+            cs, cw = _native.ROUTER_SUBMIT(c_submit), _native.ROUTER_WAIT(c_wait)
+            be = _native.gs_router_backend(cs, cw, None)
+            self._keep += [cs, cw, be]
+            _check(lib().gs_router_create(int(replicas), C.byref(be), C.byref(h)))
+        self.h = h
+        self.replicas = replicas
+
+    @classmethod
+    def on_servers(cls, servers) -> "Router":
+        return cls(len(servers), _servers=list(servers))
+
+    def place_scene(self, scene_id: int, replica: int, scene: Scene | None = None):
+        _check(lib().gs_router_place_scene(self.h, int(scene_id), int(replica), scene.h if scene else None))
+
+    def submit(self, scene_id: int, cam, rgb_host=None, opts=None, arrival_s: float = 0.0) -> int:
+        t = C.c_uint64()
+        o = opts or gs_opts()
+        ptr = C.c_void_p(rgb_host.data_ptr()) if rgb_host is not None else None
+        _check(lib().gs_router_submit(self.h, int(scene_id), C.byref(gs_camera_from(cam)), C.byref(o), ptr,
+                                      float(arrival_s), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        st = _native.gs_request_stats()
+        rep = C.c_int32(-1)
+        status = lib().gs_router_wait(self.h, C.c_uint64(ticket), int(timeout_ms), C.byref(st), C.byref(rep))
+        if status in (-1, -5):
+            raise GsError(status, lib().gs_last_error().decode(errors="replace"))
+        d = {k: getattr(st, k) for k, _ in _native.gs_request_stats._fields_}
+        d["status"] = status
+        return d, rep.value
+
+    def outstanding(self, replica: int):
+        r, p = C.c_int64(), C.c_int64()
+        _check(lib().gs_router_outstanding(self.h, int(replica), C.byref(r), C.byref(p)))
+        return r.value, p.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gs_router_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -67,6 +67,14 @@ class gs_alu_peaks(C.Structure):
 
 
 _vp = C.c_void_p
+ROUTER_SUBMIT = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.c_double, C.POINTER(C.c_uint64))
+ROUTER_WAIT = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int32, C.c_uint64, C.c_int32, C.c_void_p)
+
+
+class gs_router_backend(C.Structure):
+    _fields_ = [("submit", ROUTER_SUBMIT), ("wait", ROUTER_WAIT), ("user", C.c_void_p)]
+
 _pp = C.POINTER(C.c_void_p)
 _st = C.c_int32
 
@@ -107,6 +115,14 @@ PROTOTYPES = {
     "gs_sort_pairs": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _vp]),
     "gs_clock_s": (C.c_double, []),
     "gs_server_hold": (_st, [_vp, C.c_int32]),
+    "gs_router_create": (_st, [C.c_int32, C.POINTER(gs_router_backend), _pp]),
+    "gs_router_create_on_servers": (_st, [C.c_int32, C.POINTER(C.c_void_p), _pp]),
+    "gs_router_destroy": (_st, [_vp]),
+    "gs_router_place_scene": (_st, [_vp, C.c_int32, C.c_int32, _vp]),
+    "gs_router_submit": (_st, [_vp, C.c_int32, C.POINTER(gs_camera), C.POINTER(gs_render_opts), _vp, C.c_double,
+                               C.POINTER(C.c_uint64)]),
+    "gs_router_wait": (_st, [_vp, C.c_uint64, C.c_int32, C.POINTER(gs_request_stats), C.POINTER(C.c_int32)]),
+    "gs_router_outstanding": (_st, [_vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "gs_default_server_cfg": (_st, [C.POINTER(gs_server_cfg)]),
     "gs_server_create": (_st, [_vp, C.POINTER(gs_server_cfg), _pp]),
     "gs_server_destroy": (_st, [_vp]),

@@ -107,6 +107,58 @@ def test_plain_loop_one_at_a_time(setup):
     sv.close()
 
 
+def test_plain_loop_reports_overflow(setup):
+    """The one-at-a-time loop renders without an admission pass: a request whose pairs exceed the
+    capacity must still fail (from the frame's device status), and the others succeed."""
+    ctx, A, B, reqs, alone = setup
+    pairs = []
+    for sc, cam in reqs[:8]:
+        f = gs.Frame(ctx, sc.P, 1 << 22, cam.width, cam.height)
+        f.render(sc, cam)
+        pairs.append(f.stats()["pairs"])
+    cap = int(sorted(pairs)[-2]) + 1
+    sv = gs.Server(ctx, plain=True, pair_capacity=cap, max_gaussians=1 << 20, max_width=256, max_height=256)
+    outs, stats = run(sv, reqs[:8])
+    for i, (o, a, s) in enumerate(zip(outs, alone[:8], stats)):
+        assert s["pairs"] == pairs[i]
+        if pairs[i] > cap:
+            assert s["status"] == -3
+        else:
+            assert s["status"] == 0 and torch.equal(o, a)
+    sv.close()
+
+
+def test_router_over_two_servers(setup):
+    """The router's server backend: two servers (both on this GPU, independent of each other)
+    hold scene A, only the second holds scene B; every routed request renders bit-identical to
+    rendering it alone and lands where its scene is."""
+    ctx, A, B, reqs, alone = setup
+    kw = dict(slots=2, max_batch=4, pair_capacity=1 << 22, max_gaussians=1 << 20, max_width=256, max_height=256)
+    s0, s1 = gs.Server(ctx, **kw), gs.Server(ctx, **kw)
+    r = gs.Router.on_servers([s0, s1])
+    r.place_scene(0, 0, A)
+    r.place_scene(0, 1, A)
+    r.place_scene(1, 1, B)
+    outs, tickets = [], []
+    for sc, cam in reqs:
+        buf = torch.empty((3, cam.height, cam.width), dtype=torch.float32).pin_memory()
+        outs.append(buf)
+        tickets.append(r.submit(0 if sc is A else 1, cam, buf))
+    placed = []
+    for t in tickets:
+        st, rep = r.wait(t, 60000)
+        assert st["status"] == 0
+        placed.append(rep)
+    for (sc, cam), o, a, rep in zip(reqs, outs, alone, placed):
+        assert torch.equal(o, a)
+        if sc is B:
+            assert rep == 1
+    assert 0 in placed and all(r.outstanding(i) == (0, 0) for i in range(2))
+    r.close()
+    s0.close()
+    s1.close()
+
+
 def test_wait_timeout_and_bad_requests(setup):
     ctx, A, B, reqs, alone = setup
     sv = gs.Server(ctx, slots=1, max_batch=2, pair_capacity=1 << 22, max_gaussians=1 << 20, max_width=128,
