@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_sum(const __grid_constant__ 
 // order with the tile id alone as a 32-bit key -- a stable sort by tile then yields exactly the
 // (tile, depth, id) order of the 64-bit keys.
 template <bool DEPTH>
-__global__ void __launch_bounds__(kPreBlock, 4) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
+__global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
     __shared__ EmitSmem E;
     PreSmem &S = E.P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
