@@ -311,7 +311,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     size_t o_big = cv.take<uint4>(max_g), o_mid = cv.take<uint4>(max_g);
     size_t o_geo0 = cv.take<float4>(max_g), o_geo1 = cv.take<float4>(max_g), o_geo2 = cv.take<int4>(max_g);
     size_t o_hist = cv.take<unsigned>(8 * 256), o_offs = cv.take<unsigned>(8 * 256);
-    size_t o_desc = cv.take<unsigned long long>(f->sort.max_tiles * 256);
+    size_t o_desc = cv.take<unsigned long long>(sort_desc_words(f->sort.max_tiles));
     size_t o_rts = cv.take<unsigned>(f->sort.max_tiles * 256);
     size_t o_ctr = cv.take<FrameCounters>(1);
     f->bytes = align_up(cv.off, 256);
@@ -837,7 +837,7 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *vals, uint64_
         ctx->sort.max_tiles = 0;
         Carver cv;
         size_t oh = cv.take<unsigned>(8 * 256), oo = cv.take<unsigned>(8 * 256);
-        size_t od = cv.take<unsigned long long>(tiles * 256);
+        size_t od = cv.take<unsigned long long>(sort_desc_words(tiles));
         GS_CUDA(cudaMalloc(&ctx->sort_mem, cv.off));
         GS_CUDA(cudaMemset(ctx->sort_mem, 0, cv.off));
         char *b = (char *)ctx->sort_mem;

@@ -28,7 +28,8 @@ namespace {
 constexpr long long kNoAllocMaxPairs = 1ll << 21;                 // 2,097,152 pairs
 constexpr size_t kCtrWords = (sizeof(FrameCounters) + 7) / 8;     // tickets, epoch, status
 constexpr size_t kHistWords = (8 * 256 * sizeof(unsigned)) / 8;   // one [8][256] u32 table
-constexpr size_t kDescWords = 1024 * 256;                         // look-back descriptors
+constexpr size_t kDescTiles = 960;   // tiles of 3072 pairs: room for kNoAllocMaxPairs (683 tiles)
+constexpr size_t kDescWords = (kDescTiles + kDescTiles / 16) * 256;  // look-back descriptors (tile + block)
 constexpr size_t kScratchWords = kCtrWords + 2 * kHistWords + kDescWords;
 constexpr size_t kScratchBytes = kScratchWords * 8;
 static_assert(kScratchBytes <= (2u << 20) + (32u << 10), "the fixed scratch stays near 2 MiB");
@@ -99,7 +100,7 @@ extern "C" gs_status gs_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint6
     scr.hist = (unsigned *)(base + kCtrWords);
     scr.offs = (unsigned *)(base + kCtrWords + kHistWords);
     scr.desc = base + kCtrWords + 2 * kHistWords;
-    scr.max_tiles = (long long)(kDescWords / 256);
+    scr.max_tiles = (long long)kDescTiles;
     if (sort_max_tiles_for(n > 0 ? n : 1) > scr.max_tiles) {
         snprintf(g_msg, sizeof(g_msg), "descriptor area too small for %lld pairs", (long long)n);
         return report(GS_ERR_CAPACITY);

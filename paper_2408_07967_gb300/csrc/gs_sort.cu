@@ -7,10 +7,12 @@
 // pairs in ticket order, ranks them by digit with warp match/ballot (stable: warp-striped load
 // order equals input order), publishes its per-digit counts, places the tile in (digit, rank)
 // order in shared memory, and reads its predecessors' counts through a decoupled look-back over
-// epoch-tagged descriptors (up to 16 predecessors per round trip; no per-sort clearing; waits
-// bounded by kSpinLimit); then it writes runs of consecutive addresses.  For 32-bit keys the next
-// tile's keys and values arrive by bulk copy (cp.async.bulk on an mbarrier) while the current
-// tile is written out.
+// epoch-tagged descriptors (no per-sort clearing; waits bounded by kSpinLimit); then it writes runs
+// of consecutive addresses.  The look-back has two levels: a tile sums its own block of 16 tiles,
+// then whole-block descriptors that the last tile of each block publishes, 16 per round trip, so
+// the last of T tiles that all start together waits about 2 + T/256 round trips instead of T/16.
+// For 32-bit keys the next tile's keys and values arrive by bulk copy (cp.async.bulk on an
+// mbarrier) while the current tile is written out.
 //
 // Ranges: the first position of every tile id in the sorted keys by binary search; tile t
 // spans [start[t], start[t+1]).
@@ -26,10 +28,14 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr unsigned kDescAgg = 1u << 30;
 constexpr unsigned kDescPrefix = 2u << 30;
 constexpr unsigned kDescCount = (1u << 30) - 1;
-constexpr int kLookWindow = 16;
+constexpr int kLookWindow = 16;        // descriptors per look-back round trip
+constexpr int kLookBlock = 16;         // tiles per block descriptor
 
 int sort_tile_items() { return kSortTile; }
 long long sort_max_tiles_for(long long n) { return (n + kSortTile - 1) / kSortTile; }
+long long sort_desc_words(long long max_tiles) {
+    return (max_tiles + (max_tiles + kLookBlock - 1) / kLookBlock) * 256;
+}
 
 __device__ __forceinline__ long long pair_count(const unsigned long long *n_dev, long long n_host, long long cap) {
     long long n = n_dev ? (long long)*(const volatile unsigned long long *)n_dev : n_host;
@@ -159,6 +165,44 @@ struct ScatterSmem {
     int bulk[2];                   // buffer b was filled by a bulk copy (else: plain loads)
 };
 
+// Sums the descriptors at entries j, j-1, ..., lo (entry e at base[e * 256]) until one holds an
+// inclusive prefix: kLookWindow independent loads per round trip, aggregates added in order, a
+// descriptor not yet published re-read after a short sleep.  Returns 1 when a prefix ended the
+// walk, 0 when it ran past lo on aggregates alone, 2 on a timeout (status flagged).  The first
+// round reads `span` entries.
+__device__ __forceinline__ int look_back(const unsigned long long *base, long long j, long long lo,
+                                         unsigned long long tag, int span, unsigned &sum, FrameCounters *ctr) {
+    unsigned spins = 0;
+    while (j >= lo) {
+        unsigned long long d[kLookWindow];
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w)
+            d[w] = (w < span && j - w >= lo) ? *(const volatile unsigned long long *)(base + (j - w) * 256) : 0ull;
+        span = kLookWindow;
+        int w = 0;
+        bool done = false;
+#pragma unroll
+        for (int q = 0; q < kLookWindow; ++q) {
+            if (done || w != q || j - q < lo) continue;
+            const unsigned flag = (unsigned)d[q] & ~kDescCount;
+            if ((d[q] & 0xffffffff00000000ull) != tag || flag == 0) continue;   // not published yet
+            sum += (unsigned)d[q] & kDescCount;
+            if (flag == kDescPrefix) done = true;
+            w = q + 1;
+        }
+        if (done) return 1;
+        j -= w;
+        if (w == 0) {
+            if (++spins > kSpinLimit) {
+                atomicOr(&ctr->status, kStTimeout);
+                return 2;
+            }
+            __nanosleep(20);
+        }
+    }
+    return 0;
+}
+
 // One pass of the onesweep scatter.  Persistent CTAs take tiles in ticket order.  As soon as a
 // tile has its global digit offsets (after the look-back), the CTA takes its next ticket and
 // starts that tile's bulk copy into the other shared-memory buffer, so the copy overlaps the
@@ -174,8 +218,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
                                                                unsigned *__restrict__ vout,
                                                                const unsigned long long *n_dev, long long n_host,
                                                                long long cap, int pass, const unsigned *offs,
-                                                               unsigned long long *desc, FrameCounters *ctr,
-                                                               int bulk_ok) {
+                                                               unsigned long long *desc, unsigned long long *bdesc,
+                                                               FrameCounters *ctr, int bulk_ok) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -307,44 +351,26 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
             S.keys[db][pos] = k[i];
             S.vals[db][pos] = v[i];
         }
-        unsigned long long excl = 0;
+        unsigned excl = 0;
         if (tile > 0) {
-            // Look back kLookWindow predecessors per round trip (independent loads), summing
-            // aggregates in order until a prefix; a descriptor not yet published is re-read.
-            // The first round reads only the immediate predecessor, which has usually published
-            // its prefix already; later rounds read the whole window.
-            long long j = tile - 1;
-            unsigned spins = 0;
-            bool done = false;
-            int span = 1;
-            while (!done) {
-                unsigned long long d[kLookWindow];
-#pragma unroll
-                for (int w = 0; w < kLookWindow; ++w)
-                    d[w] = (w < span && j - w >= 0) ? *(const volatile unsigned long long *)(desc + (j - w) * 256 + tid)
-                                                     : 0ull;
-                span = kLookWindow;
-                int w = 0;
-#pragma unroll
-                for (int q = 0; q < kLookWindow; ++q) {
-                    if (done || w != q || j - q < 0) continue;
-                    const unsigned flag = (unsigned)d[q] & ~kDescCount;
-                    if ((d[q] & 0xffffffff00000000ull) != tag || flag == 0) continue;   // not published yet
-                    excl += (unsigned)d[q] & kDescCount;
-                    if (flag == kDescPrefix) done = true;
-                    w = q + 1;
-                }
-                if (done) break;
-                j -= w;
-                if (w == 0) {
-                    if (++spins > kSpinLimit) {
-                        atomicOr(&ctr->status, kStTimeout);
-                        break;
-                    }
-                    __nanosleep(20);
-                }
+            // Level 1: the tiles of this block before this one (in the first wave every tile has
+            // just started, so the whole window is read at once; later a tile's predecessor has
+            // usually published its prefix, so the first round reads it alone).  Level 2: whole
+            // blocks before this one.  The last tile of a block publishes the block's aggregate
+            // as soon as level 1 gives it, and the block's prefix with its own.
+            static_assert(kLookBlock <= kLookWindow, "one round trip covers a block");
+            const long long blk = tile / kLookBlock, lo = blk * kLookBlock;
+            const bool last_in_block = tile - lo == kLookBlock - 1;
+            int r = look_back(desc + tid, tile - 1, lo, tag, tile < gridDim.x ? kLookWindow : 1, excl, ctr);
+            if (r == 0 && blk > 0) {
+                if (last_in_block)
+                    *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescAgg | (excl + cnt_valid);
+                r = look_back(bdesc + tid, blk - 1, 0, tag, kLookWindow, excl, ctr);
             }
-            *(volatile unsigned long long *)my = tag | kDescPrefix | (unsigned)(excl + cnt_valid);
+            (void)r;   // a timeout has flagged the status; the pass's output is then void
+            *(volatile unsigned long long *)my = tag | kDescPrefix | (excl + cnt_valid);
+            if (last_in_block)
+                *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescPrefix | (excl + cnt_valid);
         }
         S.gbase[tid] = (unsigned long long)goff + excl;
         // this tile has published its prefix: take the next ticket now, so its copy overlaps the
@@ -685,7 +711,9 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
     unsigned *va = vals, *vb = vals_tmp;
     for (int p = 0; p < passes; ++p) {
         k_sort_scatter<K><<<grid, kSortThreads, sizeof(ScatterSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
-                                                                             scr.offs, scr.desc, ctr, bulk_ok);
+                                                                             scr.offs, scr.desc,
+                                                                             scr.desc + scr.max_tiles * 256, ctr,
+                                                                             bulk_ok);
         K *tk = ka;
         ka = kb;
         kb = tk;
