@@ -50,6 +50,8 @@ gs_status cuda_fail(cudaError_t e, const char *what) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Carves aligned slices out of one device allocation.
+constexpr size_t kHistBytes = 8 * 256 * sizeof(unsigned);   // the sort's [8][256] digit histograms
+
 struct Carver {
     size_t off = 0;
     template <class T>
@@ -310,10 +312,13 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     size_t o_dv0 = cv.take<unsigned>(max_g), o_dv1 = cv.take<unsigned>(max_g);
     size_t o_big = cv.take<uint4>(max_g), o_mid = cv.take<uint4>(max_g);
     size_t o_geo0 = cv.take<float4>(max_g), o_geo1 = cv.take<float4>(max_g), o_geo2 = cv.take<int4>(max_g);
-    size_t o_hist = cv.take<unsigned>(8 * 256), o_offs = cv.take<unsigned>(8 * 256);
+    size_t o_offs = cv.take<unsigned>(8 * 256);
     size_t o_desc = cv.take<unsigned long long>(sort_desc_words(f->sort.max_tiles));
     size_t o_rts = cv.take<unsigned>(f->sort.max_tiles * 256);
+    // the digit histograms sit right before the counters: one memset clears both every frame
+    size_t o_hist = cv.take<unsigned char>(kHistBytes);
     size_t o_ctr = cv.take<FrameCounters>(1);
+    static_assert(kHistBytes % 256 == 0, "the counters follow the histograms with no alignment gap");
     f->bytes = align_up(cv.off, 256);
     cudaError_t e = cudaMalloc(&f->mem, f->bytes);
     if (e != cudaSuccess) {
@@ -389,7 +394,7 @@ gs_status gs_frame_set_tuning(gs_frame *f, const gs_tuning *t) {
     if (t->blend_variant < 0 || t->blend_variant >= blend_variant_count())
         return fail(GS_ERR_INVALID_ARG, "blend_variant %d out of range", t->blend_variant);
     if (t->sort_mode < 0 || t->sort_mode > 1) return fail(GS_ERR_INVALID_ARG, "sort_mode %d not 0 or 1", t->sort_mode);
-    if (t->sort_algo < 0 || t->sort_algo > 1) return fail(GS_ERR_INVALID_ARG, "sort_algo %d not 0 or 1", t->sort_algo);
+    if (t->sort_algo < 0 || t->sort_algo > 2) return fail(GS_ERR_INVALID_ARG, "sort_algo %d not 0, 1 or 2", t->sort_algo);
     if ((t->blend_variant != f->tuning.blend_variant || t->sort_mode != f->tuning.sort_mode ||
          t->sort_algo != f->tuning.sort_algo) &&
         f->exec) {
@@ -545,8 +550,15 @@ static PreprocessArgs pre_args(gs_frame *f) {
 }
 
 // First half of the preprocess of f->batch: geometry and exact pair counts (k_pre_count).
+// Clears the per-frame counters and the digit histograms (adjacent in the frame); the sort epoch
+// and what follows it persist across frames.
+static gs_status clear_frame_counters(gs_frame *f, cudaStream_t st) {
+    GS_CUDA(cudaMemsetAsync(f->sort.hist, 0, kHistBytes + offsetof(FrameCounters, sort_epoch), st));
+    return GS_OK;
+}
+
 static gs_status batch_count(gs_frame *f, cudaStream_t st) {
-    GS_CUDA(cudaMemsetAsync(f->ctr, 0, offsetof(FrameCounters, sort_epoch), st));
+    if (gs_status r = clear_frame_counters(f, st)) return r;
     launch_pre_count(pre_args(f), st);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
@@ -554,7 +566,8 @@ static gs_status batch_count(gs_frame *f, cudaStream_t st) {
 
 // Second half: scan, (depth order,) and emission.  `counted`: batch_count already ran.
 static gs_status batch_emit(gs_frame *f, cudaStream_t st, bool counted) {
-    if (!counted) GS_CUDA(cudaMemsetAsync(f->ctr, 0, offsetof(FrameCounters, sort_epoch), st));
+    if (!counted)
+        if (gs_status r = clear_frame_counters(f, st)) return r;
     f->mode_used = f->tuning.sort_mode;
     const PreprocessArgs a = pre_args(f);
     if (f->mode_used == 1)
@@ -756,11 +769,11 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     out->contributions = (int64_t)c.evals[1];
     // count + scan + emit, sort, ranges, blend; the depth-ordered mode adds the visible-list
     // compaction, the 4-pass depth sort, the rank-chunk sums and scan and the medium- and
-    // large-Gaussian emission.  A sort runs histogram + offsets + one scatter per pass (onesweep) or count +
-    // scan + scatter per pass (reduce-then-scan).
-    const bool rts = f->tuning.sort_algo == 1;
-    const int sort_k = rts ? 3 * f->passes : 2 + f->passes;
-    const int depth_k = rts ? 12 : 6;
+    // large-Gaussian emission.  A sort runs histogram + offsets + one scatter per pass (onesweep),
+    // count + scan + scatter per pass (reduce-then-scan) or one fused launch (two passes or more).
+    const int algo = f->tuning.sort_algo;
+    const int sort_k = algo == 1 ? 3 * f->passes : algo == 2 && f->passes >= 2 ? 1 : 2 + f->passes;
+    const int depth_k = algo == 1 ? 12 : algo == 2 ? 1 : 6;
     out->kernels = f->mode_used == 1 ? 3 + 5 + depth_k + sort_k + 2 : 3 + sort_k + 2;
     return GS_OK;
 }
@@ -958,7 +971,7 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
     int best_mode = f->tuning.sort_mode, best_algo = f->tuning.sort_algo;
     float best_ms = 1e30f;
     for (int m = 0; m <= 1; ++m)
-        for (int a = 0; a <= 1; ++a) {
+        for (int a = 0; a <= 2; ++a) {
             gs_tuning t = f->tuning;
             t.sort_mode = m;
             t.sort_algo = a;

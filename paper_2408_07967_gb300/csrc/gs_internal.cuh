@@ -126,8 +126,10 @@ struct FrameCounters {
     unsigned int n_mid;              // two-level order: Gaussians left to k_emit_mid (one warp each)
     unsigned int mid_ticket;
     unsigned int sort_ticket[8];     // scatter-pass tickets
+    unsigned int sort_bar[9];        // fused sort: arrivals at grid barrier b (0..7) and exits (8);
+                                     // the last CTA out zeroes them for the next sort
     unsigned int sort_epoch;         // bumped once per sort; tags look-back descriptors
-    unsigned int pad1[5];
+    unsigned int pad1[4];
 };
 
 // ----------------------------------------------------------------------------------------------
@@ -353,7 +355,8 @@ struct SortScratch {
                                      // descriptors: per tile, then per block of tiles
     long long max_tiles;
     unsigned *counts = nullptr;      // [256][max_tiles] per-tile digit counts (reduce-then-scan)
-    int algo = 0;                    // 0 onesweep (decoupled look-back), 1 reduce-then-scan
+    int algo = 0;                    // 0 onesweep (decoupled look-back), 1 reduce-then-scan,
+                                     // 2 onesweep passes fused into one cooperative launch
 };
 
 int sort_tile_items();

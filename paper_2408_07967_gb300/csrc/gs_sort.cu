@@ -4,7 +4,7 @@
 // Sort (the stage FlashGS inherits from 3DGS's CUB SortPairs, Section 2.2): one pass over the
 // keys builds the 256-bin histograms of every 8-bit digit at once; a tiny kernel turns them into
 // exclusive digit offsets; then one scatter pass per digit.  A scatter CTA takes tiles of 3072
-// pairs in ticket order, ranks them by digit with warp match/ballot (stable: warp-striped load
+// pairs in ticket order, ranks them by digit with warp match/ballots (stable: warp-striped load
 // order equals input order), publishes its per-digit counts, places the tile in (digit, rank)
 // order in shared memory, and reads its predecessors' counts through a decoupled look-back over
 // epoch-tagged descriptors (no per-sort clearing; waits bounded by kSpinLimit); then it writes runs
@@ -25,11 +25,18 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 12;
 static_assert((kSortThreads * kSortItems * 4) % 16 == 0, "bulk copies of a full tile are whole 16-byte units");
 constexpr int kSortTile = kSortThreads * kSortItems;
+// The fused onesweep sort may take up to 14 items per thread for 64-bit keys, so that a pass of up
+// to 14 x 256 x (resident CTAs) pairs gives every CTA one tile: a second tile in some CTAs would
+// double the pass (tiles are at least kSortTile, so the descriptor area never grows).
+template <class K>
+constexpr int kMaxItems = sizeof(K) == 8 ? 14 : kSortItems;
+static_assert(32 * kMaxItems<unsigned long long> < 65536, "in-warp ranks fit 16 bits");
 constexpr unsigned kDescAgg = 1u << 30;
 constexpr unsigned kDescPrefix = 2u << 30;
 constexpr unsigned kDescCount = (1u << 30) - 1;
 constexpr int kLookWindow = 16;        // descriptors per look-back round trip
 constexpr int kLookBlock = 16;         // tiles per block descriptor
+constexpr unsigned kMatchRuns = 12;    // warps with at most this many digit runs rank by match
 
 int sort_tile_items() { return kSortTile; }
 long long sort_max_tiles_for(long long n) { return (n + kSortTile - 1) / kSortTile; }
@@ -56,6 +63,43 @@ __device__ __forceinline__ unsigned match_digit(unsigned d) {
 }
 
 // ------------------------------------------------------------------------------------------ histogram
+// Adds the digits of keys [0, n) taken by this thread (thread gtid of `stride`) to the per-pass
+// shared-memory histograms s_h[pass][256]: eight consecutive keys per thread and step, loaded
+// before any is counted, and equal digits of neighbouring keys (the pairs of one Gaussian share
+// their depth bytes) added as one run, so that far fewer atomics collide on one counter (keys are
+// 16-byte aligned whenever the base is; a misaligned base falls back to single keys).
+template <class K>
+__device__ __forceinline__ void hist_accumulate(const K *keys, long long n, int passes, unsigned *s_h, long long gtid,
+                                                long long stride) {
+    constexpr int V = 8;
+    const bool vec = ((uintptr_t)keys & 15u) == 0;
+    const long long nv = vec ? n / V : 0;
+    for (long long c = gtid; c < nv; c += stride) {
+        K k[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) k[j] = __ldcg(keys + c * V + j);
+        for (int p = 0; p < passes; ++p) {
+            unsigned cur = (unsigned)(k[0] >> (8 * p)) & 0xffu, run = 1u;
+#pragma unroll
+            for (int j = 1; j < V; ++j) {
+                const unsigned d = (unsigned)(k[j] >> (8 * p)) & 0xffu;
+                if (d == cur) {
+                    ++run;
+                } else {
+                    atomicAdd(&s_h[p * 256 + cur], run);
+                    cur = d;
+                    run = 1u;
+                }
+            }
+            atomicAdd(&s_h[p * 256 + cur], run);
+        }
+    }
+    for (long long i = nv * V + gtid; i < n; i += stride) {
+        const K k = __ldcg(keys + i);
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k >> (8 * p)) & 0xffu)], 1u);
+    }
+}
+
 template <class K>
 __global__ void __launch_bounds__(512) k_sort_hist(const K *keys, const unsigned long long *n_dev,
                                                    long long n_host, long long cap, int passes, unsigned *hist) {
@@ -63,24 +107,8 @@ __global__ void __launch_bounds__(512) k_sort_hist(const K *keys, const unsigned
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
     const long long n = pair_count(n_dev, n_host, cap);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    // four keys per thread and step, loaded before any is counted (keys are 16-byte aligned
-    // whenever the base is; a misaligned base falls back to single keys)
-    constexpr int V = 4;
-    const bool vec = ((uintptr_t)keys & 15u) == 0;
-    const long long nv = vec ? n / V : 0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nv; c += stride) {
-        K k[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) k[j] = __ldg(keys + c * V + j);
-#pragma unroll
-        for (int j = 0; j < V; ++j)
-            for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k[j] >> (8 * p)) & 0xffu)], 1u);
-    }
-    for (long long i = nv * V + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const K k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k >> (8 * p)) & 0xffu)], 1u);
-    }
+    hist_accumulate(keys, n, passes, s_h, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                    (long long)gridDim.x * blockDim.x);
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
@@ -154,8 +182,8 @@ constexpr int kBufs = sizeof(K) == 4 ? 2 : 1;
 
 template <class K>
 struct ScatterSmem {
-    K keys[kBufs<K>][kSortTile];   // tile being ranked / next tile in flight
-    unsigned vals[kBufs<K>][kSortTile];
+    K keys[kBufs<K>][kSortThreads * kMaxItems<K>];   // tile being ranked / next tile in flight
+    unsigned vals[kBufs<K>][kSortThreads * kMaxItems<K>];
     unsigned whist[kSortWarps][256];
     unsigned local_off[256];
     unsigned long long gbase[256];
@@ -203,6 +231,186 @@ __device__ __forceinline__ int look_back(const unsigned long long *base, long lo
     return 0;
 }
 
+// Starts staging tile t of a pass input into buffer b (one thread): a bulk copy for a full tile of
+// 16-byte-aligned 32-bit-key arrays, completing on the buffer's mbarrier; otherwise nothing (the
+// tile body loads the tile itself).
+template <class K>
+__device__ __forceinline__ void stage_tile(ScatterSmem<K> &S, int b, long long t, int tsize, const K *kin,
+                                           const unsigned *vin, long long nfull, int bulk_ok) {
+    S.tile[b] = t;
+    const bool bulk = kBufs<K> == 2 && bulk_ok && t < nfull;
+    S.bulk[b] = bulk;
+    if (bulk) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bar_expect(&S.bar[b], (unsigned)(tsize * (sizeof(K) + sizeof(unsigned))));
+        const int db = kBufs<K> == 2 ? b : 0;
+        bulk_g2s(S.keys[db], kin + t * tsize, (unsigned)(tsize * sizeof(K)), &S.bar[b]);
+        bulk_g2s(S.vals[db], vin + t * tsize, (unsigned)(tsize * sizeof(unsigned)), &S.bar[b]);
+    }
+}
+
+// One tile of `items` x 256 pairs (kSortItems <= items <= kMaxItems, uniform over the CTA) of a
+// scatter pass, run by the whole CTA once the per-warp digit counters are zero and the tile's
+// staging (stage_tile into buffer b) has been started: load, stable ranking, publish
+// of the tile's digit counts, placement in (digit, rank) order in shared memory, the two-level
+// look-back, then `next()` (the caller's hook, run once the tile's global offsets are known),
+// then the global writes in runs of consecutive addresses.  Returns false when the staged copy
+// did not arrive (status flagged; uniform over the CTA).
+template <class K, class Next>
+__device__ __forceinline__ bool scatter_tile(ScatterSmem<K> &S, int b, long long tile, const K *__restrict__ kin,
+                                             const unsigned *__restrict__ vin, K *__restrict__ kout,
+                                             unsigned *__restrict__ vout, long long n, int items, int shift,
+                                             unsigned goff,
+                                             unsigned long long *desc, unsigned long long *bdesc,
+                                             unsigned long long tag, FrameCounters *ctr, unsigned &phases, Next next) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    constexpr int M = kMaxItems<K>;
+    const int tsize = kSortThreads * items;
+    const int db = kBufs<K> == 2 ? b : 0;      // data buffer of this tile
+    const long long tbase = tile * tsize;
+    const int wofs = warp * (32 * items);
+    bool failed = false;
+
+    K k[M];
+    unsigned v[M];
+    unsigned rank[(M + 1) / 2] = {};           // two 16-bit in-warp ranks per register
+    if (S.bulk[b]) {
+        if (bar_wait(&S.bar[b], (phases >> b) & 1u)) {
+            phases ^= 1u << b;
+        } else {
+            if (lane == 0) atomicOr(&ctr->status, kStTimeout);
+            failed = true;
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (i >= items) break;
+            k[i] = S.keys[db][wofs + i * 32 + lane];
+            v[i] = S.vals[db][wofs + i * 32 + lane];
+        }
+    } else {
+        // L2-only loads: in the fused sort another CTA rewrote these lines since this SM last
+        // read them
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (i >= items) break;
+            const long long idx = tbase + wofs + i * 32 + lane;
+            if (idx < n) {
+                k[i] = __ldcg(kin + idx);
+                v[i] = __ldcg(vin + idx);
+            } else {
+                k[i] = (K)~(K)0;
+                v[i] = 0u;
+            }
+        }
+    }
+    if (__syncthreads_or(failed)) return false;
+    // stable warp-level ranking in (item, lane) order
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        if (i >= items) break;
+        const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+        // A hardware match costs about as much per distinct value as the eight ballots cost in
+        // all, so it serves warps whose digits come in few runs (keys of one Gaussian, nearly
+        // sorted bytes) and the ballots serve the rest; the run count takes one shuffle and one
+        // ballot.
+        const unsigned prev = __shfl_up_sync(FULL, d, 1);
+        const unsigned runs = __popc(__ballot_sync(FULL, lane == 0 || d != prev));
+        const unsigned peers = runs <= kMatchRuns ? __match_any_sync(FULL, d) : match_digit(d);
+        const unsigned before = __popc(peers & lt_mask);
+        const unsigned bb = S.whist[warp][d];
+        __syncwarp();
+        rank[i >> 1] |= (bb + before) << (16 * (i & 1));
+        if (before == 0) S.whist[warp][d] = bb + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread tid owns digit tid: warp-exclusive offsets and the tile count
+    unsigned cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const unsigned c = S.whist[w][tid];
+        S.whist[w][tid] = cnt;
+        cnt += c;
+    }
+    // tile-local exclusive scan over digits
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) S.wsum[warp] = incl;
+    // publish this tile's count of valid items for digit tid, then look back
+    const long long valid_here = min((long long)tsize, n - tbase);
+    const unsigned cnt_valid = tid == 255 ? cnt - (unsigned)(tsize - valid_here) : cnt;
+    // (a descriptor is one self-contained 64-bit word: nothing it describes needs a fence)
+    unsigned long long *my = desc + tile * 256 + tid;
+    if (tile == 0) {
+        *(volatile unsigned long long *)my = tag | kDescPrefix | cnt_valid;
+    } else {
+        *(volatile unsigned long long *)my = tag | kDescAgg | cnt_valid;
+    }
+    __syncthreads();
+    unsigned wex = 0;
+    for (int w = 0; w < warp; ++w) wex += S.wsum[w];
+    S.local_off[tid] = wex + incl - cnt;
+    __syncthreads();
+    // scatter into this tile's buffer (its contents are in registers) in (digit, rank) order
+    // before the look-back, so that only the digit's registers stay live while it waits
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        if (i >= items) break;
+        const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+        const unsigned pos = S.local_off[d] + S.whist[warp][d] + ((rank[i >> 1] >> (16 * (i & 1))) & 0xffffu);
+        S.keys[db][pos] = k[i];
+        S.vals[db][pos] = v[i];
+    }
+    unsigned excl = 0;
+    if (tile > 0) {
+        // Level 1: the tiles of this block before this one (in the first wave every tile has
+        // just started, so the whole window is read at once; later a tile's predecessor has
+        // usually published its prefix, so the first round reads it alone).  Level 2: whole
+        // blocks before this one.  The last tile of a block publishes the block's aggregate
+        // as soon as level 1 gives it, and the block's prefix with its own.
+        static_assert(kLookBlock <= kLookWindow, "one round trip covers a block");
+        const long long blk = tile / kLookBlock, lo = blk * kLookBlock;
+        const bool last_in_block = tile - lo == kLookBlock - 1;
+        int r = look_back(desc + tid, tile - 1, lo, tag, tile < gridDim.x ? kLookWindow : 1, excl, ctr);
+        if (r == 0 && blk > 0) {
+            if (last_in_block)
+                *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescAgg | (excl + cnt_valid);
+            r = look_back(bdesc + tid, blk - 1, 0, tag, kLookWindow, excl, ctr);
+        }
+        (void)r;   // a timeout has flagged the status; the pass's output is then void
+        *(volatile unsigned long long *)my = tag | kDescPrefix | (excl + cnt_valid);
+        if (last_in_block)
+            *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescPrefix | (excl + cnt_valid);
+    }
+    S.gbase[tid] = (unsigned long long)goff + excl;
+    next();
+    __syncthreads();
+    for (int s = tid; s < valid_here; s += kSortThreads) {
+        const K key = S.keys[db][s];
+        const unsigned d = (unsigned)(key >> shift) & 0xffu;
+        const unsigned long long dst = S.gbase[d] + (unsigned long long)(s - S.local_off[d]);
+        kout[dst] = key;
+        vout[dst] = S.vals[db][s];
+    }
+    __syncthreads();
+    return true;
+}
+
+// A failed wait leaves copies possibly in flight: give them a bounded chance to land (the phase
+// of a buffer is advanced only by a successful wait, so it names the pending one).
+template <class K>
+__device__ __forceinline__ void drain_staging(ScatterSmem<K> &S, unsigned phases) {
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 2; ++q)
+            if (S.bulk[q]) bar_wait(&S.bar[q], (phases >> q) & 1u);
+}
+
 // One pass of the onesweep scatter.  Persistent CTAs take tiles in ticket order.  As soon as a
 // tile has its global digit offsets (after the look-back), the CTA takes its next ticket and
 // starts that tile's bulk copy into the other shared-memory buffer, so the copy overlaps the
@@ -222,34 +430,19 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
                                                                FrameCounters *ctr, int bulk_ok) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned FULL = 0xffffffffu;
-    const int shift = 8 * pass;
+    const int tid = threadIdx.x;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
     const long long nfull = n / kSortTile;
     const unsigned epoch = *(volatile unsigned *)&ctr->sort_epoch;
     const unsigned long long tag = (unsigned long long)(epoch * 8u + (unsigned)pass) << 32;
-    const unsigned lt_mask = (1u << lane) - 1u;
     const unsigned goff = offs[pass * 256 + tid];
     unsigned phases = 0u;          // bit q: parity of buffer q's next pending phase
-    bool failed = false;
 
-    // Takes the next ticket into buffer b and starts its bulk copy when it is a full tile.
+    // Takes the next ticket into buffer b and starts its staging.
     auto fetch = [&](int b) {
-        if (tid == 0) {
-            const long long t = (long long)atomicAdd(&ctr->sort_ticket[pass], 1u);
-            S.tile[b] = t;
-            const bool bulk = kBufs<K> == 2 && bulk_ok && t < nfull;
-            S.bulk[b] = bulk;
-            if (bulk) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                bar_expect(&S.bar[b], (unsigned)(kSortTile * (sizeof(K) + sizeof(unsigned))));
-                const int db = kBufs<K> == 2 ? b : 0;
-                bulk_g2s(S.keys[db], kin + t * kSortTile, (unsigned)(kSortTile * sizeof(K)), &S.bar[b]);
-                bulk_g2s(S.vals[db], vin + t * kSortTile, (unsigned)(kSortTile * sizeof(unsigned)), &S.bar[b]);
-            }
-        }
+        if (tid == 0)
+            stage_tile(S, b, (long long)atomicAdd(&ctr->sort_ticket[pass], 1u), kSortTile, kin, vin, nfull, bulk_ok);
     };
 
     if (tid == 0) {
@@ -265,133 +458,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
         __syncthreads();
         const long long tile = S.tile[b];
         if (tile >= ntiles) break;
-        const int db = kBufs<K> == 2 ? b : 0;      // data buffer of this tile
-        const long long tbase = tile * kSortTile;
-        const int wofs = warp * (32 * kSortItems);
-
-        K k[kSortItems];
-        unsigned v[kSortItems];
-        unsigned rank[kSortItems];
-        if (S.bulk[b]) {
-            if (bar_wait(&S.bar[b], (phases >> b) & 1u)) {
-                phases ^= 1u << b;
-            } else {
-                if (lane == 0) atomicOr(&ctr->status, kStTimeout);
-                failed = true;
-            }
-#pragma unroll
-            for (int i = 0; i < kSortItems; ++i) {
-                k[i] = S.keys[db][wofs + i * 32 + lane];
-                v[i] = S.vals[db][wofs + i * 32 + lane];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < kSortItems; ++i) {
-                const long long idx = tbase + wofs + i * 32 + lane;
-                if (idx < n) {
-                    k[i] = kin[idx];
-                    v[i] = vin[idx];
-                } else {
-                    k[i] = (K)~(K)0;
-                    v[i] = 0u;
-                }
-            }
+        // once this tile has published its prefix, take the next ticket, so its copy overlaps
+        // the writes while no later tile waits on a ticket that is not being worked on
+        if (!scatter_tile(S, b, tile, kin, vin, kout, vout, n, kSortItems, 8 * pass, goff, desc, bdesc, tag, ctr,
+                          phases, [&] { fetch(b ^ 1); })) {
+            drain_staging(S, phases);
+            return;
         }
-        if (__syncthreads_or(failed)) break;
-        // stable warp-level ranking in (item, lane) order
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-            const unsigned peers = __match_any_sync(FULL, d);   // latency: it precedes the publish
-            const unsigned before = __popc(peers & lt_mask);
-            const unsigned bb = S.whist[warp][d];
-            __syncwarp();
-            rank[i] = bb + before;
-            if (before == 0) S.whist[warp][d] = bb + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        // thread tid owns digit tid: warp-exclusive offsets and the tile count
-        unsigned cnt = 0;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            const unsigned c = S.whist[w][tid];
-            S.whist[w][tid] = cnt;
-            cnt += c;
-        }
-        // tile-local exclusive scan over digits
-        unsigned incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) S.wsum[warp] = incl;
-        // publish this tile's count of valid items for digit tid, then look back
-        const long long valid_here = min((long long)kSortTile, n - tbase);
-        const unsigned cnt_valid = tid == 255 ? cnt - (unsigned)(kSortTile - valid_here) : cnt;
-        unsigned long long *my = desc + tile * 256 + tid;
-        __threadfence();
-        if (tile == 0) {
-            *(volatile unsigned long long *)my = tag | kDescPrefix | cnt_valid;
-        } else {
-            *(volatile unsigned long long *)my = tag | kDescAgg | cnt_valid;
-        }
-        __syncthreads();
-        unsigned wex = 0;
-        for (int w = 0; w < warp; ++w) wex += S.wsum[w];
-        S.local_off[tid] = wex + incl - cnt;
-        __syncthreads();
-        // scatter into this tile's buffer (its contents are in registers) in (digit, rank) order
-        // before the look-back, so that only the digit's registers stay live while it waits
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-            const unsigned pos = S.local_off[d] + S.whist[warp][d] + rank[i];
-            S.keys[db][pos] = k[i];
-            S.vals[db][pos] = v[i];
-        }
-        unsigned excl = 0;
-        if (tile > 0) {
-            // Level 1: the tiles of this block before this one (in the first wave every tile has
-            // just started, so the whole window is read at once; later a tile's predecessor has
-            // usually published its prefix, so the first round reads it alone).  Level 2: whole
-            // blocks before this one.  The last tile of a block publishes the block's aggregate
-            // as soon as level 1 gives it, and the block's prefix with its own.
-            static_assert(kLookBlock <= kLookWindow, "one round trip covers a block");
-            const long long blk = tile / kLookBlock, lo = blk * kLookBlock;
-            const bool last_in_block = tile - lo == kLookBlock - 1;
-            int r = look_back(desc + tid, tile - 1, lo, tag, tile < gridDim.x ? kLookWindow : 1, excl, ctr);
-            if (r == 0 && blk > 0) {
-                if (last_in_block)
-                    *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescAgg | (excl + cnt_valid);
-                r = look_back(bdesc + tid, blk - 1, 0, tag, kLookWindow, excl, ctr);
-            }
-            (void)r;   // a timeout has flagged the status; the pass's output is then void
-            *(volatile unsigned long long *)my = tag | kDescPrefix | (excl + cnt_valid);
-            if (last_in_block)
-                *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescPrefix | (excl + cnt_valid);
-        }
-        S.gbase[tid] = (unsigned long long)goff + excl;
-        // this tile has published its prefix: take the next ticket now, so its copy overlaps the
-        // scatter below while no later tile waits on a ticket that is not being worked on
-        fetch(b ^ 1);
-        __syncthreads();
-        for (int s = tid; s < valid_here; s += kSortThreads) {
-            const K key = S.keys[db][s];
-            const unsigned d = (unsigned)(key >> shift) & 0xffu;
-            const unsigned long long dst = S.gbase[d] + (unsigned long long)(s - S.local_off[d]);
-            kout[dst] = key;
-            vout[dst] = S.vals[db][s];
-        }
-        __syncthreads();
         b ^= 1;
-    }
-    // a failed wait leaves copies possibly in flight: give them a bounded chance to land (the
-    // phase of a buffer is advanced only by a successful wait, so it names the pending one)
-    if (failed && tid == 0) {
-        for (int q = 0; q < 2; ++q)
-            if (S.bulk[q]) bar_wait(&S.bar[q], (phases >> q) & 1u);
     }
 }
 
@@ -406,6 +480,170 @@ static int scatter_grid() {
                              (int)sizeof(ScatterSmem<K>));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_scatter<K>, kSortThreads,
                                                       sizeof(ScatterSmem<K>));
+        grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    return grid;
+}
+
+// ------------------------------------------------------------------------------------------ fused onesweep
+// Grid-wide barrier of a cooperative launch (every CTA resident) on a counter that starts at zero
+// and serves this one barrier: after a CTA-wide barrier one thread makes the CTA's writes visible,
+// adds its arrival without waiting for the result, and polls until every CTA has arrived.
+// Bounded: false after kSpinLimit polls, or as soon as another CTA has flagged a timeout (the
+// status then carries kStTimeout).
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned ncta, FrameCounters *ctr) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(count, 1u);
+        unsigned it = 0;
+        while (*(volatile unsigned *)count < ncta) {
+            if (++it > kSpinLimit || (*(volatile unsigned *)&ctr->status & kStTimeout)) {
+                atomicOr(&ctr->status, kStTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class K>
+struct FusedSmem {
+    ScatterSmem<K> s;
+    unsigned offs[8][256];         // exclusive digit offsets of every pass
+};
+
+// The whole sort in one cooperative launch (all CTAs resident, so tiles are dealt statically:
+// CTA c takes tiles c, c + G, ...; a tile waits only on smaller tiles, each of which its CTA
+// reaches without waiting on larger ones).  The histograms of every pass come first; a grid
+// barrier; every CTA scans them into its own digit offsets; then the passes, each ending in a
+// grid barrier before the next reads its output.  Removes the per-pass launch gap, the launch
+// ramp and the tickets, which dominate sorts of a few thousand tiles.  The pass ping-pongs
+// between (k0, v0) and (k1, v1), starting from (k0, v0).  The histograms are cleared for the
+// next sort once every CTA has read them (and, after a failed launch, by the frame's counter
+// clear); the epoch used for this sort's tags is published for the next one once every CTA has
+// read the previous value.  bars: nine counters, zero at the start (barriers 0..7, exits).
+template <class K>
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_fused(K *k0, unsigned *v0, K *k1, unsigned *v1,
+                                                             const unsigned long long *n_dev, long long n_host,
+                                                             long long cap, int passes, unsigned *hist,
+                                                             unsigned long long *desc, unsigned long long *bdesc,
+                                                             FrameCounters *ctr, unsigned *bars, int bulk_ok) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FusedSmem<K> &F = *reinterpret_cast<FusedSmem<K> *>(smem_raw);
+    ScatterSmem<K> &S = F.s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long n = pair_count(n_dev, n_host, cap);
+    // items per thread: the fewest (>= kSortItems) that give every CTA at most one tile, if any do
+    int items = kSortItems;
+    while (items < kMaxItems<K> && n > (long long)gridDim.x * kSortThreads * items) ++items;
+    const int tsize = kSortThreads * items;
+    const long long ntiles = (n + tsize - 1) / tsize;
+    const long long nfull = n / tsize;
+    const unsigned epoch = *(volatile unsigned *)&ctr->sort_epoch + 1u;
+    unsigned phases = 0u;
+    bool failed = false;
+
+    if (tid == 0) {
+        bar_init(&S.bar[0]);
+        bar_init(&S.bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    unsigned *s_h = &S.whist[0][0];
+    static_assert(sizeof(S.whist) >= 8 * 256 * sizeof(unsigned), "histograms of 8 passes fit the warp counters");
+    for (int i = tid; i < passes * 256; i += kSortThreads) s_h[i] = 0;
+    __syncthreads();
+    hist_accumulate((const K *)k0, n, passes, s_h, (long long)blockIdx.x * kSortThreads + tid,
+                    (long long)gridDim.x * kSortThreads);
+    __syncthreads();
+    for (int i = tid; i < passes * 256; i += kSortThreads)
+        if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
+    if (!grid_barrier(&bars[0], gridDim.x, ctr)) failed = true;
+    if (!failed && blockIdx.x == 0 && tid == 0) atomicMax(&ctr->sort_epoch, epoch);
+    unsigned hc[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) hc[p] = p < passes ? __ldcg(hist + p * 256 + tid) : 0u;   // all in flight
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        if (p >= passes || failed) break;
+        const unsigned c = hc[p];
+        unsigned incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) S.wsum[warp] = incl;
+        __syncthreads();
+        unsigned wex = 0;
+        for (int w = 0; w < warp; ++w) wex += S.wsum[w];
+        F.offs[p][tid] = wex + incl - c;
+        __syncthreads();
+    }
+    for (int pass = 0; pass < passes && !failed; ++pass) {
+        if (pass == 1 && blockIdx.x == 0)
+            for (int i = tid; i < passes * 256; i += kSortThreads) hist[i] = 0u;
+        const K *kin = (pass & 1) ? k1 : k0;
+        const unsigned *vin = (pass & 1) ? v1 : v0;
+        K *kout = (pass & 1) ? k0 : k1;
+        unsigned *vout = (pass & 1) ? v0 : v1;
+        const unsigned long long tag = (unsigned long long)(epoch * 8u + (unsigned)pass) << 32;
+        const unsigned goff = F.offs[pass][tid];
+        long long tile = blockIdx.x;
+        int b = 0;
+        if (tid == 0 && tile < ntiles) {
+            // the input was written by other CTAs (generic proxy) before the barrier; the bulk
+            // copies read it through the async proxy
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            stage_tile(S, b, tile, tsize, kin, vin, nfull, bulk_ok);
+        }
+        while (tile < ntiles) {
+            for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+            __syncthreads();
+            const long long nxt = tile + gridDim.x;
+            if (!scatter_tile(S, b, tile, kin, vin, kout, vout, n, items, 8 * pass, goff, desc, bdesc, tag, ctr,
+                              phases, [&] {
+                                  if (tid == 0 && nxt < ntiles)
+                                      stage_tile(S, b ^ 1, nxt, tsize, kin, vin, nfull, bulk_ok);
+                              })) {
+                failed = true;
+                break;
+            }
+            tile = nxt;
+            b ^= 1;
+        }
+        if (!failed && pass + 1 < passes && !grid_barrier(&bars[pass + 1], gridDim.x, ctr)) failed = true;
+    }
+    if (failed) {
+        // Some CTAs may have tagged descriptors with this epoch while others gave up before it
+        // was published: move the epoch well past every tag this launch can have used.  The
+        // barrier counters stay as they are until the frame's counter clear.
+        drain_staging(S, phases);
+        if (tid == 0) atomicAdd(&ctr->sort_epoch, 1024u);
+        return;
+    }
+    // the last CTA out (every other one has finished its last barrier wait) zeroes the counters
+    if (tid == 0 && atomicAdd(&bars[8], 1u) + 1u == gridDim.x)
+        for (int i = 0; i <= 8; ++i) *(volatile unsigned *)&bars[i] = 0u;
+}
+
+template <class K>
+static int fused_grid() {
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_sort_fused<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(FusedSmem<K>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_fused<K>, kSortThreads, sizeof(FusedSmem<K>));
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return grid;
@@ -702,6 +940,22 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
             va = vb;
             vb = tv;
         }
+        return passes;
+    }
+    if (scr.algo == 2 && passes >= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)min((long long)fused_grid<K>(), max_tiles > 0 ? max_tiles : 1));
+        cfg.blockDim = dim3(kSortThreads);
+        cfg.dynamicSmemBytes = sizeof(FusedSmem<K>);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_sort_fused<K>, keys, vals, keys_tmp, vals_tmp, n_dev, n_host, cap, passes, scr.hist,
+                           scr.desc, scr.desc + scr.max_tiles * 256, ctr,
+                           (unsigned *)((char *)ctr + offsetof(FrameCounters, sort_bar)), bulk_ok);
         return passes;
     }
     k_sort_hist<K><<<sms * 2, 512, 0, s>>>(keys, n_dev, n_host, cap, passes, scr.hist);

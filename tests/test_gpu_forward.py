@@ -100,7 +100,7 @@ def check(res, ref, check_unsorted=True, t_min=1e-4, alpha_max=0.99):
         assert np.all(ref.T[diff] <= stop_regime) and np.all(res["T"][diff] <= stop_regime)
 
 
-@pytest.mark.parametrize("sort_algo", [0, 1])
+@pytest.mark.parametrize("sort_algo", [0, 1, 2])
 @pytest.mark.parametrize("sort_mode", [0, 1])
 def test_tiny_config_parity(ctx, sort_mode, sort_algo):
     scene, cams = synth.load_config("tiny")
@@ -131,7 +131,7 @@ def test_raw_parameters_activated_on_device(ctx):
     check(run_gpu(ctx, scene, cam), ref)
 
 
-@pytest.mark.parametrize("sort_algo", [0, 1])
+@pytest.mark.parametrize("sort_algo", [0, 1, 2])
 @pytest.mark.parametrize("sort_mode", [0, 1])
 def test_large_gaussians_many_candidate_tiles(ctx, sort_mode, sort_algo):
     """Gaussians with hundreds of candidate tiles spread over many load-balanced steps."""
@@ -142,7 +142,7 @@ def test_large_gaussians_many_candidate_tiles(ctx, sort_mode, sort_algo):
     check(run_gpu(ctx, scene, cam, sort_mode=sort_mode, sort_algo=sort_algo), ref)
 
 
-@pytest.mark.parametrize("sort_algo", [0, 1])
+@pytest.mark.parametrize("sort_algo", [0, 1, 2])
 @pytest.mark.parametrize("sort_mode", [0, 1])
 def test_elongated_gaussians_row_runs(ctx, sort_mode, sort_algo):
     """Thin rotated ellipses up to a few hundred pixels long: many tiles are hit only through a
@@ -283,7 +283,7 @@ def test_autotune_picks_a_shape_and_caches_it(ctx, tmp_path):
     ref, _, _ = fr.render(sc, cams[0])
     cache = tmp_path / "tune.txt"
     t1 = fr.gs_autotune(sc, cams, cache_path=cache)
-    assert 0 <= t1["blend_variant"] < 6 and t1["sort_mode"] in (0, 1) and t1["sort_algo"] in (0, 1)
+    assert 0 <= t1["blend_variant"] < 6 and t1["sort_mode"] in (0, 1) and t1["sort_algo"] in (0, 1, 2)
     assert fr.gs_frame_get_tuning() == t1
     line = cache.read_text().strip().split()
     assert line[0] == "gs-autotune-v2"
