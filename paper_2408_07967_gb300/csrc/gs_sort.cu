@@ -64,35 +64,23 @@ __device__ __forceinline__ unsigned match_digit(unsigned d) {
 
 // ------------------------------------------------------------------------------------------ histogram
 // Adds the digits of keys [0, n) taken by this thread (thread gtid of `stride`) to the per-pass
-// shared-memory histograms s_h[pass][256]: eight consecutive keys per thread and step, loaded
-// before any is counted, and equal digits of neighbouring keys (the pairs of one Gaussian share
-// their depth bytes) added as one run, so that far fewer atomics collide on one counter (keys are
-// 16-byte aligned whenever the base is; a misaligned base falls back to single keys).
+// shared-memory histograms s_h[pass][256]: four consecutive keys per thread and step, loaded
+// before any is counted, so that the lanes of one atomic touch keys four apart (the pairs of one
+// Gaussian share their depth bytes: neighbouring keys would collide on one counter).  Keys are
+// 16-byte aligned whenever the base is; a misaligned base falls back to single keys.
 template <class K>
 __device__ __forceinline__ void hist_accumulate(const K *keys, long long n, int passes, unsigned *s_h, long long gtid,
                                                 long long stride) {
-    constexpr int V = 8;
+    constexpr int V = 4;
     const bool vec = ((uintptr_t)keys & 15u) == 0;
     const long long nv = vec ? n / V : 0;
     for (long long c = gtid; c < nv; c += stride) {
         K k[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) k[j] = __ldcg(keys + c * V + j);
-        for (int p = 0; p < passes; ++p) {
-            unsigned cur = (unsigned)(k[0] >> (8 * p)) & 0xffu, run = 1u;
 #pragma unroll
-            for (int j = 1; j < V; ++j) {
-                const unsigned d = (unsigned)(k[j] >> (8 * p)) & 0xffu;
-                if (d == cur) {
-                    ++run;
-                } else {
-                    atomicAdd(&s_h[p * 256 + cur], run);
-                    cur = d;
-                    run = 1u;
-                }
-            }
-            atomicAdd(&s_h[p * 256 + cur], run);
-        }
+        for (int j = 0; j < V; ++j)
+            for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k[j] >> (8 * p)) & 0xffu)], 1u);
     }
     for (long long i = nv * V + gtid; i < n; i += stride) {
         const K k = __ldcg(keys + i);
@@ -306,23 +294,39 @@ __device__ __forceinline__ bool scatter_tile(ScatterSmem<K> &S, int b, long long
         }
     }
     if (__syncthreads_or(failed)) return false;
+    // Per-warp lane masks of each digit, in this tile's value buffer (free until the placement
+    // below: the values are in registers).
+    unsigned(*mm)[256] = reinterpret_cast<unsigned(*)[256]>(&S.vals[db][0]);
+    static_assert(sizeof(S.vals[0]) >= sizeof(unsigned) * kSortWarps * 256, "match masks fit a value buffer");
+    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&mm[0][0])[i] = 0u;
+    __syncthreads();
     // stable warp-level ranking in (item, lane) order
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i >= items) break;
         const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-        // A hardware match costs about as much per distinct value as the eight ballots cost in
-        // all, so it serves warps whose digits come in few runs (keys of one Gaussian, nearly
-        // sorted bytes) and the ballots serve the rest; the run count takes one shuffle and one
-        // ballot.
+        // The lanes holding the same digit: a hardware match costs about as much per distinct
+        // value as a shared-memory OR costs per lane colliding on one digit, so the match serves
+        // warps whose digits come in few runs (keys of one Gaussian, nearly sorted bytes) and the
+        // OR the rest; the run count takes one shuffle and one ballot.
         const unsigned prev = __shfl_up_sync(FULL, d, 1);
-        const unsigned runs = __popc(__ballot_sync(FULL, lane == 0 || d != prev));
-        const unsigned peers = runs <= kMatchRuns ? __match_any_sync(FULL, d) : match_digit(d);
+        const bool few = __popc(__ballot_sync(FULL, lane == 0 || d != prev)) <= kMatchRuns;
+        unsigned peers;
+        if (few) {
+            peers = __match_any_sync(FULL, d);
+        } else {
+            atomicOr(&mm[warp][d], 1u << lane);
+            __syncwarp();
+            peers = mm[warp][d];
+        }
         const unsigned before = __popc(peers & lt_mask);
         const unsigned bb = S.whist[warp][d];
         __syncwarp();
         rank[i >> 1] |= (bb + before) << (16 * (i & 1));
-        if (before == 0) S.whist[warp][d] = bb + __popc(peers);
+        if (before == 0) {
+            S.whist[warp][d] = bb + __popc(peers);
+            if (!few) mm[warp][d] = 0u;
+        }
         __syncwarp();
     }
     __syncthreads();
