@@ -314,7 +314,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     size_t o_geo0 = cv.take<float4>(max_g), o_geo1 = cv.take<float4>(max_g), o_geo2 = cv.take<int4>(max_g);
     size_t o_offs = cv.take<unsigned>(8 * 256);
     size_t o_desc = cv.take<unsigned long long>(sort_desc_words(f->sort.max_tiles));
-    size_t o_rts = cv.take<unsigned>(f->sort.max_tiles * 256);
+    size_t o_rts = cv.take<unsigned>(rts_stride(f->sort.max_tiles) * 256);
     // the digit histograms sit right before the counters: one memset clears both every frame
     size_t o_hist = cv.take<unsigned char>(kHistBytes);
     size_t o_ctr = cv.take<FrameCounters>(1);

@@ -354,7 +354,8 @@ struct SortScratch {
     unsigned long long *desc;        // [sort_desc_words(max_tiles)] epoch-tagged look-back
                                      // descriptors: per tile, then per block of tiles
     long long max_tiles;
-    unsigned *counts = nullptr;      // [256][max_tiles] per-tile digit counts (reduce-then-scan)
+    unsigned *counts = nullptr;      // [256][rts_stride(max_tiles)] per-tile digit counts
+                                     // (reduce-then-scan)
     int algo = 0;                    // 0 onesweep (decoupled look-back), 1 reduce-then-scan,
                                      // 2 onesweep passes fused into one cooperative launch
 };
@@ -362,6 +363,7 @@ struct SortScratch {
 int sort_tile_items();
 long long sort_max_tiles_for(long long n);
 long long sort_desc_words(long long max_tiles);
+long long rts_stride(long long max_tiles);
 // Sorts by key bits [0, end_bit).  n_dev: device pointer to the pair count (clamped to cap);
 // returns the number of passes (result in the tmp buffers when odd).
 int launch_sort(unsigned long long *keys, unsigned *vals, unsigned long long *keys_tmp, unsigned *vals_tmp,

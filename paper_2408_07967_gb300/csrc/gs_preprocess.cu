@@ -430,8 +430,7 @@ __device__ __forceinline__ int block_scan_cand(PreSmem &S, int ncand) {
 // geometry for pass 3.
 __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constant__ PreprocessArgs A) {
     __shared__ PreSmem S;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x;
     const long long chunk = blockIdx.x;
     const int ri = req_of_chunk(A.B, chunk);
     const ReqDesc &R = A.B.r[ri];
@@ -604,8 +603,7 @@ template <bool DEPTH>
 __global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
     __shared__ EmitSmem E;
     PreSmem &S = E.P;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x;
     const long long chunk = blockIdx.x;
     long long gid;                    // here: the record index (request rec0 + Gaussian id)
     bool in_range;

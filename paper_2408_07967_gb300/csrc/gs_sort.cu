@@ -239,18 +239,18 @@ __device__ __forceinline__ void stage_tile(ScatterSmem<K> &S, int b, long long t
 
 // One tile of `items` x 256 pairs (kSortItems <= items <= kMaxItems, uniform over the CTA) of a
 // scatter pass, run by the whole CTA once the per-warp digit counters are zero and the tile's
-// staging (stage_tile into buffer b) has been started: load, stable ranking, publish
-// of the tile's digit counts, placement in (digit, rank) order in shared memory, the two-level
-// look-back, then `next()` (the caller's hook, run once the tile's global offsets are known),
-// then the global writes in runs of consecutive addresses.  Returns false when the staged copy
-// did not arrive (status flagged; uniform over the CTA).
-template <class K, class Next>
-__device__ __forceinline__ bool scatter_tile(ScatterSmem<K> &S, int b, long long tile, const K *__restrict__ kin,
-                                             const unsigned *__restrict__ vin, K *__restrict__ kout,
-                                             unsigned *__restrict__ vout, long long n, int items, int shift,
-                                             unsigned goff,
-                                             unsigned long long *desc, unsigned long long *bdesc,
-                                             unsigned long long tag, FrameCounters *ctr, unsigned &phases, Next next) {
+// staging (stage_tile into buffer b) has been started: load, stable ranking, `publish(cnt)` of
+// the tile's count of valid items of digit tid, placement in (digit, rank) order in shared
+// memory, `resolve(cnt)` -> the global position of the tile's first item of digit tid, `next()`,
+// then the global writes in runs of consecutive addresses.  The onesweep and the
+// reduce-then-scan passes differ only in the hooks.  Returns false when the staged copy did not
+// arrive (status flagged; uniform over the CTA).
+template <class K, class Publish, class Resolve, class Next>
+__device__ __forceinline__ bool sort_tile(ScatterSmem<K> &S, int b, long long tile, const K *__restrict__ kin,
+                                          const unsigned *__restrict__ vin, K *__restrict__ kout,
+                                          unsigned *__restrict__ vout, long long n, int items, int shift,
+                                          FrameCounters *ctr, unsigned &phases, Publish publish, Resolve resolve,
+                                          Next next) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -346,23 +346,18 @@ __device__ __forceinline__ bool scatter_tile(ScatterSmem<K> &S, int b, long long
         if (lane >= o) incl += y;
     }
     if (lane == 31) S.wsum[warp] = incl;
-    // publish this tile's count of valid items for digit tid, then look back
+    // the tile's count of valid items for digit tid (padding keys all have digit 255)
     const long long valid_here = min((long long)tsize, n - tbase);
     const unsigned cnt_valid = tid == 255 ? cnt - (unsigned)(tsize - valid_here) : cnt;
-    // (a descriptor is one self-contained 64-bit word: nothing it describes needs a fence)
-    unsigned long long *my = desc + tile * 256 + tid;
-    if (tile == 0) {
-        *(volatile unsigned long long *)my = tag | kDescPrefix | cnt_valid;
-    } else {
-        *(volatile unsigned long long *)my = tag | kDescAgg | cnt_valid;
-    }
+    publish(cnt_valid);
     __syncthreads();
     unsigned wex = 0;
     for (int w = 0; w < warp; ++w) wex += S.wsum[w];
     S.local_off[tid] = wex + incl - cnt;
     __syncthreads();
-    // scatter into this tile's buffer (its contents are in registers) in (digit, rank) order
-    // before the look-back, so that only the digit's registers stay live while it waits
+    // place the tile in (digit, rank) order in its own buffer (its contents are in registers)
+    // before resolving the global positions, so that no item registers stay live while the
+    // onesweep look-back waits
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i >= items) break;
@@ -371,28 +366,7 @@ __device__ __forceinline__ bool scatter_tile(ScatterSmem<K> &S, int b, long long
         S.keys[db][pos] = k[i];
         S.vals[db][pos] = v[i];
     }
-    unsigned excl = 0;
-    if (tile > 0) {
-        // Level 1: the tiles of this block before this one (in the first wave every tile has
-        // just started, so the whole window is read at once; later a tile's predecessor has
-        // usually published its prefix, so the first round reads it alone).  Level 2: whole
-        // blocks before this one.  The last tile of a block publishes the block's aggregate
-        // as soon as level 1 gives it, and the block's prefix with its own.
-        static_assert(kLookBlock <= kLookWindow, "one round trip covers a block");
-        const long long blk = tile / kLookBlock, lo = blk * kLookBlock;
-        const bool last_in_block = tile - lo == kLookBlock - 1;
-        int r = look_back(desc + tid, tile - 1, lo, tag, tile < gridDim.x ? kLookWindow : 1, excl, ctr);
-        if (r == 0 && blk > 0) {
-            if (last_in_block)
-                *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescAgg | (excl + cnt_valid);
-            r = look_back(bdesc + tid, blk - 1, 0, tag, kLookWindow, excl, ctr);
-        }
-        (void)r;   // a timeout has flagged the status; the pass's output is then void
-        *(volatile unsigned long long *)my = tag | kDescPrefix | (excl + cnt_valid);
-        if (last_in_block)
-            *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescPrefix | (excl + cnt_valid);
-    }
-    S.gbase[tid] = (unsigned long long)goff + excl;
+    S.gbase[tid] = resolve(cnt_valid);
     next();
     __syncthreads();
     for (int s = tid; s < valid_here; s += kSortThreads) {
@@ -404,6 +378,41 @@ __device__ __forceinline__ bool scatter_tile(ScatterSmem<K> &S, int b, long long
     }
     __syncthreads();
     return true;
+}
+
+// The onesweep hooks: publish the tile's count as an aggregate (a prefix for tile 0; a descriptor
+// is one self-contained 64-bit word, so nothing it describes needs a fence), and resolve the
+// global position by the two-level look-back.  Level 1: the tiles of this block before this one
+// (in the first wave every tile has just started, so the whole window is read at once; later a
+// tile's predecessor has usually published its prefix, so the first round reads it alone).
+// Level 2: whole blocks before this one.  The last tile of a block publishes the block's
+// aggregate as soon as level 1 gives it, and the block's prefix with its own.
+__device__ __forceinline__ void onesweep_publish(unsigned long long *desc, long long tile, unsigned long long tag,
+                                                 unsigned cnt) {
+    *(volatile unsigned long long *)(desc + tile * 256 + threadIdx.x) = tag | (tile == 0 ? kDescPrefix : kDescAgg) | cnt;
+}
+
+__device__ __forceinline__ unsigned long long onesweep_resolve(unsigned long long *desc, unsigned long long *bdesc,
+                                                               long long tile, unsigned long long tag, unsigned goff,
+                                                               unsigned cnt, FrameCounters *ctr) {
+    const int tid = threadIdx.x;
+    unsigned excl = 0;
+    if (tile > 0) {
+        static_assert(kLookBlock <= kLookWindow, "one round trip covers a block");
+        const long long blk = tile / kLookBlock, lo = blk * kLookBlock;
+        const bool last_in_block = tile - lo == kLookBlock - 1;
+        int r = look_back(desc + tid, tile - 1, lo, tag, tile < gridDim.x ? kLookWindow : 1, excl, ctr);
+        if (r == 0 && blk > 0) {
+            if (last_in_block)
+                *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescAgg | (excl + cnt);
+            r = look_back(bdesc + tid, blk - 1, 0, tag, kLookWindow, excl, ctr);
+        }
+        (void)r;   // a timeout has flagged the status; the pass's output is then void
+        *(volatile unsigned long long *)(desc + tile * 256 + tid) = tag | kDescPrefix | (excl + cnt);
+        if (last_in_block)
+            *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescPrefix | (excl + cnt);
+    }
+    return (unsigned long long)goff + excl;
 }
 
 // A failed wait leaves copies possibly in flight: give them a bounded chance to land (the phase
@@ -464,8 +473,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
         if (tile >= ntiles) break;
         // once this tile has published its prefix, take the next ticket, so its copy overlaps
         // the writes while no later tile waits on a ticket that is not being worked on
-        if (!scatter_tile(S, b, tile, kin, vin, kout, vout, n, kSortItems, 8 * pass, goff, desc, bdesc, tag, ctr,
-                          phases, [&] { fetch(b ^ 1); })) {
+        if (!sort_tile(
+                S, b, tile, kin, vin, kout, vout, n, kSortItems, 8 * pass, ctr, phases,
+                [&](unsigned c) { onesweep_publish(desc, tile, tag, c); },
+                [&](unsigned c) { return onesweep_resolve(desc, bdesc, tile, tag, goff, c, ctr); },
+                [&] { fetch(b ^ 1); })) {
             drain_staging(S, phases);
             return;
         }
@@ -612,11 +624,13 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_fused(K *k0, unsigned 
             for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
             __syncthreads();
             const long long nxt = tile + gridDim.x;
-            if (!scatter_tile(S, b, tile, kin, vin, kout, vout, n, items, 8 * pass, goff, desc, bdesc, tag, ctr,
-                              phases, [&] {
-                                  if (tid == 0 && nxt < ntiles)
-                                      stage_tile(S, b ^ 1, nxt, tsize, kin, vin, nfull, bulk_ok);
-                              })) {
+            if (!sort_tile(
+                    S, b, tile, kin, vin, kout, vout, n, items, 8 * pass, ctr, phases,
+                    [&](unsigned c) { onesweep_publish(desc, tile, tag, c); },
+                    [&](unsigned c) { return onesweep_resolve(desc, bdesc, tile, tag, goff, c, ctr); },
+                    [&] {
+                        if (tid == 0 && nxt < ntiles) stage_tile(S, b ^ 1, nxt, tsize, kin, vin, nfull, bulk_ok);
+                    })) {
                 failed = true;
                 break;
             }
@@ -665,7 +679,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rts_count(const K *__restrict_
                                                             long long n_host, long long cap, int pass,
                                                             unsigned *counts, long long stride) {
     __shared__ unsigned s_h[256];
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int shift = 8 * pass;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
@@ -691,24 +705,35 @@ __global__ void __launch_bounds__(kSortThreads) k_rts_count(const K *__restrict_
 // One CTA per digit: counts[d][t] becomes the sum of counts[d][t'] over t' < t, and the row's total
 // goes to tot[d] (the scatter turns the 256 totals into the digits' global offsets).
 constexpr int kRtsScanThreads = 1024;
-constexpr int kRtsScanRun = 24;   // 24576 tiles per sweep
+// Row stride of the per-tile digit counts: a multiple of 4, so that every row is 16-byte aligned.
+long long rts_stride(long long max_tiles) { return (max_tiles + 3) & ~3ll; }
+
+// One CTA per digit: counts[d][t] becomes the sum of counts[d][t'] over t' < t, and the row's total
+// goes to tot[d] (the scatter turns the 256 totals into the digits' global offsets).  The row is
+// read and written four entries per thread (16-byte accesses, coalesced), 4096 entries per step,
+// with a block-wide scan of the threads' sums and a running carry; entries past the last tile
+// count as zero.
 __global__ void __launch_bounds__(kRtsScanThreads) k_rts_scan(unsigned *counts, long long stride,
                                                               const unsigned long long *n_dev, long long n_host,
                                                               long long cap, unsigned *tot_out) {
     __shared__ unsigned s_w[kRtsScanThreads / 32];
-    __shared__ unsigned s_carry;
     const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
-    unsigned *row = counts + (long long)d * stride;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    for (long long b0 = 0; b0 < ntiles; b0 += (long long)kRtsScanThreads * kRtsScanRun) {
-        const long long my0 = b0 + (long long)tid * kRtsScanRun;
-        unsigned sum = 0;
-#pragma unroll 8
-        for (int r = 0; r < kRtsScanRun; ++r)
-            if (my0 + r < ntiles) sum += row[my0 + r];
+    const long long n4 = (ntiles + 3) / 4;          // within the row: stride is a multiple of 4, >= ntiles
+    uint4 *row = reinterpret_cast<uint4 *>(counts + (long long)d * stride);
+    unsigned carry = 0;
+    for (long long c0 = 0; c0 < n4; c0 += kRtsScanThreads) {
+        const long long i = c0 + tid;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (i < n4) {
+            v = row[i];
+            const long long t = 4 * i;
+            if (t + 1 >= ntiles) v.y = 0u;
+            if (t + 2 >= ntiles) v.z = 0u;
+            if (t + 3 >= ntiles) v.w = 0u;
+        }
+        const unsigned sum = v.x + v.y + v.z + v.w;
         unsigned incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -724,32 +749,20 @@ __global__ void __launch_bounds__(kRtsScanThreads) k_rts_scan(unsigned *counts, 
             wex += w < warp ? x : 0u;
             tot += x;
         }
-        unsigned run = s_carry + wex + incl - sum;
-#pragma unroll 8
-        for (int r = 0; r < kRtsScanRun; ++r)
-            if (my0 + r < ntiles) {
-                const unsigned x = row[my0 + r];    // read before this thread overwrites it
-                row[my0 + r] = run;
-                run += x;
-            }
-        __syncthreads();
-        if (tid == 0) s_carry += tot;
+        if (i < n4) {
+            const unsigned e = carry + wex + incl - sum;
+            row[i] = make_uint4(e, e + v.x, e + v.x + v.y, e + v.x + v.y + v.z);
+        }
+        carry += tot;
         __syncthreads();
     }
-    if (tid == 0) tot_out[d] = s_carry;
+    if (tid == 0) tot_out[d] = carry;
 }
 
-template <class K>
-struct RtsSmem {
-    K keys[kBufs<K>][kSortTile];     // tile being ranked / next tile arriving (32-bit keys)
-    unsigned vals[kBufs<K>][kSortTile];
-    unsigned whist[kSortWarps][256];
-    unsigned local_off[256];
-    unsigned gbase[256];
-    unsigned wsum[kSortWarps];
-    unsigned long long bar[2];
-};
-
+// Tiles are dealt round-robin, so each CTA knows its next tile: with 32-bit keys its bulk copy
+// (full tiles of 16-byte-aligned arrays) lands in the other buffer while this one is ranked.  The
+// global position of the tile's first item of digit d is the digit's offset (the exclusive scan
+// of the digit totals) plus offs_t[d][tile].
 template <class K>
 __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__restrict__ kin,
                                                               const unsigned *__restrict__ vin, K *__restrict__ kout,
@@ -759,13 +772,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__rest
                                                               long long stride, const unsigned *tot,
                                                               int bulk_ok, FrameCounters *ctr) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    RtsSmem<K> &S = *reinterpret_cast<RtsSmem<K> *>(smem_raw);
+    ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned FULL = 0xffffffffu;
-    const int shift = 8 * pass;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
-    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long nfull = n / kSortTile;
     // global offset of digit tid: exclusive scan of the digit totals
     unsigned dbase;
     {
@@ -773,7 +784,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__rest
         unsigned incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(FULL, incl, o);
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
         if (lane == 31) S.wsum[warp] = incl;
@@ -781,120 +792,29 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__rest
         unsigned wex = 0;
         for (int w = 0; w < warp; ++w) wex += S.wsum[w];
         dbase = wex + incl - c;
-        __syncthreads();
     }
-    // Tiles are dealt round-robin, so each CTA knows its next tile: with 32-bit keys its bulk copy
-    // (full tiles of 16-byte-aligned arrays) lands in the other buffer while this one is ranked.
-    const long long nfull = n / kSortTile;
-    constexpr bool kPrefetch = kBufs<K> == 2;
     unsigned phases = 0u;
-    bool failed = false;
-    auto issue = [&](long long t, int b) {
-        if (kPrefetch && tid == 0 && bulk_ok && t < nfull) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bar_expect(&S.bar[b], (unsigned)(kSortTile * (sizeof(K) + sizeof(unsigned))));
-            bulk_g2s(S.keys[b], kin + t * kSortTile, (unsigned)(kSortTile * sizeof(K)), &S.bar[b]);
-            bulk_g2s(S.vals[b], vin + t * kSortTile, (unsigned)(kSortTile * sizeof(unsigned)), &S.bar[b]);
-        }
-    };
-    if (kPrefetch && tid == 0) {
+    if (tid == 0) {
         bar_init(&S.bar[0]);
         bar_init(&S.bar[1]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    issue(blockIdx.x, 0);
-    int it = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int b = kPrefetch ? (it & 1) : 0;
+    if (tid == 0 && blockIdx.x < ntiles) stage_tile(S, 0, (long long)blockIdx.x, kSortTile, kin, vin, nfull, bulk_ok);
+    int b = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
-        S.gbase[tid] = dbase + offs_t[(long long)tid * stride + tile];
-        issue(tile + gridDim.x, b ^ 1);      // the other buffer was released at the end of the last tile
-        const long long tbase = tile * kSortTile;
-        const long long wbase = tbase + (long long)warp * (32 * kSortItems);
-        K k[kSortItems];
-        unsigned v[kSortItems];
-        unsigned rank[kSortItems];
-        if (kPrefetch && bulk_ok && tile < nfull) {
-            if (bar_wait(&S.bar[b], (phases >> b) & 1u)) {
-                phases ^= 1u << b;
-            } else {
-                if (lane == 0) atomicOr(&ctr->status, kStTimeout);
-                failed = true;
-            }
-            const int wofs = warp * (32 * kSortItems);
-#pragma unroll
-            for (int i = 0; i < kSortItems; ++i) {
-                k[i] = S.keys[b][wofs + i * 32 + lane];
-                v[i] = S.vals[b][wofs + i * 32 + lane];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < kSortItems; ++i) {
-                const long long idx = wbase + i * 32 + lane;
-                if (idx < n) {
-                    k[i] = kin[idx];
-                    v[i] = vin[idx];
-                } else {
-                    k[i] = (K)~(K)0;
-                    v[i] = 0u;
-                }
-            }
-        }
-        if (__syncthreads_or(failed)) break;
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-            const unsigned peers = match_digit(d);
-            const unsigned before = __popc(peers & lt_mask);
-            const unsigned bb = S.whist[warp][d];
-            __syncwarp();
-            rank[i] = bb + before;
-            if (before == 0) S.whist[warp][d] = bb + __popc(peers);
-            __syncwarp();
-        }
+        const unsigned long long gb = (unsigned long long)dbase + offs_t[(long long)tid * stride + tile];
         __syncthreads();
-        unsigned cnt = 0;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            const unsigned c = S.whist[w][tid];
-            S.whist[w][tid] = cnt;
-            cnt += c;
+        // the other buffer was released at the end of the last tile
+        if (tid == 0 && tile + gridDim.x < ntiles)
+            stage_tile(S, b ^ 1, tile + gridDim.x, kSortTile, kin, vin, nfull, bulk_ok);
+        if (!sort_tile(S, b, tile, kin, vin, kout, vout, n, kSortItems, 8 * pass, ctr, phases, [](unsigned) {},
+                       [&](unsigned) { return gb; }, [] {})) {
+            drain_staging(S, phases);
+            return;
         }
-        unsigned incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) S.wsum[warp] = incl;
-        __syncthreads();
-        unsigned wex = 0;
-        for (int w = 0; w < warp; ++w) wex += S.wsum[w];
-        S.local_off[tid] = wex + incl - cnt;
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-            const unsigned pos = S.local_off[d] + S.whist[warp][d] + rank[i];
-            S.keys[b][pos] = k[i];
-            S.vals[b][pos] = v[i];
-        }
-        __syncthreads();
-        const long long valid_here = min((long long)kSortTile, n - tbase);
-        for (int s = tid; s < valid_here; s += kSortThreads) {
-            const K key = S.keys[b][s];
-            const unsigned d = (unsigned)(key >> shift) & 0xffu;
-            const unsigned long long dst = (unsigned long long)S.gbase[d] + (unsigned long long)(s - S.local_off[d]);
-            kout[dst] = key;
-            vout[dst] = S.vals[b][s];
-        }
-        __syncthreads();
-    }
-    // a failed wait leaves copies possibly in flight: give them a bounded chance to land
-    if (kPrefetch && failed && tid == 0) {
-        bar_wait(&S.bar[0], phases & 1u);
-        bar_wait(&S.bar[1], (phases >> 1) & 1u);
+        b ^= 1;
     }
 }
 
@@ -905,8 +825,9 @@ static int rts_scatter_grid() {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_rts_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RtsSmem<K>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rts_scatter<K>, kSortThreads, sizeof(RtsSmem<K>));
+        cudaFuncSetAttribute(k_rts_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ScatterSmem<K>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rts_scatter<K>, kSortThreads, sizeof(ScatterSmem<K>));
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return grid;
@@ -930,13 +851,13 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
         const int rgrid = (int)min((long long)rts_scatter_grid<K>(), max_tiles > 0 ? max_tiles : 1);
         K *ka = keys, *kb = keys_tmp;
         unsigned *va = vals, *vb = vals_tmp;
+        const long long stride = rts_stride(scr.max_tiles);
         for (int p = 0; p < passes; ++p) {
-            k_rts_count<K><<<cgrid, kSortThreads, 0, s>>>(ka, n_dev, n_host, cap, p, scr.counts, scr.max_tiles);
-            k_rts_scan<<<256, kRtsScanThreads, 0, s>>>(scr.counts, scr.max_tiles, n_dev, n_host, cap,
-                                                       scr.offs + p * 256);
-            k_rts_scatter<K><<<rgrid, kSortThreads, sizeof(RtsSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
-                                                                           scr.counts, scr.max_tiles,
-                                                                           scr.offs + p * 256, bulk_ok, ctr);
+            k_rts_count<K><<<cgrid, kSortThreads, 0, s>>>(ka, n_dev, n_host, cap, p, scr.counts, stride);
+            k_rts_scan<<<256, kRtsScanThreads, 0, s>>>(scr.counts, stride, n_dev, n_host, cap, scr.offs + p * 256);
+            k_rts_scatter<K><<<rgrid, kSortThreads, sizeof(ScatterSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
+                                                                               scr.counts, stride,
+                                                                               scr.offs + p * 256, bulk_ok, ctr);
             K *tk = ka;
             ka = kb;
             kb = tk;
