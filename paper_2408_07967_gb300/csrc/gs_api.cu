@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 using namespace gs;
@@ -543,6 +545,9 @@ static PreprocessArgs pre_args(gs_frame *f) {
     a.chunk_base2 = f->chunk_base2;
     a.big = f->big;
     a.mid = f->mid;
+    // the sort's second key buffer is free until the sort: the count pass keeps its masks there
+    a.masks = (unsigned char *)f->keys[1];
+    a.mask_cap = std::min<long long>(8ll * f->max_pairs, 0xfffffffell);
     a.ctr = f->ctr;
     a.pair_cap = f->max_pairs;
     a.n_chunks = f->batch.total_chunks;
@@ -935,7 +940,7 @@ extern "C" gs_status gs_autotune(gs_frame *f, const gs_scene *s, const gs_camera
                     sscanf(line + kl + 1, "%d %d %d", &found_v, &found_m, &found_a);
             fclose(fp);
             if (found_v >= 0 && found_v < blend_variant_count() && (found_m == 0 || found_m == 1) &&
-                (found_a == 0 || found_a == 1)) {
+                found_a >= 0 && found_a <= 2) {
                 gs_tuning t = f->tuning;
                 t.blend_variant = found_v;
                 t.sort_mode = found_m;

@@ -121,6 +121,7 @@ struct FrameCounters {
     unsigned int chunk_ticket;       // preprocess chunk ticket
     unsigned long long n_vis64;      // paired Gaussians (two-level order)
     unsigned long long scratch64;    // unused scan total
+    unsigned long long mask_used;    // bytes of unit hit masks taken by the count pass
     unsigned int n_big;              // two-level order: Gaussians left to k_emit_big
     unsigned int big_ticket;
     unsigned int n_mid;              // two-level order: Gaussians left to k_emit_mid (one warp each)
@@ -318,7 +319,7 @@ struct PreprocessArgs {
     Rec *recs;
     unsigned long long *keys;
     unsigned *vals;
-    float4 *geo0, *geo1;             // per Gaussian: (u, v, a, b), (c, t, z bits, -)
+    float4 *geo0, *geo1;             // per Gaussian: (u, v, a, b), (c, t, z bits, mask offset bits)
     int4 *geo2;                      // per Gaussian: (tx0, ty0, w, h) of the candidate box, 0 if unpaired
     unsigned *chunk_hits;            // pairs per 256-Gaussian chunk
     unsigned long long *chunk_base;  // exclusive scan of chunk_hits
@@ -333,6 +334,11 @@ struct PreprocessArgs {
     unsigned long long *chunk_base2; // exclusive scan of chunk_hits2
     uint4 *big;                      // (record, request, output base lo, hi) of large Gaussians
     uint4 *mid;                      // the same for medium Gaussians
+    // The count pass keeps each candidate unit's hit mask (one byte per run of kSeg tiles, a
+    // Gaussian's units row-major from its offset in geo1.w; kNoMasks when the area was full) so
+    // that emission reads the decisions instead of repeating the tests.
+    unsigned char *masks;
+    long long mask_cap;              // bytes, < 2^32
     FrameCounters *ctr;
     long long pair_cap;
     long long n_chunks;

@@ -320,7 +320,11 @@ struct PreSmem {
     unsigned long long pbase[kPreBlock];   // depth order: first output position of each Gaussian
     unsigned run[kPreBlock];               // depth order: hits of each Gaussian written so far
     unsigned xr[kPreBlock];                // depth order: exclusive hit rank of each slot of a step
+    unsigned moff[kPreBlock];              // first hit-mask byte of each Gaussian (emission)
+    unsigned long long mbase;              // first hit-mask byte of the chunk (count pass)
 };
+
+constexpr unsigned kNoMasks = 0xffffffffu;   // geo1.w: the unit masks were not kept
 
 // Depth-ordered emission by footprint: Gaussians with more candidate tiles than kBigCand are
 // emitted by k_emit_big (a CTA each), those above kMidCand by k_emit_mid (a warp each), the rest
@@ -375,6 +379,13 @@ __device__ __forceinline__ unsigned unit_hits(const PreSmem &S, const BatchDesc 
     if (B.r[S.req[U.g]].opt.intersect == 1) return (1u << U.n) - 1u;    // 3DGS square: every tile
     const Cam &cam = B.r[S.req[U.g]].cam;
     return run_hits(cam.W, cam.H, S.u[U.g], S.v[U.g], S.a[U.g], S.b[U.g], S.c[U.g], S.t[U.g], U.tx, U.n, U.ty);
+}
+
+// Emission: the count pass's decision for a unit (its kept mask byte), else the test again.
+__device__ __forceinline__ unsigned kept_hits(const PreSmem &S, const PreprocessArgs &A, const Unit &U, int slot) {
+    const unsigned mo = S.moff[U.g];
+    return mo != kNoMasks ? (unsigned)A.masks[(unsigned long long)mo + (unsigned)(slot - S.cstart[U.g])]
+                          : unit_hits(S, A.B, U);
 }
 
 // Block exclusive scan of one unsigned per thread (uses S.wsum); returns the exclusive prefix and
@@ -458,12 +469,17 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
     S.w[tid] = w > 0 ? w : 1;
     S.cnt[tid] = 0;
     const int ctotal = block_scan_cand(S, valid ? units_of(w, h) : 0);
+    // one range of mask bytes per chunk (kept only while the area lasts)
+    if (tid == 0) S.mbase = ctotal > 0 ? atomicAdd(&A.ctr->mask_used, (unsigned long long)ctotal) : 0ull;
+    __syncthreads();
+    const bool keep = S.mbase + (unsigned long long)ctotal <= (unsigned long long)A.mask_cap;
 
     for (int base = 0; base < ctotal; base += kPreBlock) {
         const int slot = base + tid;
         if (slot < ctotal) {
             const Unit U = unit_of(S, slot);
             const unsigned m = unit_hits(S, A.B, U);
+            if (keep) A.masks[S.mbase + slot] = (unsigned char)m;
             if (m) atomicAdd(&S.cnt[U.g], (unsigned)__popc(m));
         }
     }
@@ -482,7 +498,8 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
     if (vis) {
         A.geo2[rec] = make_int4(G.tx0, G.ty0, w, h);
         A.geo0[rec] = make_float4(G.u, G.v, G.a, G.b);
-        A.geo1[rec] = make_float4(G.c, G.t, __uint_as_float(__float_as_uint(G.z)), 0.0f);
+        const unsigned moff = keep ? (unsigned)(S.mbase + (unsigned long long)S.cstart[tid]) : kNoMasks;
+        A.geo1[rec] = make_float4(G.c, G.t, __uint_as_float(__float_as_uint(G.z)), __uint_as_float(moff));
         const float4 po = __ldg(R.scene.pos_opa + gid);
         float rgb[3];
         sh_colour(R.scene, gid, cam, po.x, po.y, po.z, rgb);
@@ -636,6 +653,7 @@ __global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __g
             S.c[tid] = g1.x;
             S.t[tid] = g1.y;
             S.zb[tid] = __float_as_uint(g1.z);
+            S.moff[tid] = __float_as_uint(g1.w);
             S.tx0[tid] = g2.x;
             S.ty0[tid] = g2.y;
         }
@@ -675,7 +693,7 @@ __global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __g
             Unit U{-1, 0, 0, 0};
             if (slot < ctotal) {
                 U = unit_of(S, slot);
-                m = unit_hits(S, A.B, U);
+                m = kept_hits(S, A, U, slot);
             }
             unsigned step_tot;
             const unsigned xr = block_excl(S, (unsigned)__popc(m), &step_tot);   // exclusive hit rank in the step
@@ -716,7 +734,7 @@ __global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __g
         Unit U{0, 0, 0, 0};
         if (slot < ctotal) {
             U = unit_of(S, slot);
-            m = unit_hits(S, A.B, U);
+            m = kept_hits(S, A, U, slot);
         }
         unsigned step_tot;
         const unsigned xr = block_excl(S, (unsigned)__popc(m), &step_tot);
@@ -764,6 +782,7 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_mid(const __grid_constant__ 
         unsigned long long run = ((unsigned long long)it.w << 32) | it.z;
         const float4 g0 = A.geo0[rec], g1 = A.geo1[rec];
         const int4 g2 = A.geo2[rec];
+        const unsigned mo = __float_as_uint(g1.w);
         const int segs = (g2.z + kSeg - 1) / kSeg;
         const int nunits = segs * g2.w;
         for (int base = 0; base < nunits; base += 32) {
@@ -775,8 +794,9 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_mid(const __grid_constant__ 
                 tx = g2.x + seg * kSeg;
                 ty = g2.y + dy;
                 const int nrun = min(kSeg, g2.z - seg * kSeg);
-                m = R.opt.intersect == 1 ? (1u << nrun) - 1u
-                                         : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, nrun, ty);
+                m = mo != kNoMasks       ? (unsigned)A.masks[(unsigned long long)mo + (unsigned)k]
+                    : R.opt.intersect == 1 ? (1u << nrun) - 1u
+                                           : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, nrun, ty);
             }
             const unsigned c = (unsigned)__popc(m);
             unsigned incl = c;
@@ -825,6 +845,7 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
         unsigned long long run = ((unsigned long long)it.w << 32) | it.z;
         const float4 g0 = A.geo0[rec], g1 = A.geo1[rec];
         const int4 g2 = A.geo2[rec];
+        const unsigned mo = __float_as_uint(g1.w);
         const int segs = (g2.z + kSeg - 1) / kSeg;
         const int nunits = segs * g2.w;
         for (int base = 0; base < nunits; base += kPreBlock) {
@@ -836,8 +857,9 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
                 tx = g2.x + seg * kSeg;
                 ty = g2.y + dy;
                 const int nrun = min(kSeg, g2.z - seg * kSeg);
-                m = R.opt.intersect == 1 ? (1u << nrun) - 1u
-                                         : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, nrun, ty);
+                m = mo != kNoMasks       ? (unsigned)A.masks[(unsigned long long)mo + (unsigned)k]
+                    : R.opt.intersect == 1 ? (1u << nrun) - 1u
+                                           : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, nrun, ty);
             }
             // block exclusive scan of the hit counts
             const unsigned c = (unsigned)__popc(m);
