@@ -224,9 +224,9 @@ gs_status gs_frame_use_graph(gs_frame *frame, int32_t enable);
    keys and sorted over 32 + ceil(log2 tiles) bits; sort_mode 1 (two-level): the paired
    Gaussians are sorted once by depth (32-bit keys), pairs are emitted in that order with the
    tile id alone as a 32-bit key, and a stable sort over ceil(log2 tiles) bits finishes -- the
-   same (tile, depth, id) order with far fewer bytes moved.  sort_algo picks how each radix pass
-   is carried out (below).  Results are bit-identical across all choices.  GS_ERR_INVALID_ARG for
-   out-of-range values. */
+   same (tile, depth, id) order with far fewer bytes moved.  sort_algo picks how the radix passes
+   of the pair sort are carried out (below; the depth sort of sort_mode 1 always runs fused).
+   Results are bit-identical across all choices.  GS_ERR_INVALID_ARG for out-of-range values. */
 typedef struct {
     int32_t blend_variant;
     int32_t sort_mode;

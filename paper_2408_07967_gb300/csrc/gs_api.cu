@@ -778,7 +778,7 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     // count + scan + scatter per pass (reduce-then-scan) or one fused launch (two passes or more).
     const int algo = f->tuning.sort_algo;
     const int sort_k = algo == 1 ? 3 * f->passes : algo == 2 && f->passes >= 2 ? 1 : 2 + f->passes;
-    const int depth_k = algo == 1 ? 12 : algo == 2 ? 1 : 6;
+    const int depth_k = 1;   // the depth sort always runs fused
     out->kernels = f->mode_used == 1 ? 3 + 5 + depth_k + sort_k + 2 : 3 + sort_k + 2;
     return GS_OK;
 }

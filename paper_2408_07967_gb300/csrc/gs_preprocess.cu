@@ -516,20 +516,26 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
 // Exclusive scan of up to two arrays of chunk counts (one CTA; each thread sums a run of chunks).
 // Writes the totals to *tot_a / *tot_b.
 constexpr int kScanThreads = 1024;
-constexpr int kScanRun = 40;   // 40960 chunks per sweep: one sweep up to 10M Gaussians per batch
+// Exclusive scan (64-bit sums) of n per-chunk counts, four per thread and 4096 per step (16-byte
+// loads and stores, coalesced), with a block scan of the threads' sums and a running carry.
 __device__ void chunk_scan(const unsigned *in, unsigned long long *out, long long n, unsigned long long *total) {
     __shared__ unsigned long long s_w[kScanThreads / 32];
-    __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    for (long long base = 0; base < n; base += (long long)kScanThreads * kScanRun) {
-        // each thread sums a run of counts; the second sweep re-reads them from L1
-        const long long my0 = base + (long long)tid * kScanRun;
-        unsigned long long sum = 0;
-#pragma unroll 8
-        for (int r = 0; r < kScanRun; ++r)
-            if (my0 + r < n) sum += __ldg(in + my0 + r);
+    const long long n4 = (n + 3) / 4;
+    unsigned long long carry = 0;
+    for (long long c0 = 0; c0 < n4; c0 += kScanThreads) {
+        const long long i = c0 + tid, e = 4 * i;
+        const bool whole = e + 3 < n;
+        unsigned x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+        if (whole) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in) + i);
+            x0 = v.x, x1 = v.y, x2 = v.z, x3 = v.w;
+        } else if (e < n) {
+            x0 = __ldg(in + e);
+            if (e + 1 < n) x1 = __ldg(in + e + 1);
+            if (e + 2 < n) x2 = __ldg(in + e + 2);
+        }
+        const unsigned long long sum = (unsigned long long)x0 + x1 + x2 + x3;
         unsigned long long incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -539,25 +545,27 @@ __device__ void chunk_scan(const unsigned *in, unsigned long long *out, long lon
         if (lane == 31) s_w[warp] = incl;
         __syncthreads();
         unsigned long long wex = 0, tot = 0;
+#pragma unroll
         for (int w2 = 0; w2 < kScanThreads / 32; ++w2) {
-            const unsigned long long x = s_w[w2];
-            wex += w2 < warp ? x : 0ull;
-            tot += x;
+            const unsigned long long y = s_w[w2];
+            wex += w2 < warp ? y : 0ull;
+            tot += y;
         }
-        unsigned long long run = s_carry + wex + incl - sum;
-        if (out) {
-#pragma unroll 8
-            for (int r = 0; r < kScanRun; ++r)
-                if (my0 + r < n) {
-                    out[my0 + r] = run;
-                    run += __ldg(in + my0 + r);
-                }
+        if (out && e < n) {
+            const unsigned long long o0 = carry + wex + incl - sum, o1 = o0 + x0, o2 = o1 + x1, o3 = o2 + x2;
+            if (whole) {
+                reinterpret_cast<ulonglong2 *>(out)[2 * i] = make_ulonglong2(o0, o1);
+                reinterpret_cast<ulonglong2 *>(out)[2 * i + 1] = make_ulonglong2(o2, o3);
+            } else {
+                out[e] = o0;
+                if (e + 1 < n) out[e + 1] = o1;
+                if (e + 2 < n) out[e + 2] = o2;
+            }
         }
-        __syncthreads();
-        if (tid == 0) s_carry += tot;
+        carry += tot;
         __syncthreads();
     }
-    if (tid == 0) *total = s_carry;
+    if (tid == 0) *total = carry;
     __syncthreads();
 }
 
@@ -915,7 +923,11 @@ int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cud
                                             &a.ctr->n_vis64, a.n_chunks, a.pair_cap, &a.ctr->status);
     k_vis_compact<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
     // depth sort of the paired Gaussians: 32-bit float bits of z (positive, so bit order = value order)
-    const int dp = launch_sort32(a.dkey, a.dval, a.dkey_tmp, a.dval_tmp, &a.ctr->n_vis64, a.B.total_recs, 32, scr,
+    // (always the fused onesweep: a few hundred thousand to a few million keys, where its single
+    // launch beats the per-pass forms; the frame's sort_algo applies to the pair sort)
+    SortScratch dscr = scr;
+    dscr.algo = 2;
+    const int dp = launch_sort32(a.dkey, a.dval, a.dkey_tmp, a.dval_tmp, &a.ctr->n_vis64, a.B.total_recs, 32, dscr,
                                  a.ctr, s);
     (void)dp;   // four passes: the result is back in dkey / dval
     // depth ranks run over all records of the batch: size the rank chunks by total_recs
