@@ -674,39 +674,61 @@ static int fused_grid() {
 // k_rts_scatter ranks each tile exactly as the onesweep CTA does and writes it at those offsets.
 // It reads the keys twice per pass, but no tile ever waits on a predecessor, so large sorts run at
 // the memory system's pace instead of the look-back's.
+// Per-tile digit counts, kCountGroup consecutive tiles per CTA step: each tile's keys are loaded
+// while the previous tile is counted (plain shared-memory atomics), and thread d writes digit d's
+// counts of the group as two 16-byte stores (rows of rts_stride entries, a multiple of
+// kCountGroup, so a group never leaves its row).
+constexpr int kCountGroup = 8;
 template <class K>
 __global__ void __launch_bounds__(kSortThreads) k_rts_count(const K *__restrict__ kin, const unsigned long long *n_dev,
                                                             long long n_host, long long cap, int pass,
                                                             unsigned *counts, long long stride) {
-    __shared__ unsigned s_h[256];
+    __shared__ unsigned s_h[kCountGroup][256];
     const int tid = threadIdx.x;
     const int shift = 8 * pass;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        s_h[tid] = 0;
-        __syncthreads();
-        const long long base = tile * kSortTile;
-        unsigned dg[kSortItems];
+    const long long ngroups = (ntiles + kCountGroup - 1) / kCountGroup;
+    auto load = [&](K (&k)[kSortItems], long long tile) {
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {        // all loads in flight before any ranking
-            const long long idx = base + i * kSortThreads + tid;
-            dg[i] = idx < n ? (unsigned)(__ldg(kin + idx) >> shift) & 0xffu : 256u;
+        for (int i = 0; i < kSortItems; ++i) {
+            const long long idx = tile * kSortTile + i * kSortThreads + tid;
+            k[i] = idx < n ? __ldg(kin + idx) : (K)0;
         }
+    };
+    for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i)
-            if (dg[i] < 256u) atomicAdd(&s_h[dg[i]], 1u);
+        for (int j = 0; j < kCountGroup; ++j) s_h[j][tid] = 0;
         __syncthreads();
-        counts[(long long)tid * stride + tile] = s_h[tid];
+        const long long t0 = g * kCountGroup;
+        K nxt[kSortItems];
+        load(nxt, t0);
+#pragma unroll 1
+        for (int j = 0; j < kCountGroup; ++j) {
+            K cur[kSortItems];
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) cur[i] = nxt[i];
+            if (j + 1 < kCountGroup) load(nxt, t0 + j + 1);
+            const long long base = (t0 + j) * kSortTile;
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i)
+                if (base + i * kSortThreads + tid < n) atomicAdd(&s_h[j][(unsigned)(cur[i] >> shift) & 0xffu], 1u);
+        }
+        __syncthreads();
+        uint4 *dst = reinterpret_cast<uint4 *>(counts + (long long)tid * stride + t0);
+        dst[0] = make_uint4(s_h[0][tid], s_h[1][tid], s_h[2][tid], s_h[3][tid]);
+        dst[1] = make_uint4(s_h[4][tid], s_h[5][tid], s_h[6][tid], s_h[7][tid]);
         __syncthreads();
     }
 }
+static_assert(kCountGroup == 8, "two 16-byte stores per digit and group");
 
 // One CTA per digit: counts[d][t] becomes the sum of counts[d][t'] over t' < t, and the row's total
 // goes to tot[d] (the scatter turns the 256 totals into the digits' global offsets).
 constexpr int kRtsScanThreads = 1024;
-// Row stride of the per-tile digit counts: a multiple of 4, so that every row is 16-byte aligned.
-long long rts_stride(long long max_tiles) { return (max_tiles + 3) & ~3ll; }
+// Row stride of the per-tile digit counts: a multiple of kCountGroup (8), so that every row is
+// 32-byte aligned and a count group never leaves its row.
+long long rts_stride(long long max_tiles) { return (max_tiles + 7) & ~7ll; }
 
 // One CTA per digit: counts[d][t] becomes the sum of counts[d][t'] over t' < t, and the row's total
 // goes to tot[d] (the scatter turns the 256 totals into the digits' global offsets).  The row is
@@ -847,7 +869,7 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
     // bulk copy 16-byte aligned
     const int bulk_ok = (((uintptr_t)keys | (uintptr_t)vals | (uintptr_t)keys_tmp | (uintptr_t)vals_tmp) & 15u) == 0;
     if (scr.algo == 1 && scr.counts && max_tiles <= scr.max_tiles) {
-        const int cgrid = (int)min((long long)sms * 8, max_tiles > 0 ? max_tiles : 1);
+        const int cgrid = (int)min((long long)sms * 8, max(1ll, (max_tiles + kCountGroup - 1) / kCountGroup));
         const int rgrid = (int)min((long long)rts_scatter_grid<K>(), max_tiles > 0 ? max_tiles : 1);
         K *ka = keys, *kb = keys_tmp;
         unsigned *va = vals, *vb = vals_tmp;
