@@ -28,10 +28,13 @@ if ROOT not in sys.path:
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
-# FP32-pipe operations of one contributing (pixel, entry) evaluation: q from the pixel offset
-# (2 sub, 3 mul, 2 fma), the q <= t test, the exponent fma and the alpha clamp, T' (1 fma),
-# the stop test, w = alpha T and three colour fmas; plus one MUFU ex2.  Entries that cannot
-# reach alpha >= tau at a pixel are work a culler may avoid, so they are not counted.
+# Algorithmic work of the blend: every (pixel, list entry) the method evaluates before the pixel
+# stops, E (the oracle's count, pinned against the device counter in the tests), at 14 FP32-pipe
+# operations (pixel offset, q, the alpha >= tau test, exponent and clamp, T', the stop test, three
+# colour fmas) and one MUFU ex2 each; the bound is the slower of the two pipes.
+BLEND_OPS_PER_EVAL = 14
+# Stricter secondary figure: only the contributing evaluations, at the 15 FP32-pipe operations a
+# contributing one costs (entries below tau are work a culler may avoid).
 BLEND_OPS_PER_CONTRIB = 15
 
 
@@ -486,7 +489,12 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
         sort_bytes = 8 * N + passes * 24 * N
     ntiles = ((W + 15) // 16) * ((H + 15) // 16)
     ranges_bytes = (ntiles + 1) * (4 + 8 * max(1, math.ceil(math.log2(max(N, 2)))))
-    blend_ops = Ec * BLEND_OPS_PER_CONTRIB
+    blend_ops = E * BLEND_OPS_PER_EVAL
+    ex2_peak = (alu or {}).get("ex2_tops")
+    if ex2_peak:
+        ex2_peak = ex2_peak * (sm_mhz / ((alu or {}).get("sm_mhz") or sm_mhz))
+    # the MUFU pipe bounds instead when E ex2 take longer than 14 E FP32 operations
+    mufu_bound = bool(ex2_peak) and E / ex2_peak > blend_ops / alu_peak
     per_stage = {
         "preprocess": {"ms": stage_ms[0], "bound": "hbm", "achieved": pre_bytes / (stage_ms[0] * 1e-3) / 1e9,
                        "peak": hbm_peak, "unit": "GB/s"},
@@ -494,27 +502,38 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
                  "peak": hbm_peak, "unit": "GB/s"},
         "ranges": {"ms": stage_ms[2], "bound": "hbm", "achieved": ranges_bytes / (stage_ms[2] * 1e-3) / 1e9,
                    "peak": hbm_peak, "unit": "GB/s"},
-        "blend": {"ms": stage_ms[3], "bound": "alu", "achieved": blend_ops / (stage_ms[3] * 1e-3) / 1e12,
-                  "peak": alu_peak, "unit": "TOP/s"},
+        "blend": ({"ms": stage_ms[3], "bound": "alu", "achieved": E / (stage_ms[3] * 1e-3) / 1e12,
+                   "peak": ex2_peak, "unit": "T ex2/s"} if mufu_bound else
+                  {"ms": stage_ms[3], "bound": "alu", "achieved": blend_ops / (stage_ms[3] * 1e-3) / 1e12,
+                   "peak": alu_peak, "unit": "TOP/s"}),
     }
     for v in per_stage.values():
         v["frac"] = v["achieved"] / v["peak"]
         for k in ("ms", "achieved", "frac"):
             v[k] = round(v[k], 4)
+    per_stage["blend"]["frac_contributing"] = round(
+        Ec * BLEND_OPS_PER_CONTRIB / (stage_ms[3] * 1e-3) / 1e12 / alu_peak, 4)
     dom = max(per_stage, key=lambda k: per_stage[k]["ms"])
     d = per_stage[dom]
-    kernel = {"preprocess": "k_pre_count + k_pre_emit", "sort": "k_sort_scatter (all passes)",
-              "ranges": "k_tile_starts", "blend": f"k_blend<variant {tuning.get('blend_variant')}>"}[dom]
+    sort_kernels = {0: "k_sort_hist + k_sort_offsets + k_sort_scatter per pass",
+                    1: "k_rts_count + k_rts_scan + k_rts_scatter per pass",
+                    2: "k_sort_fused (one cooperative launch)"}.get(tuning.get("sort_algo"), "sort kernels")
+    kernel = {"preprocess": "k_pre_count + k_pre_emit (+ depth order: k_sort_fused, k_emit_mid, k_emit_big)",
+              "sort": sort_kernels, "ranges": "k_tile_starts",
+              "blend": f"k_blend<variant {tuning.get('blend_variant')}>"}[dom]
     algo = {"preprocess": "16P + 32 P_culled_in + 240 V + 12 N bytes",
             "sort": "8N + 24N per pass (64-bit keys) / 4N + 16N per pass + 68V (two-level)",
             "ranges": "(tiles + 1) x (4 + 8 log2 N) bytes",
-            "blend": f"{BLEND_OPS_PER_CONTRIB} FP32 ops x contributing evaluations (E_c = {Ec:.4g} of "
-                     f"E = {E:.4g} walked per frame)"}[dom]
+            "blend": f"{BLEND_OPS_PER_EVAL} FP32 ops (+1 ex2) x evaluations, E = {E:.4g} (pixel, entry) pairs "
+                     f"evaluated per frame before early stop, as the oracle counts them; of these E_c = {Ec:.4g} "
+                     f"contribute (frac_contributing: {BLEND_OPS_PER_CONTRIB} ops x E_c)"}[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": traffic_for(config, dom, tuning) if config else None, "kernel": kernel,
                 "stage": dom,
                 "peak_source": ("measured HBM copy (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else alu_src),
                 "algorithmic": algo}
+    if "frac_contributing" in d:
+        roofline["frac_contributing"] = d["frac_contributing"]
     res = {"frames": K, "ms_total": tot_ms, "frames_per_s": K / (tot_ms / 1000.0), "ms_per_frame": tot_ms / K,
            "ms_median": med_ms, "frames_per_s_median": 1000.0 / med_ms,
            "wall_s": wall, "clocks": clocks, "gpu_launches": kernels, "tuning": tuning, "roofline": roofline,
