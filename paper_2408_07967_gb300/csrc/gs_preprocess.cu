@@ -619,8 +619,9 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_sum(const __grid_constant__ 
 }
 
 // Emission: the same load-balanced units, their decisions read from the count pass's masks; every
-// hit is written at the chunk's base + its rank in slot order.  DEPTH = false: chunk c holds Gaussians 256c .. 256c+255 and the pairs land in
-// (Gaussian id, tile row-major) order with 64-bit (tile, depth) keys.  DEPTH = true: chunk c holds
+// hit is written at the chunk's base + its rank in slot order.  DEPTH = false: chunk c holds
+// Gaussians 256c .. 256c+255 and the pairs land in (Gaussian id, tile row-major) order with
+// 64-bit (tile, depth) keys.  DEPTH = true: chunk c holds
 // the depth-sorted Gaussians of ranks 256c .. 256c+255 and the pairs land in (depth, id, tile)
 // order with the tile id alone as a 32-bit key -- a stable sort by tile then yields exactly the
 // (tile, depth, id) order of the 64-bit keys.
