@@ -488,7 +488,8 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
     else:
         sort_bytes = 8 * N + passes * 24 * N
     ntiles = ((W + 15) // 16) * ((H + 15) // 16)
-    ranges_bytes = (ntiles + 1) * (4 + 8 * max(1, math.ceil(math.log2(max(N, 2)))))
+    # one read of the sorted keys and the (start, end) words of every tile
+    ranges_bytes = (4 if tuning.get("sort_mode", 0) == 1 else 8) * N + 8 * ntiles
     blend_ops = E * BLEND_OPS_PER_EVAL
     ex2_peak = (alu or {}).get("ex2_tops")
     if ex2_peak:
@@ -523,7 +524,7 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
               "blend": f"k_blend<variant {tuning.get('blend_variant')}>"}[dom]
     algo = {"preprocess": "16P + 32 P_culled_in + 240 V + 12 N bytes",
             "sort": "8N + 24N per pass (64-bit keys) / 4N + 16N per pass + 68V (two-level)",
-            "ranges": "(tiles + 1) x (4 + 8 log2 N) bytes",
+            "ranges": "8N (4N for 32-bit keys) + 8 x tiles bytes",
             "blend": f"{BLEND_OPS_PER_EVAL} FP32 ops (+1 ex2) x evaluations, E = {E:.4g} (pixel, entry) pairs "
                      f"evaluated per frame before early stop, as the oracle counts them; of these E_c = {Ec:.4g} "
                      f"contribute (frac_contributing: {BLEND_OPS_PER_CONTRIB} ops x E_c)"}[dom]

@@ -940,36 +940,58 @@ int launch_sort32(unsigned *keys, unsigned *vals, unsigned *keys_tmp, unsigned *
 
 // ------------------------------------------------------------------------------------------ ranges
 // Key layouts: (tile << 32 | depth bits) as u64 (shift 32), or the tile id alone as u32 (shift 0).
+// With at least one and at most kScanPairsPerTile pairs per tile on average, one pass over the
+// sorted keys: position i compares the tiles of keys i-1 and i and writes i as the start of every
+// tile in between (each start is written once; position n closes the last tiles).  Otherwise a
+// binary search per tile.  Grid-stride loops: the grid does not depend on the pair count.
+constexpr long long kScanPairsPerTile = 512;
 template <class K, int SHIFT>
-__global__ void k_tile_starts(const K *keys, const unsigned long long *n_dev, long long cap, int ntiles,
-                              unsigned *starts) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b > ntiles) return;
+__global__ void __launch_bounds__(256) k_tile_starts(const K *keys, const unsigned long long *n_dev, long long cap,
+                                                     int ntiles, unsigned *starts) {
     const long long n = pair_count(n_dev, 0, cap);
-    const K target = (K)b << SHIFT;
-    long long lo = 0, hi = n;
-    while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        if (keys[mid] < target)
-            lo = mid + 1;
-        else
-            hi = mid;
+    const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (n >= ntiles && n <= kScanPairsPerTile * ntiles) {
+        for (long long i = g0; i <= n; i += stride) {
+            const long long prev = i == 0 ? -1 : (long long)(keys[i - 1] >> SHIFT);
+            const long long cur = i == n ? (long long)ntiles : (long long)(keys[i] >> SHIFT);
+            for (long long t = prev + 1; t <= cur; ++t) starts[t] = (unsigned)i;
+        }
+        return;
     }
-    starts[b] = (unsigned)lo;
+    for (long long b = g0; b <= ntiles; b += stride) {
+        const K target = (K)b << SHIFT;
+        long long lo = 0, hi = n;
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (keys[mid] < target)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        starts[b] = (unsigned)lo;
+    }
+}
+
+static int ranges_grid() {
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = 8 * sms;
+    }
+    return grid;
 }
 
 void launch_ranges(const unsigned long long *keys, const unsigned long long *n_dev, long long cap, int ntiles,
                    unsigned *starts, cudaStream_t s) {
-    const int threads = 256;
-    const int blocks = (ntiles + 1 + threads - 1) / threads;
-    k_tile_starts<unsigned long long, 32><<<blocks, threads, 0, s>>>(keys, n_dev, cap, ntiles, starts);
+    k_tile_starts<unsigned long long, 32><<<ranges_grid(), 256, 0, s>>>(keys, n_dev, cap, ntiles, starts);
 }
 
 void launch_ranges32(const unsigned *keys, const unsigned long long *n_dev, long long cap, int ntiles,
                      unsigned *starts, cudaStream_t s) {
-    const int threads = 256;
-    const int blocks = (ntiles + 1 + threads - 1) / threads;
-    k_tile_starts<unsigned, 0><<<blocks, threads, 0, s>>>(keys, n_dev, cap, ntiles, starts);
+    k_tile_starts<unsigned, 0><<<ranges_grid(), 256, 0, s>>>(keys, n_dev, cap, ntiles, starts);
 }
 
 }  // namespace gs

@@ -206,29 +206,34 @@ def test_3dgs_square_pairs(ctx, sort_mode, cap):
         assert np.array_equal(ex["rgb"], res["rgb"]) and np.array_equal(ex["T"], res["T"])
 
 
-def test_empty_view(ctx):
+@pytest.mark.parametrize("sort_algo", [0, 1, 2])
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_empty_view(ctx, sort_mode, sort_algo):
     scene, cam = synth.random_small_scene(1000, 14, 64, 48)
     cam.R = (-np.eye(3)).astype(np.float32)        # looking the other way
     cam.R[1, 1] = 1.0
     ref = oracle.Frame(scene, cam, oracle.opts(bg=(0.2, 0.3, 0.4)), mode=64)
     assert ref.N == 0
-    res = run_gpu(ctx, scene, cam, dict(bg=(0.2, 0.3, 0.4)))
+    res = run_gpu(ctx, scene, cam, dict(bg=(0.2, 0.3, 0.4)), sort_mode=sort_mode, sort_algo=sort_algo)
     check(res, ref)
     assert np.allclose(res["rgb"][0], np.float32(0.2)) and np.all(res["T"] == 1.0)
 
 
-def test_single_gaussian_and_tiny_scene_sizes(ctx):
+@pytest.mark.parametrize("sort_algo", [0, 1, 2])
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_single_gaussian_and_tiny_scene_sizes(ctx, sort_mode, sort_algo):
     for P in (1, 255, 257):
         scene, cam = synth.random_small_scene(P, 15 + P, 64, 64, log_scale_mu=-2.0)
         ref = oracle.Frame(scene, cam, mode=64)
-        check(run_gpu(ctx, scene, cam), ref)
+        check(run_gpu(ctx, scene, cam, sort_mode=sort_mode, sort_algo=sort_algo), ref)
 
 
+@pytest.mark.parametrize("sort_algo", [0, 2])
 @pytest.mark.parametrize("sort_mode", [0, 1])
-def test_pair_overflow_is_reported(ctx, sort_mode):
+def test_pair_overflow_is_reported(ctx, sort_mode, sort_algo):
     scene, cam = synth.random_small_scene(2000, 16, 128, 96, log_scale_mu=-2.4)
     ref = oracle.Frame(scene, cam, mode=32)
-    res = run_gpu(ctx, scene, cam, max_pairs=ref.N // 3, sort_mode=sort_mode)
+    res = run_gpu(ctx, scene, cam, max_pairs=ref.N // 3, sort_mode=sort_mode, sort_algo=sort_algo)
     assert res["stats"]["status"] == -3, res["stats"]
     assert res["stats"]["pairs"] == ref.N
     # the frame stays usable
