@@ -1,21 +1,28 @@
-// gs_sort.cu -- device-wide LSD radix sort of (key, u32 value) pairs in the onesweep form, and
-// the per-tile range search.
+// gs_sort.cu -- device-wide stable LSD radix sort of (key, u32 value) pairs, 8-bit digits, and
+// the per-tile ranges of the sorted pairs.
 //
-// Sort (the stage FlashGS inherits from 3DGS's CUB SortPairs, Section 2.2): one pass over the
-// keys builds the 256-bin histograms of every 8-bit digit at once; a tiny kernel turns them into
-// exclusive digit offsets; then one scatter pass per digit.  A scatter CTA takes tiles of 3072
-// pairs in ticket order, ranks them by digit with warp match/ballots (stable: warp-striped load
-// order equals input order), publishes its per-digit counts, places the tile in (digit, rank)
-// order in shared memory, and reads its predecessors' counts through a decoupled look-back over
-// epoch-tagged descriptors (no per-sort clearing; waits bounded by kSpinLimit); then it writes runs
-// of consecutive addresses.  The look-back has two levels: a tile sums its own block of 16 tiles,
-// then whole-block descriptors that the last tile of each block publishes, 16 per round trip, so
-// the last of T tiles that all start together waits about 2 + T/256 round trips instead of T/16.
+// Sort (the stage FlashGS inherits from 3DGS's CUB SortPairs, Section 2.2).  Three forms share
+// one tile body (sort_tile): a CTA loads a tile of 3072 pairs (up to 3584 in the fused form),
+// ranks it by digit within each warp (stable: warp-striped load order equals input order; the
+// lanes sharing a digit come from a hardware match when the warp's digits form few runs, else
+// from shared-memory OR masks), places it in (digit, rank) order in shared memory, learns where
+// each digit's run goes, and writes runs of consecutive addresses.
+//   * Onesweep (decoupled look-back): the histograms of every digit come from one read of the
+//     keys; a tile publishes its per-digit counts in epoch-tagged descriptors (no per-sort
+//     clearing) and sums its predecessors' through a two-level look-back -- its own block of 16
+//     tiles, then whole-block descriptors that the last tile of each block publishes -- so the
+//     last of T tiles that start together waits about 2 + T/256 round trips instead of T/16.
+//     Either one kernel per pass with tiles taken in ticket order (k_sort_hist, k_sort_offsets,
+//     k_sort_scatter), or the whole sort in one cooperative launch (k_sort_fused): histograms,
+//     a grid barrier, then the passes separated by grid barriers, tiles dealt statically.
+//   * Reduce-then-scan (k_rts_count, k_rts_scan, k_rts_scatter): per pass, per-tile digit counts,
+//     a scan across tiles, then the scatter at the scanned positions; no tile waits on another.
 // For 32-bit keys the next tile's keys and values arrive by bulk copy (cp.async.bulk on an
-// mbarrier) while the current tile is written out.
+// mbarrier) while the current tile is written out.  Every wait is bounded by kSpinLimit polls
+// and reports a timeout in the frame's status word.
 //
-// Ranges: the first position of every tile id in the sorted keys by binary search; tile t
-// spans [start[t], start[t+1]).
+// Ranges: the first position of every tile id in the sorted keys, by one pass over the keys or a
+// binary search per tile; tile t spans [start[t], start[t+1]).
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -900,10 +907,14 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, k_sort_fused<K>, keys, vals, keys_tmp, vals_tmp, n_dev, n_host, cap, passes, scr.hist,
-                           scr.desc, scr.desc + scr.max_tiles * 256, ctr,
-                           (unsigned *)((char *)ctr + offsetof(FrameCounters, sort_bar)), bulk_ok);
-        return passes;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_sort_fused<K>, keys, vals, keys_tmp, vals_tmp, n_dev, n_host,
+                                                 cap, passes, scr.hist, scr.desc, scr.desc + scr.max_tiles * 256, ctr,
+                                                 (unsigned *)((char *)ctr + offsetof(FrameCounters, sort_bar)),
+                                                 bulk_ok);
+        if (e == cudaSuccess) return passes;
+        // a cooperative launch refused (e.g. by a device or mode that does not allow it): the
+        // error is not sticky, so clear it and run the per-pass form below instead
+        cudaGetLastError();
     }
     k_sort_hist<K><<<sms * 2, 512, 0, s>>>(keys, n_dev, n_host, cap, passes, scr.hist);
     k_sort_offsets<<<passes, 256, 0, s>>>(scr.hist, scr.offs, ctr);
