@@ -120,6 +120,7 @@ struct gs_frame {
     unsigned long long *keys[2] = {nullptr, nullptr};
     unsigned *vals[2] = {nullptr, nullptr};
     unsigned *starts = nullptr;
+    unsigned *torder = nullptr;      // blend order of the tiles
     unsigned long long *chunk_base = nullptr, *vis_base = nullptr, *chunk_base2 = nullptr;
     unsigned *chunk_hits = nullptr, *chunk_vis = nullptr, *chunk_hits2 = nullptr, *counts = nullptr;
     unsigned *dkey[2] = {nullptr, nullptr}, *dval[2] = {nullptr, nullptr};
@@ -305,6 +306,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     size_t o_k0 = cv.take<unsigned long long>(max_pairs), o_k1 = cv.take<unsigned long long>(max_pairs);
     size_t o_v0 = cv.take<unsigned>(max_pairs), o_v1 = cv.take<unsigned>(max_pairs);
     size_t o_starts = cv.take<unsigned>(tiles + 1);
+    size_t o_torder = cv.take<unsigned>(tiles);
     size_t o_cbase = cv.take<unsigned long long>(f->max_chunks);
     size_t o_chits = cv.take<unsigned>(f->max_chunks);
     size_t o_vbase = cv.take<unsigned long long>(f->max_chunks), o_cbase2 = cv.take<unsigned long long>(f->max_chunks);
@@ -335,6 +337,7 @@ gs_status gs_frame_create(gs_context *ctx, int64_t max_g, int64_t max_pairs, int
     f->vals[0] = (unsigned *)(b + o_v0);
     f->vals[1] = (unsigned *)(b + o_v1);
     f->starts = (unsigned *)(b + o_starts);
+    f->torder = (unsigned *)(b + o_torder);
     f->chunk_base = (unsigned long long *)(b + o_cbase);
     f->chunk_hits = (unsigned *)(b + o_chits);
     f->vis_base = (unsigned long long *)(b + o_vbase);
@@ -645,6 +648,7 @@ gs_status gs_ranges(gs_frame *f, gs_stream stream) {
     else
         launch_ranges(f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs, f->batch.total_tiles, f->starts,
                       (cudaStream_t)stream);
+    launch_tile_order(f->starts, f->batch.total_tiles, f->torder, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -663,6 +667,7 @@ static gs_status blend_batch(gs_frame *f, float *const *rgb, float *const *T, ui
     a.recs = f->recs;
     a.vals = f->vals[f->sorted_buf];
     a.starts = f->starts;
+    a.order = f->torder;
     a.n_dev = &f->ctr->n_pairs;
     a.cap = f->max_pairs;
     a.evals = f->ctr->evals;
@@ -779,7 +784,7 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     const int algo = f->tuning.sort_algo;
     const int sort_k = algo == 1 ? 3 * f->passes : algo == 2 && f->passes >= 2 ? 1 : 2 + f->passes;
     const int depth_k = 1;   // the depth sort always runs fused
-    out->kernels = f->mode_used == 1 ? 3 + 5 + depth_k + sort_k + 2 : 3 + sort_k + 2;
+    out->kernels = f->mode_used == 1 ? 3 + 5 + depth_k + sort_k + 3 : 3 + sort_k + 3;   // ranges: starts + order
     return GS_OK;
 }
 

@@ -383,12 +383,15 @@ int launch_sort32(unsigned *keys, unsigned *vals, unsigned *keys_tmp, unsigned *
                   FrameCounters *ctr, cudaStream_t s);
 void launch_ranges32(const unsigned *keys, const unsigned long long *n_dev, long long cap, int ntiles,
                      unsigned *starts, cudaStream_t s);
+// Blend order of the tiles: decreasing list length class (see gs_render.cu).
+void launch_tile_order(const unsigned *starts, int ntiles, unsigned *order, cudaStream_t s);
 
 struct BlendArgs {
     BatchDesc B;
     const Rec *recs;
     const unsigned *vals;
     const unsigned *starts;
+    const unsigned *order;           // [total_tiles]: tile of each CTA (nullable: CTA i takes tile i)
     const unsigned long long *n_dev;
     long long cap;
     unsigned long long *evals;       // [2]: entries walked, entries passing q <= t (count mode)
