@@ -53,6 +53,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Carves aligned slices out of one device allocation.
 constexpr size_t kHistBytes = 8 * 256 * sizeof(unsigned);   // the sort's [8][256] digit histograms
+// The blend takes its tiles longest list first up to this many tiles (a 1080p frame has 8160);
+// beyond, each SM works through so many tiles that the last ones no longer set the makespan,
+// and the one-CTA ordering kernel would cost more than it saves (4K: 32400 tiles).
+constexpr int kOrderMaxTiles = 16384;
 
 struct Carver {
     size_t off = 0;
@@ -648,7 +652,8 @@ gs_status gs_ranges(gs_frame *f, gs_stream stream) {
     else
         launch_ranges(f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs, f->batch.total_tiles, f->starts,
                       (cudaStream_t)stream);
-    launch_tile_order(f->starts, f->batch.total_tiles, f->torder, (cudaStream_t)stream);
+    if (f->batch.total_tiles <= kOrderMaxTiles)
+        launch_tile_order(f->starts, f->batch.total_tiles, f->torder, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
@@ -667,7 +672,7 @@ static gs_status blend_batch(gs_frame *f, float *const *rgb, float *const *T, ui
     a.recs = f->recs;
     a.vals = f->vals[f->sorted_buf];
     a.starts = f->starts;
-    a.order = f->torder;
+    a.order = f->batch.total_tiles <= kOrderMaxTiles ? f->torder : nullptr;
     a.n_dev = &f->ctr->n_pairs;
     a.cap = f->max_pairs;
     a.evals = f->ctr->evals;
@@ -784,7 +789,8 @@ gs_status gs_frame_get_stats(gs_frame *f, gs_frame_stats *out, gs_stream stream)
     const int algo = f->tuning.sort_algo;
     const int sort_k = algo == 1 ? 3 * f->passes : algo == 2 && f->passes >= 2 ? 1 : 2 + f->passes;
     const int depth_k = 1;   // the depth sort always runs fused
-    out->kernels = f->mode_used == 1 ? 3 + 5 + depth_k + sort_k + 3 : 3 + sort_k + 3;   // ranges: starts + order
+    const int ranges_k = f->batch.total_tiles <= kOrderMaxTiles ? 2 : 1;   // starts (+ blend order)
+    out->kernels = f->mode_used == 1 ? 3 + 5 + depth_k + sort_k + ranges_k + 1 : 3 + sort_k + ranges_k + 1;
     return GS_OK;
 }
 
