@@ -366,7 +366,6 @@ struct SortScratch {
                                      // 2 onesweep passes fused into one cooperative launch
 };
 
-int sort_tile_items();
 long long sort_max_tiles_for(long long n);
 long long sort_desc_words(long long max_tiles);
 long long rts_stride(long long max_tiles);

@@ -45,7 +45,6 @@ constexpr int kLookWindow = 16;        // descriptors per look-back round trip
 constexpr int kLookBlock = 16;         // tiles per block descriptor
 constexpr unsigned kMatchRuns = 12;    // warps with at most this many digit runs rank by match
 
-int sort_tile_items() { return kSortTile; }
 long long sort_max_tiles_for(long long n) { return (n + kSortTile - 1) / kSortTile; }
 long long sort_desc_words(long long max_tiles) {
     return (max_tiles + (max_tiles + kLookBlock - 1) / kLookBlock) * 256;
@@ -54,19 +53,6 @@ long long sort_desc_words(long long max_tiles) {
 __device__ __forceinline__ long long pair_count(const unsigned long long *n_dev, long long n_host, long long cap) {
     long long n = n_dev ? (long long)*(const volatile unsigned long long *)n_dev : n_host;
     return n < cap ? n : cap;
-}
-
-// Lanes of the warp holding the same 8-bit digit, from eight ballots (one per digit bit): plain
-// ALU work at full rate, where a hardware match over 32-bit values is a long-latency operation.
-__device__ __forceinline__ unsigned match_digit(unsigned d) {
-    unsigned m = 0xffffffffu;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const unsigned bit = (d >> b) & 1u;
-        const unsigned bal = __ballot_sync(0xffffffffu, bit);
-        m &= bit ? bal : ~bal;
-    }
-    return m;
 }
 
 // ------------------------------------------------------------------------------------------ histogram
