@@ -73,6 +73,12 @@ typedef struct {
     int64_t P;
     int32_t sh_degree;     /* 0..3 */
     int32_t activated;     /* 1: scales/opacities as given; 0: exp / sigmoid applied on device */
+    int32_t sh_half;       /* 1: opt-in reduced precision -- the scene keeps the SH coefficients as
+                              IEEE binary16 (round to nearest even), 96 instead of 192 bytes per
+                              Gaussian; colours then follow the rounded coefficients (the paper
+                              quantises nothing; pairs and keys do not depend on SH).  0: binary32.
+                              Fixed at gs_scene_create: gs_scene_update must pass the same value. */
+    int32_t reserved;      /* 0 */
 } gs_gaussians;
 
 typedef struct {

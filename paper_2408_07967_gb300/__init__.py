@@ -107,39 +107,43 @@ class Context:
 
 
 class Scene:
-    """gs_scene: device-resident Gaussians (position plane, scale/rotation plane, SH blocks)."""
+    """gs_scene: device-resident Gaussians (position plane, scale/rotation plane, SH blocks).
+    sh_half=True keeps the SH coefficients as binary16 (opt-in reduced precision)."""
 
-    def __init__(self, ctx: Context, means, scales, quats, opacity, sh, sh_degree=3, activated=True, stream=None):
+    def __init__(self, ctx: Context, means, scales, quats, opacity, sh, sh_degree=3, activated=True, stream=None,
+                 sh_half=False):
         self.ctx = ctx
-        g = self._struct(means, scales, quats, opacity, sh, sh_degree, activated)
+        self.sh_half = bool(sh_half)
+        g = self._struct(means, scales, quats, opacity, sh, sh_degree, activated, self.sh_half)
         h = C.c_void_p()
         _check(lib().gs_scene_create(ctx.h, C.byref(g), _stream(stream), C.byref(h)))
         self.h = h
         self.P = int(g.P)
 
     @staticmethod
-    def _struct(means, scales, quats, opacity, sh, sh_degree, activated):
+    def _struct(means, scales, quats, opacity, sh, sh_degree, activated, sh_half=False):
         g = _native.gs_gaussians()
         g.means, g.scales, g.quats, g.opacity, g.sh = (_ptr(x) for x in (means, scales, quats, opacity, sh))
         g.P = int(means.shape[0])
         g.sh_degree = int(sh_degree)
         g.activated = int(bool(activated))
+        g.sh_half = int(bool(sh_half))
         for x, k in ((means, 3), (scales, 3), (quats, 4), (sh, 48)):
             assert x.numel() == g.P * k, "array size does not match P"
         assert opacity.numel() == g.P
         return g
 
     def gs_scene_update(self, means, scales, quats, opacity, sh, sh_degree=3, activated=True, stream=None):
-        g = self._struct(means, scales, quats, opacity, sh, sh_degree, activated)
+        g = self._struct(means, scales, quats, opacity, sh, sh_degree, activated, self.sh_half)
         _check(lib().gs_scene_update(self.h, C.byref(g), _stream(stream)))
 
     @classmethod
-    def from_numpy(cls, ctx, scene, device="cuda", stream=None):
+    def from_numpy(cls, ctx, scene, device="cuda", stream=None, sh_half=False):
         """Upload a synth.Scene-like object (numpy float32 arrays) and build the device scene."""
         import torch
         arrs = [torch.from_numpy(a.reshape(a.shape[0], -1) if a.ndim > 1 else a).to(device).contiguous()
                 for a in (scene.means, scene.scales, scene.quats, scene.opacity, scene.sh)]
-        s = cls(ctx, *arrs, sh_degree=3, activated=scene.activated, stream=stream)
+        s = cls(ctx, *arrs, sh_degree=3, activated=scene.activated, stream=stream, sh_half=sh_half)
         s._inputs = arrs          # kept alive until the pack kernel has run
         return s
 

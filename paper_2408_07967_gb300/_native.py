@@ -19,7 +19,8 @@ class gs_camera(C.Structure):
 
 class gs_gaussians(C.Structure):
     _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacity", C.c_void_p),
-                ("sh", C.c_void_p), ("P", C.c_int64), ("sh_degree", C.c_int32), ("activated", C.c_int32)]
+                ("sh", C.c_void_p), ("P", C.c_int64), ("sh_degree", C.c_int32), ("activated", C.c_int32),
+                ("sh_half", C.c_int32), ("reserved", C.c_int32)]
 
 
 class gs_render_opts(C.Structure):

@@ -108,8 +108,10 @@ struct gs_scene {
     long long P = 0;
     int sh_degree = 3;
     int activated = 1;
+    int sh_half = 0;                 // SH stored as binary16 (fixed at creation)
     void *mem = nullptr;
-    float4 *pos_opa = nullptr, *rs = nullptr, *sh = nullptr;
+    float4 *pos_opa = nullptr, *rs = nullptr;
+    void *sh = nullptr;
 };
 
 struct gs_frame {
@@ -224,6 +226,7 @@ static gs_status check_gaussians(const gs_gaussians *g) {
     if (!g->means || !g->scales || !g->quats || !g->opacity || !g->sh)
         return fail(GS_ERR_INVALID_ARG, "a Gaussian array pointer is NULL");
     if (g->sh_degree < 0 || g->sh_degree > 3) return fail(GS_ERR_INVALID_ARG, "sh_degree %d not in 0..3", g->sh_degree);
+    if (g->sh_half != 0 && g->sh_half != 1) return fail(GS_ERR_INVALID_ARG, "sh_half %d not 0 or 1", g->sh_half);
     return GS_OK;
 }
 
@@ -238,17 +241,20 @@ gs_status gs_scene_create(gs_context *ctx, const gs_gaussians *g, gs_stream stre
     s->ctx = ctx;
     s->device = ctx->device;
     s->P = g->P;
+    s->sh_half = g->sh_half;
     // SH blocks first (256-byte aligned by cudaMalloc, so every 192-byte block starts on a
-    // 64-byte boundary), then scale/rotation, then positions
-    cudaError_t e = cudaMalloc(&s->mem, (size_t)(kShPlanes + 3) * (size_t)g->P * sizeof(float4));
+    // 64-byte boundary, every 96-byte binary16 block on a 32-byte one), then scale/rotation, then
+    // positions
+    const size_t sh_f4 = (size_t)(g->sh_half ? kShPlanes / 2 : kShPlanes) * (size_t)g->P;   // in float4 units
+    cudaError_t e = cudaMalloc(&s->mem, (sh_f4 + 3 * (size_t)g->P) * sizeof(float4));
     if (e != cudaSuccess) {
         delete s;
         return cuda_fail(e, "cudaMalloc(scene)");
     }
     float4 *base = (float4 *)s->mem;
     s->sh = base;
-    s->rs = base + (size_t)kShPlanes * g->P;
-    s->pos_opa = base + (size_t)(kShPlanes + 2) * g->P;
+    s->rs = base + sh_f4;
+    s->pos_opa = base + sh_f4 + 2 * (size_t)g->P;
     st = gs_scene_update(s, g, stream);
     if (st) {
         cudaFree(s->mem);
@@ -264,6 +270,7 @@ gs_status gs_scene_update(gs_scene *s, const gs_gaussians *g, gs_stream stream) 
     gs_status st = check_gaussians(g);
     if (st) return st;
     if (g->P != s->P) return fail(GS_ERR_INVALID_ARG, "P changed (%lld != %lld)", (long long)g->P, s->P);
+    if (g->sh_half != s->sh_half) return fail(GS_ERR_INVALID_ARG, "sh_half differs from the scene's creation");
     s->sh_degree = g->sh_degree;
     s->activated = g->activated ? 1 : 0;
     launch_pack_scene(*g, s->pos_opa, s->rs, s->sh, (cudaStream_t)stream);
@@ -491,6 +498,7 @@ static SceneView view_of(const gs_scene *s) {
     v.P = s->P;
     v.sh_degree = s->sh_degree;
     v.activated = s->activated;
+    v.sh_half = s->sh_half;
     return v;
 }
 
@@ -1063,6 +1071,7 @@ extern "C" gs_status gs_render_backward(gs_frame *f, const gs_scene *s, const fl
     a.scene.P = s->P;
     a.scene.sh_degree = s->sh_degree;
     a.scene.activated = s->activated;
+    a.scene.sh_half = s->sh_half;
     a.W = f->W;
     a.H = f->H;
     a.tiles_x = f->tiles_x;

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
         float f[48];
 #pragma unroll
         for (int k = 0; k < kShPlanes; ++k) {
-            const float4 v4 = sh_of(S, gid)[k];
+            const float4 v4 = sh_plane(S, gid, k);
             f[4 * k] = v4.x;
             f[4 * k + 1] = v4.y;
             f[4 * k + 2] = v4.z;

@@ -7,6 +7,7 @@
 // it.  The rest (SH colour, blending values) uses ordinary float arithmetic.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,17 +48,28 @@ struct Opts {
 //                       every Gaussian that passes the cull (most of them), so a dense plane;
 //   sh[kShPlanes i + k] SH floats 4k .. 4k+3: read only for paired Gaussians, which are scattered
 //                       over the id range, so each Gaussian's 192 bytes are contiguous (three
-//                       64-byte bursts) instead of twelve planes with one burst each.
+//                       64-byte bursts) instead of twelve planes with one burst each.  With
+//                       binary16 storage (opt-in) plane k is four halves, 96 bytes a Gaussian.
 struct SceneView {
     const float4 *pos_opa;
     const float4 *rs;
-    const float4 *sh;
+    const void *sh;
     int64_t P;
     int sh_degree;
     int activated;
+    int sh_half;             // SH kept as binary16
 };
 __device__ __forceinline__ const float4 *rs_of(const SceneView &S, long long gid) { return S.rs + 2 * gid; }
-__device__ __forceinline__ const float4 *sh_of(const SceneView &S, long long gid) { return S.sh + kShPlanes * gid; }
+// SH floats 4k .. 4k+3 of Gaussian gid (k < kShPlanes), from either storage.
+__device__ __forceinline__ float4 sh_plane(const SceneView &S, long long gid, int k) {
+    if (S.sh_half) {
+        const uint2 h = __ldg(reinterpret_cast<const uint2 *>(S.sh) + kShPlanes * gid + k);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&h.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&h.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    return __ldg(reinterpret_cast<const float4 *>(S.sh) + kShPlanes * gid + k);
+}
 
 // Render record of a paired Gaussian (48 bytes, three float4):
 //   r0 = (u, v, a, b2)   centre and conic, b2 = 2 b
@@ -344,7 +356,7 @@ struct PreprocessArgs {
     long long n_chunks;
 };
 
-void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *rs, float4 *sh, cudaStream_t s);
+void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *rs, void *sh, cudaStream_t s);
 void launch_pre_count(const PreprocessArgs &a, cudaStream_t s);
 void launch_req_pairs(const PreprocessArgs &a, unsigned long long *out, cudaStream_t s);
 void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted);

@@ -31,14 +31,24 @@ int preprocess_chunk() { return kPreBlock; }
 
 // ------------------------------------------------------------------------------------------ pack
 // Canonical AoS arrays -> the internal position, scale/rotation and SH arrays.  The SH block of
-// a CTA is contiguous in both layouts (48 floats per Gaussian), so it is copied as float4s.
-__global__ void __launch_bounds__(kPackBlock) k_pack_scene(gs_gaussians g, float4 *pos_opa, float4 *rs, float4 *sh) {
+// a CTA is contiguous in both layouts (48 floats per Gaussian), so it is copied four floats at a
+// time -- as float4s, or as four binary16 values (round to nearest even) when g.sh_half.
+__global__ void __launch_bounds__(kPackBlock) k_pack_scene(gs_gaussians g, float4 *pos_opa, float4 *rs, void *sh) {
     const long long base = (long long)blockIdx.x * kPackBlock;
     const int n = (int)min((long long)kPackBlock, g.P - base);
     const float *src = g.sh + base * 48;
-    float4 *dst = sh + base * kShPlanes;
-    for (int k = threadIdx.x; k < n * kShPlanes; k += kPackBlock)
-        dst[k] = make_float4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
+    if (g.sh_half) {
+        uint2 *dst = reinterpret_cast<uint2 *>(sh) + base * kShPlanes;
+        for (int k = threadIdx.x; k < n * kShPlanes; k += kPackBlock) {
+            const __half2 a = __floats2half2_rn(src[4 * k], src[4 * k + 1]);
+            const __half2 b = __floats2half2_rn(src[4 * k + 2], src[4 * k + 3]);
+            dst[k] = make_uint2(*reinterpret_cast<const unsigned *>(&a), *reinterpret_cast<const unsigned *>(&b));
+        }
+    } else {
+        float4 *dst = reinterpret_cast<float4 *>(sh) + base * kShPlanes;
+        for (int k = threadIdx.x; k < n * kShPlanes; k += kPackBlock)
+            dst[k] = make_float4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
+    }
     const long long i = base + threadIdx.x;
     if (threadIdx.x < n) {
         const float *m = g.means + 3 * i;
@@ -50,7 +60,7 @@ __global__ void __launch_bounds__(kPackBlock) k_pack_scene(gs_gaussians g, float
     }
 }
 
-void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *rs, float4 *sh, cudaStream_t s) {
+void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *rs, void *sh, cudaStream_t s) {
     long long blocks = (g.P + kPackBlock - 1) / kPackBlock;
     k_pack_scene<<<(unsigned)blocks, kPackBlock, 0, s>>>(g, pos_opa, rs, sh);
 }
@@ -92,11 +102,10 @@ __device__ __forceinline__ void sh_colour(const SceneView &S, long long gid, con
     const int nplanes = (3 * ncoef + 3) / 4;
     // SH float f = 3 i + ch belongs to coefficient i of channel ch; each channel accumulates in
     // ascending i as the planes stream in (float4 k holds floats 4k .. 4k+3)
-    const float4 *src = sh_of(S, gid);
     float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int k = 0; k < kShPlanes; ++k) {
-        const float4 v = k < nplanes ? __ldg(src + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 v = k < nplanes ? sh_plane(S, gid, k) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {

@@ -30,8 +30,8 @@ def ctx():
 
 
 def run_gpu(ctx, scene, cam, opts_kw=None, max_pairs=1 << 22, graph=False, variant=None, sort_mode=None,
-            sort_algo=None):
-    sc = gs.Scene.from_numpy(ctx, scene)
+            sort_algo=None, sh_half=False):
+    sc = gs.Scene.from_numpy(ctx, scene, sh_half=sh_half)
     fr = gs.Frame(ctx, scene.P, max_pairs, cam.width, cam.height)
     fr.gs_frame_set_tuning(blend_variant=variant, sort_mode=sort_mode, sort_algo=sort_algo)
     o = gs.gs_opts(**(opts_kw or {}))
@@ -129,6 +129,32 @@ def test_raw_parameters_activated_on_device(ctx):
     scene, cam = synth.random_small_scene(3000, 12, 128, 96, activated=False, log_scale_mu=-2.6)
     ref = oracle.Frame(scene, cam, mode=64)
     check(run_gpu(ctx, scene, cam), ref)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_sh_half_storage(ctx, sort_mode, graph):
+    """Opt-in binary16 SH storage: against the oracle given the same rounded coefficients (numpy's
+    IEEE round to nearest even, as the device's conversion) every forward bar holds as for binary32
+    storage -- pairs and keys do not depend on SH; against the unrounded coefficients the image
+    moves by the rounding alone, within the image bar."""
+    import dataclasses
+    scene, cam = synth.random_small_scene(3000, 21, 128, 96, log_scale_mu=-2.4)
+    rounded = dataclasses.replace(scene, sh=scene.sh.astype(np.float16).astype(np.float32))
+    res = run_gpu(ctx, scene, cam, sort_mode=sort_mode, graph=graph, sh_half=True)
+    check(res, oracle.Frame(rounded, cam, mode=64))
+    full = oracle.Frame(scene, cam, mode=64)
+    moved = np.abs(res["rgb"] - full.rgb)
+    assert 0 < moved.max() <= RGB_MAX, moved.max()
+
+
+def test_sh_half_fixed_at_creation(ctx):
+    scene, cam = synth.random_small_scene(100, 22, 64, 64)
+    sc = gs.Scene.from_numpy(ctx, scene, sh_half=True)
+    arrs = sc._inputs
+    sc.sh_half = False          # an update must keep the creation's storage
+    with pytest.raises(gs.GsError):
+        sc.gs_scene_update(*arrs)
 
 
 @pytest.mark.parametrize("sort_algo", [0, 1, 2])
