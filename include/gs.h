@@ -240,8 +240,8 @@ typedef struct {
                               scan passes (per-tile digit counts, a scan across tiles, then the
                               scatter: keys read twice, no tile waits on another); 2: the onesweep
                               passes of a sort fused into one cooperative launch (histograms, then
-                              the passes, separated by grid-wide barriers; sorts of one pass run
-                              as 0) */
+                              the passes, separated by grid-wide barriers; sorts of one pass, and
+                              any sort whose cooperative launch the device refuses, run as 0) */
     int32_t reserved[5];
 } gs_tuning;
 gs_status gs_frame_set_tuning(gs_frame *frame, const gs_tuning *tuning);
