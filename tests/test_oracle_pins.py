@@ -386,6 +386,27 @@ def test_bruteforce_equals_tiled_large_gaussians(oracle_lib, cap):
         assert f.evals >= int(f.last.sum())
 
 
+def test_transmittance_non_increasing_along_the_depth_order(oracle_lib):
+    """Invariant: a pixel's transmittance never rises as the list grows -- rendering only the k
+    nearest Gaussians (a prefix of every pixel's front-to-back list) gives T_k >= T_k' for k < k'
+    (each further entry multiplies T by 1 - alpha in [0.01, 1], is skipped, or meets the stop)."""
+    sc, cam = synth.random_small_scene(400, 23, 64, 48, log_scale_mu=-2.2, log_scale_sigma=0.8)
+    f = oracle.Frame(sc, cam, mode=64)
+    order = oracle.depth_order(f.valid, f.rec32)
+    prev = None
+    for k in (0, 1, 5, 20, 80, 200, len(order)):
+        valid = np.zeros_like(f.valid)
+        valid[order[:k]] = f.valid[order[:k]]
+        rgb, T = oracle.blend_brute(64, cam, valid, f.rec32, f.rec64)
+        if k == 0:
+            assert np.all(T == 1.0)
+        else:
+            assert np.all(T <= prev)
+        assert np.all(T >= 1e-4 * (1 - 1e-12)) and np.all(rgb >= 0.0)
+        prev = T
+    assert np.array_equal(prev, f.T)     # the whole list is the tiled frame
+
+
 def test_pairs_cover_every_alpha_above_tau(oracle_lib):
     """Invariant: every (pixel, Gaussian) with alpha0 exp(-q/2) >= tau in binary64 has its tile in
     the Gaussian's pair set (Section 4.1: only false positives are removed)."""
