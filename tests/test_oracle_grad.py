@@ -52,3 +52,22 @@ def test_gradient_is_zero_for_unused_gaussians(setup):
     used[fz.gid[: fz.n_contrib]] = True
     for k in ("means", "scales", "quats", "opacity", "sh"):
         assert np.all(an[k][~used] == 0)
+
+
+def test_frozen_forward_equals_the_render(setup):
+    """At the reference parameters the frozen-decision forward is the binary64 render itself
+    (the contributor lists and clamp states it holds fixed are the render's own)."""
+    scene, cam, fz, w, an = setup
+    rgb, T = fz.forward(fz.p0)
+    assert np.abs(rgb - fz.ref.rgb).max() <= 1e-12
+    assert np.abs(T - fz.ref.T).max() <= 1e-12
+    assert fz.ref.rgb.max() > 0.05            # the view is not empty
+
+
+def test_frozen_forward_equals_render_with_background_and_raw_inputs(oracle_lib):
+    scene, cam = synth.grad_subset(P=120, size=40, seed=5)
+    o = oracle.opts(bg=(0.3, 0.05, 0.6))
+    fz = oracle.Frozen(scene, cam, o)
+    rgb, T = fz.forward(fz.p0)
+    ref = oracle.Frame(scene, cam, o, mode=64)
+    assert np.abs(rgb - ref.rgb).max() <= 1e-12 and np.abs(T - ref.T).max() <= 1e-12

@@ -224,6 +224,44 @@ def test_fov_clamp_only_beyond_1p3_tan(oracle_lib):
     assert a[0, oracle.D["S00"]] < b[0, oracle.D["S00"]]
 
 
+def test_fov_clamp_sits_at_1p3_tan_half_fov(oracle_lib):
+    """The Jacobian clamp bites exactly beyond x/z = 1.3 tan(half fov) = 1.3 (W/2)/fx (and the
+    same for y with H and fy): just inside, Sigma' is that of the unclamped projection; just
+    outside, Sigma' no longer depends on how far out the Gaussian is (the off-axis Jacobian term
+    is frozen at the bound), while the unclamped Sigma' keeps changing.  The crossing found by
+    bisection on that behaviour lands on 1.3 (W/2)/fx."""
+    W, H, f = 64, 48, 50.0
+    cam = cam_simple(W=W, H=H, f=f)
+    z = 2.0
+    shape = dict(scales=[[0.05, 0.02, 0.01]], quats=[[0.8, 0.2, 0.5, 0.1]])
+    D = oracle.D
+
+    def sig(xz, yz, clamp=True):
+        sc = scene_of([[xz * z, yz * z, z]], **shape)
+        r = oracle.preprocess(sc, cam, oracle.opts(clamp_fov=clamp))[2][0]
+        return np.array([r[D["S00"]], r[D["S01"]], r[D["S11"]]])
+
+    for axis, lim in ((0, 1.3 * (W / 2) / f), (1, 1.3 * (H / 2) / f)):
+        def at(k, clamp=True):
+            return sig(k, 0.0, clamp) if axis == 0 else sig(0.0, k, clamp)
+        for sgn in (1.0, -1.0):
+            inside = sgn * lim * (1 - 1e-3)
+            assert np.array_equal(at(inside), at(inside, clamp=False))
+            out1, out2 = sgn * lim * (1 + 1e-3), sgn * lim * 1.5
+            assert np.array_equal(at(out1), at(out2))
+            assert not np.array_equal(at(out1, clamp=False), at(out2, clamp=False))
+            # bisection on "clamped == unclamped" between 0.5 lim and 1.5 lim
+            lo, hi = 0.5 * lim, 1.5 * lim
+            ref_out = at(sgn * hi)
+            for _ in range(40):
+                mid = 0.5 * (lo + hi)
+                if np.array_equal(at(sgn * mid), ref_out):
+                    hi = mid
+                else:
+                    lo = mid
+            assert abs(hi - lim) <= 1e-6 * lim, (axis, sgn, hi, lim)
+
+
 # ------------------------------------------------------------------ SH basis
 
 def test_sh_orthonormal_by_quadrature(oracle_lib):
@@ -249,6 +287,60 @@ def test_sh_addition_theorem(oracle_lib):
         for l in range(4):
             band = Y[l * l:(l + 1) * (l + 1)]
             assert abs((band ** 2).sum() - (2 * l + 1) / (4 * math.pi)) < 1e-12
+
+
+def real_sh_from_complex(d):
+    """Real SH of degree <= 3 built from scipy's complex spherical harmonics (which carry the
+    Condon-Shortley phase): m > 0 -> sqrt(2) Re Y_l^m, m < 0 -> sqrt(2) Im Y_l^|m|, m = 0 -> Y_l^0,
+    at index l^2 + l + m.  This is the sign and order convention of the 3DGS colour model (its
+    l = 1 band reads (-y, z, -x) times sqrt(3 / 4 pi)); nothing here comes from the oracle."""
+    special = pytest.importorskip("scipy.special")
+    x, y, z = d
+    theta = math.acos(max(-1.0, min(1.0, z)))
+    phi = math.atan2(y, x)
+    out = np.zeros(16)
+    for l in range(4):
+        for m in range(-l, l + 1):
+            Y = complex(special.sph_harm_y(l, abs(m), theta, phi))
+            out[l * l + l + m] = (math.sqrt(2) * Y.real if m > 0 else math.sqrt(2) * Y.imag if m < 0 else Y.real)
+    return out
+
+
+def test_sh_basis_sign_and_order_vs_scipy(oracle_lib):
+    """Index by index, the oracle's basis equals the real SH built from scipy's complex ones, at
+    random directions and at the axes (where a sign or an index swap within a band shows)."""
+    rng = np.random.default_rng(21)
+    dirs = [np.array(v, float) for v in ([1, 0, 0], [0, 1, 0], [0, 0, 1], [-1, 0, 0], [0, 0, -1])]
+    for _ in range(40):
+        d = rng.standard_normal(3)
+        dirs.append(d / np.linalg.norm(d))
+    for d in dirs:
+        ref = real_sh_from_complex(d)
+        got = oracle.sh_basis(d)
+        assert np.allclose(got, ref, atol=1e-12, rtol=0), (d, got - ref)
+    # the l = 1 band of the convention, written out: sqrt(3 / 4 pi) (-y, z, -x)
+    d = np.array([0.36, -0.48, 0.8])
+    assert np.allclose(real_sh_from_complex(d)[1:4], math.sqrt(3 / (4 * math.pi)) * np.array([0.48, 0.8, -0.36]))
+
+
+def test_sh_coefficient_layout_in_colour(oracle_lib):
+    """The colour of a Gaussian whose only SH coefficient is k_i (channel c of coefficient i at
+    sh[:, i, c], the [P,16,3] layout) is max(0, Y_i(d) k_i + 1/2) with Y_i from scipy and d the
+    unit vector from the camera centre -- for every i and channel."""
+    cam = synth.look_at((0.3, -2.5, 1.2), (0.1, 0.2, 0.9), 64, 64)
+    mean = np.array([0.1, 0.1, 0.9])
+    d = mean - cam.position()
+    Ysc = real_sh_from_complex(d / np.linalg.norm(d))
+    for i in range(16):
+        for c in range(3):
+            sh = np.zeros((1, 16, 3), np.float32)
+            sh[0, i, c] = 0.4 - 0.1 * c
+            sc = scene_of([mean], [[0.02] * 3], sh=sh)
+            valid, rec32, rec64, _ = oracle.preprocess(sc, cam)
+            assert valid[0] == 1
+            exp = np.full(3, 0.5)
+            exp[c] = max(0.0, Ysc[i] * float(sh[0, i, c]) + 0.5)
+            assert np.allclose(rec64[0, 6:9], exp, atol=1e-7), (i, c, rec64[0, 6:9], exp)
 
 
 def test_sh_colour_in_record(oracle_lib):
