@@ -165,7 +165,8 @@ gs_status gs_preprocess(gs_frame *frame, const gs_scene *scene, const gs_camera 
    read on the device. */
 gs_status gs_sort(gs_frame *frame, gs_stream stream);
 
-/* Stage c: start of every tile's run in the sorted keys (binary search per tile). */
+/* Stage c: start of every tile's run in the sorted keys -- one pass over the keys when the tiles
+   hold between 1 and 512 pairs on average, else a binary search per tile. */
 gs_status gs_ranges(gs_frame *frame, gs_stream stream);
 
 /* Stage d (Section 2.2 render; Section 5.2): per 16x16 tile, walk the tile's sorted list
@@ -279,6 +280,20 @@ typedef struct {
 } gs_alu_peaks;
 gs_status gs_measure_alu_peaks(int32_t device, double target_ms, gs_alu_peaks *out);
 
+/* Evaluates, over n binary32 inputs x_dev[i] (device), the device routines whose bits decide the
+   pair set, exactly as the preprocess kernel runs them, into y_dev[i] (device):
+     fn 0: t = 2 ln(x / param), the opacity-aware threshold of Eq. 3 (x = alpha0, param = tau,
+           Section 4.1);
+     fn 1: e^x, the activation of a log-scale (Section 2.2's 3D covariance from scales);
+     fn 2: 1 / (1 + e^-x), the activation of an opacity logit.
+   ln and exp are the library's own binary32 routines (argument reduction, a fixed polynomial,
+   every operation explicitly rounded), so that a host program implementing the same published
+   method reproduces them bit for bit; this call exists to test that over whole input domains.
+   Enqueued on `stream`, no synchronisation.  The caller owns both arrays.  Errors:
+   GS_ERR_INVALID_ARG (fn out of range, n < 0, NULL array with n > 0), GS_ERR_CUDA. */
+gs_status gs_eval_decision_math(int32_t fn, const float *x_dev, float *y_dev, int64_t n, float param,
+                                gs_stream stream);
+
 /* Enables (1) or disables (0) the instrumented blend that counts, per frame, the (pixel, entry)
    pairs walked before early stop and those passing q <= t (gs_frame_stats.evaluations /
    .contributions).  Same outputs; slower; meant for measurement, not for timed runs. */
@@ -322,10 +337,30 @@ gs_status gs_frame_ranges(gs_frame *frame, uint32_t *starts_dev, int64_t cap, gs
    buffers of the same sizes are caller-provided ping-pong storage.  *in_tmp (host) is set to 1
    when the result ended in the tmp buffers (odd number of passes), else 0.  Scratch for the
    histograms and the chained scan comes from the context (grown on demand, never freed before
-   gs_context_destroy).  Errors: GS_ERR_INVALID_ARG (n < 0, n >= 2^30, end_bit out of range). */
+   gs_context_destroy).  The call only enqueues work; a device-side failure (a bounded wait that
+   gave up, which leaves the output invalid) is reported by gs_sort_pairs_status.  Errors:
+   GS_ERR_INVALID_ARG (n < 0, n >= 2^30, end_bit out of range). */
 gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys_dev, uint32_t *vals_dev, uint64_t *keys_tmp_dev,
                         uint32_t *vals_tmp_dev, int64_t n, int32_t end_bit, int32_t *in_tmp,
                         gs_stream stream);
+
+/* Synchronises `stream` and reports the device-side outcome of the last gs_sort_pairs on `ctx`:
+   GS_OK, or GS_ERR_DEVICE_TIMEOUT when one of its bounded waits gave up (its output is then not
+   a sorted permutation and must be discarded; the next gs_sort_pairs starts clean).  Errors:
+   GS_ERR_INVALID_ARG (NULL context), GS_ERR_CUDA. */
+gs_status gs_sort_pairs_status(gs_context *ctx, gs_stream stream);
+
+/* Bounded waits.  Kernels that wait on other thread blocks (the sort's look-back between tiles,
+   the grid barriers of the fused sort) give up after a number of polls, set a device status
+   (reported as GS_ERR_DEVICE_TIMEOUT by gs_frame_get_stats, gs_sort_pairs_status and
+   gs_sort_pairs_noalloc_status) and return; kernels launched after such a failure that would read
+   its output write nothing.  gs_set_wait_limit sets that number of polls for every launch that
+   follows, process-wide (0 restores the default, 2^22 polls of at least 20 ns each); a small value
+   makes correct runs fail and exists to test the failure path.  Waits of a thread block on its own
+   bulk copies always keep the default, so that no block leaves while a copy into its shared memory
+   is in flight.  gs_get_wait_limit returns the limit in force.  The paper has no counterpart. */
+gs_status gs_set_wait_limit(uint32_t polls);
+uint32_t gs_get_wait_limit(void);
 
 /* ------------------------------------------------------------------------------------------
    Serving: a continuous-batching request loop over device-resident scenes (a worker thread
@@ -447,10 +482,20 @@ gs_status gs_router_outstanding(gs_router *router, int32_t replica, int64_t *req
    capture.  Every call on a device shares the array and it keeps the last call's contents (the
    call clears what must start at zero), so calls whose work overlaps on the GPU -- e.g. on two
    streams without an ordering between them -- race and must not be issued.  Calls no cudaMalloc,
-   cudaFree or allocating library routine. */
+   cudaFree or allocating library routine.  The device address looked up by the first call is kept
+   for the life of the process: after cudaDeviceReset on that device the array's old address is
+   stale, so do not use this entry point again in that process.  Like gs_sort_pairs it only
+   enqueues work; gs_sort_pairs_noalloc_status reports a device-side failure of the last call. */
 gs_status gs_sort_pairs_noalloc(uint64_t *keys_dev, uint32_t *vals_dev, uint64_t *keys_tmp_dev,
                                 uint32_t *vals_tmp_dev, int64_t n, int32_t end_bit, int32_t *in_tmp,
                                 gs_stream stream);
+
+/* Synchronises `stream` (on which the last gs_sort_pairs_noalloc of the current device was issued)
+   and reads that call's device status from the fixed array: GS_OK, or GS_ERR_DEVICE_TIMEOUT when
+   one of its bounded waits gave up (the output is then invalid; the next call clears the status).
+   Allocates nothing.  Errors: GS_ERR_INVALID_ARG (no allocation-free sort has run on the current
+   device), GS_ERR_CUDA. */
+gs_status gs_sort_pairs_noalloc_status(gs_stream stream);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,8 @@ def lib():
             L.or_logf_max_ulp.argtypes = [C.c_float, C.c_float, _fp]
             L.or_expf_max_ulp.restype = C.c_double
             L.or_expf_max_ulp.argtypes = [C.c_float, C.c_float, C.c_int32, _fp]
+            L.or_eval_decision_math.restype = None
+            L.or_eval_decision_math.argtypes = [C.c_int32, _i64, C.c_void_p, C.c_float, C.c_void_p]
             L.or_sh_basis.restype = None
             L.or_sh_basis.argtypes = [_dp, _dp]
             L.or_tile_hit.restype = C.c_int
@@ -174,6 +176,15 @@ def expf_max_ulp(lo, hi, stride=1):
     w = C.c_float()
     e = lib().or_expf_max_ulp(float(lo), float(hi), int(stride), C.byref(w))
     return e, w.value
+
+
+def eval_decision_math(fn: int, x, param: float = 0.0):
+    """The oracle's binary32 decision arithmetic over an array: fn 0 the Eq. 3 threshold
+    2 ln(x / param), fn 1 e^x, fn 2 1 / (1 + e^-x) -- the routines its preprocess runs."""
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.empty_like(x)
+    lib().or_eval_decision_math(int(fn), x.shape[0], _ptr(x), float(param), _ptr(y))
+    return y
 
 
 def sh_basis(d):

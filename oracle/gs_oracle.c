@@ -170,6 +170,29 @@ float or_expf(float x)
     return (p * s1) * s2;
 }
 
+/* Opacity-aware threshold of Eq. 3 in binary32: alpha0 exp(-q/2) >= tau <=> q <= 2 ln(alpha0/tau). */
+float or_threshold(float alpha0, float tau)
+{
+    float ratio = alpha0 / tau;
+    return 2.0f * or_logf(ratio);
+}
+
+/* Opacity from its logit in binary32: 1 / (1 + e^-x) with or_expf. */
+float or_sigmoidf(float x)
+{
+    float e = or_expf(-x);
+    return 1.0f / (1.0f + e);
+}
+
+/* The three functions above over an array (fn 0: or_threshold(x[i], param); 1: or_expf(x[i]);
+ * 2: or_sigmoidf(x[i])), for exhaustive comparisons over whole input domains. */
+void or_eval_decision_math(int32_t fn, int64_t n, const float *x, float param, float *y)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        y[i] = fn == 0 ? or_threshold(x[i], param) : fn == 1 ? or_expf(x[i]) : or_sigmoidf(x[i]);
+}
+
 /* Max ulp error of or_logf against binary64 log over every float in [lo, hi]. */
 double or_logf_max_ulp(float lo, float hi, float *worst_x)
 {
@@ -402,15 +425,13 @@ static int preprocess_one(const OrGauss *G, int64_t g, const OrCamera *cam, cons
     if (G->activated) {
         alpha0 = G->opac[g];
     } else {
-        float e = or_expf(-G->opac[g]);
-        alpha0 = 1.0f / (1.0f + e);
+        alpha0 = or_sigmoidf(G->opac[g]);
     }
     /* cull (Alg. 4): z > near and opacity > tau */
     if (!(p[2] > cam->near_z)) return 0;
     if (!(alpha0 > o->tau)) return 0;
     /* opacity-aware threshold (Eq. 3): q <= t = 2 ln(alpha0 / tau) */
-    float ratio = alpha0 / o->tau;
-    float t_full = 2.0f * or_logf(ratio);
+    float t_full = or_threshold(alpha0, o->tau);
     float t = t_full;
     if (o->cap_3sigma && t > 9.0f) t = 9.0f;
     /* 3D covariance Sigma = R S S^T R^T */

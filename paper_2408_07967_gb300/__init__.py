@@ -14,7 +14,7 @@ import ctypes as C
 
 from . import _native
 
-__all__ = ["GsError", "Context", "Scene", "Frame", "Server", "Router", "gs_camera_from", "gs_opts", "gs_sort_pairs", "lib"]
+__all__ = ["GsError", "Context", "Scene", "Frame", "Server", "Router", "gs_camera_from", "gs_opts", "gs_sort_pairs", "gs_eval_decision_math", "lib"]
 
 GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_PAIR_OVERFLOW", -4: "GS_ERR_CUDA",
@@ -473,3 +473,12 @@ def gs_sort_pairs(ctx: Context, keys, vals, end_bit: int = 64, stream=None):
     _check(lib().gs_sort_pairs(ctx.h, _ptr(keys), _ptr(vals), _ptr(kt), _ptr(vt), n, int(end_bit), C.byref(in_tmp),
                                _stream(stream)))
     return (kt, vt) if in_tmp.value else (keys, vals)
+
+
+def gs_eval_decision_math(fn: int, x, param: float = 0.0, stream=None):
+    """The device's binary32 decision arithmetic over a float32 CUDA tensor: fn 0 the Eq. 3
+    threshold 2 ln(x / param), fn 1 e^x, fn 2 1 / (1 + e^-x).  Returns a new tensor."""
+    import torch
+    y = torch.empty_like(x)
+    _check(lib().gs_eval_decision_math(int(fn), _ptr(x), _ptr(y), int(x.numel()), float(param), _stream(stream)))
+    return y

@@ -132,6 +132,11 @@ PROTOTYPES = {
     "gs_server_wait": (_st, [_vp, C.c_uint64, C.c_int32, C.POINTER(gs_request_stats)]),
     "gs_server_get_stats": (_st, [_vp, C.POINTER(gs_server_stats)]),
     "gs_sort_pairs_noalloc": (_st, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int32), _vp]),
+    "gs_eval_decision_math": (_st, [C.c_int32, _vp, _vp, C.c_int64, C.c_float, _vp]),
+    "gs_sort_pairs_status": (_st, [_vp, _vp]),
+    "gs_set_wait_limit": (_st, [C.c_uint32]),
+    "gs_get_wait_limit": (C.c_uint32, []),
+    "gs_sort_pairs_noalloc_status": (_st, [_vp]),
 }
 
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include <algorithm>
+#include <atomic>
 
 #include "gs_internal.cuh"
 
@@ -19,11 +20,16 @@ using namespace gs;
 namespace {
 
 thread_local std::string g_err;
+std::atomic<unsigned> g_wait_limit{0};   // 0: kSpinLimit
 
 }  // namespace
 
 namespace gs {
 void set_error_message(const char *msg) { g_err = msg ? msg : ""; }
+unsigned wait_limit() {
+    const unsigned v = g_wait_limit.load(std::memory_order_relaxed);
+    return v ? v : kSpinLimit;
+}
 }  // namespace gs
 
 namespace {
@@ -656,10 +662,10 @@ gs_status gs_ranges(gs_frame *f, gs_stream stream) {
     if (f->W <= 0) return fail(GS_ERR_INVALID_ARG, "gs_ranges before gs_preprocess");
     if (f->mode_used == 1)
         launch_ranges32((const unsigned *)f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs,
-                        f->batch.total_tiles, f->starts, (cudaStream_t)stream);
+                        f->batch.total_tiles, f->starts, f->ctr, (cudaStream_t)stream);
     else
         launch_ranges(f->keys[f->sorted_buf], &f->ctr->n_pairs, f->max_pairs, f->batch.total_tiles, f->starts,
-                      (cudaStream_t)stream);
+                      f->ctr, (cudaStream_t)stream);
     if (f->batch.total_tiles <= kOrderMaxTiles)
         launch_tile_order(f->starts, f->batch.total_tiles, f->torder, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
@@ -670,6 +676,7 @@ static gs_status blend_batch(gs_frame *f, float *const *rgb, float *const *T, ui
                              const gs_render_opts *opts_override, gs_stream stream) {
     BlendArgs a;
     a.B = f->batch;
+    a.ctr = f->ctr;
     for (int r = 0; r < a.B.n; ++r) {
         if (!rgb[r]) return fail(GS_ERR_INVALID_ARG, "rgb output %d is NULL", r);
         a.B.r[r].rgb = rgb[r];
@@ -837,7 +844,8 @@ gs_status gs_frame_pairs(gs_frame *f, int32_t which, uint64_t *keys, uint32_t *v
     if (m > 0) {
         if (keys) {
             if (f->mode_used == 1)   // rebuild (tile << 32 | depth bits) from the 32-bit tile keys
-                launch_make_keys((const unsigned *)f->keys[b], f->vals[b], f->geo1, m, (unsigned long long *)keys, st);
+                launch_make_keys((const unsigned *)f->keys[b], f->vals[b], f->geo1, m, (unsigned long long *)keys,
+                                 f->ctr, st);
             else
                 GS_CUDA(cudaMemcpyAsync(keys, f->keys[b], (size_t)m * 8, cudaMemcpyDeviceToDevice, st));
             GS_CUDA(cudaGetLastError());
@@ -883,12 +891,32 @@ gs_status gs_sort_pairs(gs_context *ctx, uint64_t *keys, uint32_t *vals, uint64_
         ctx->sort.desc = (unsigned long long *)(b + od);
         ctx->sort.max_tiles = tiles;
     }
+    // a timeout reported by an earlier sort on this context must not stop this one
+    GS_CUDA(cudaMemsetAsync(&ctx->ctr->status, 0, sizeof(unsigned), (cudaStream_t)stream));
     const int passes = launch_sort((unsigned long long *)keys, vals, (unsigned long long *)keys_tmp, vals_tmp, nullptr,
                                    n, n, end_bit, ctx->sort, ctx->ctr, (cudaStream_t)stream);
     GS_CUDA(cudaGetLastError());
     *in_tmp = passes & 1;
     return GS_OK;
 }
+
+gs_status gs_sort_pairs_status(gs_context *ctx, gs_stream stream) {
+    if (!ctx) return fail(GS_ERR_INVALID_ARG, "context is NULL");
+    GS_CUDA(cudaSetDevice(ctx->device));
+    GS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned status = 0;
+    GS_CUDA(cudaMemcpy(&status, &ctx->ctr->status, sizeof(status), cudaMemcpyDeviceToHost));
+    if (status & kStTimeout)
+        return fail(GS_ERR_DEVICE_TIMEOUT, "a bounded wait of the last gs_sort_pairs gave up: its output is invalid");
+    return GS_OK;
+}
+
+gs_status gs_set_wait_limit(uint32_t polls) {
+    g_wait_limit.store(polls, std::memory_order_relaxed);
+    return GS_OK;
+}
+
+uint32_t gs_get_wait_limit(void) { return wait_limit(); }
 
 }  // extern "C"
 
@@ -1058,6 +1086,7 @@ extern "C" gs_status gs_render_backward(gs_frame *f, const gs_scene *s, const fl
     }
     GS_CUDA(cudaMemsetAsync(f->grad2d, 0, sizeof(float) * (size_t)grad2d_floats() * (size_t)s->P, st));
     BwdArgs a;
+    a.ctr = f->ctr;
     a.recs = f->recs;
     a.vals = f->vals[f->sorted_buf];
     a.starts = f->starts;

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(const __grid_con
     __shared__ unsigned s_gid[kBwdThreads];
     __shared__ float s_acc[kBwdThreads][9];
     __shared__ unsigned s_maxlast;
+    if (upstream_timed_out(A.ctr)) return;   // the forward's sort gave up: its ids may be garbage
     const int tid = threadIdx.x, lane = tid & 31;
     const unsigned FULL = 0xffffffffu;
     const int tile = blockIdx.x;

@@ -21,8 +21,12 @@ constexpr int kShPlanes = 12;        // 48 SH floats as twelve float4
 // device-side status bits, collected in FrameCounters::status
 enum : unsigned { kStPairOverflow = 1u, kStTimeout = 2u };
 
-// Bounded waits: a spin gives up after this many polls and sets kStTimeout.
+// Bounded waits: a spin gives up after this many polls and sets kStTimeout.  Waits on other CTAs
+// (look-back descriptors, grid barriers) take the process-wide limit wait_limit() (this value
+// unless gs_set_wait_limit changed it); waits of a CTA on its own bulk copies always take this one,
+// so a CTA never leaves while a copy into its shared memory is in flight.
 constexpr unsigned kSpinLimit = 1u << 22;
+unsigned wait_limit();
 
 struct Cam {
     float R[9];
@@ -145,6 +149,14 @@ struct FrameCounters {
     unsigned int pad1[4];
 };
 
+// True when a bounded wait of this frame gave up earlier in the stream: the sort output that a
+// consumer would read may then be incomplete (wrong ids, tile keys out of range), so consumers
+// return at once.  For kernels that never set the timeout bit themselves, so every thread reads
+// the same value and may branch on it without a barrier.
+__device__ __forceinline__ bool upstream_timed_out(const FrameCounters *ctr) {
+    return (*(const volatile unsigned *)&ctr->status & kStTimeout) != 0u;
+}
+
 // ----------------------------------------------------------------------------------------------
 // explicit IEEE binary32 operations (never contracted)
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
@@ -219,6 +231,12 @@ __device__ __forceinline__ float exp_rn(float x) {
     float s2 = __uint_as_float((unsigned)(k2 + 127) << 23);
     return fmul(fmul(p, s1), s2);
 }
+
+// Eq. 3: alpha0 exp(-q/2) >= tau  <=>  q <= t = 2 ln(alpha0 / tau), in binary32 with the own ln.
+__device__ __forceinline__ float threshold_t(float alpha0, float tau) { return fmul(2.0f, log_rn(fdiv(alpha0, tau))); }
+
+// Opacity from its logit, 1 / (1 + e^-x), with the own exp.
+__device__ __forceinline__ float sigmoid_rn(float x) { return fdiv(1.0f, fadd(1.0f, exp_rn(-x))); }
 
 // Exact ellipse/tile test (Algorithm 3, Eq. 9 with the linear coefficient halved): the tile
 // [x0,x1] x [y0,y1] meets {a X^2 + 2 b X Y + c Y^2 <= t} about (u, v) iff the centre is inside,
@@ -363,7 +381,7 @@ void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted);
 struct SortScratch;
 int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cudaStream_t s, bool counted);
 void launch_make_keys(const unsigned *tkeys, const unsigned *vals, const float4 *geo1, long long n,
-                      unsigned long long *out, cudaStream_t s);
+                      unsigned long long *out, const FrameCounters *ctr, cudaStream_t s);
 int preprocess_chunk();
 
 struct SortScratch {
@@ -387,18 +405,19 @@ int launch_sort(unsigned long long *keys, unsigned *vals, unsigned long long *ke
                 const unsigned long long *n_dev, long long n_host, long long cap, int end_bit,
                 const SortScratch &scr, FrameCounters *ctr, cudaStream_t s);
 void launch_ranges(const unsigned long long *keys, const unsigned long long *n_dev, long long cap, int ntiles,
-                   unsigned *starts, cudaStream_t s);
+                   unsigned *starts, const FrameCounters *ctr, cudaStream_t s);
 // 32-bit-key forms (depth bits alone, tile id alone) used by the two-level sort.
 int launch_sort32(unsigned *keys, unsigned *vals, unsigned *keys_tmp, unsigned *vals_tmp,
                   const unsigned long long *n_dev, long long cap, int end_bit, const SortScratch &scr,
                   FrameCounters *ctr, cudaStream_t s);
 void launch_ranges32(const unsigned *keys, const unsigned long long *n_dev, long long cap, int ntiles,
-                     unsigned *starts, cudaStream_t s);
+                     unsigned *starts, const FrameCounters *ctr, cudaStream_t s);
 // Blend order of the tiles: decreasing list length class (see gs_render.cu).
 void launch_tile_order(const unsigned *starts, int ntiles, unsigned *order, cudaStream_t s);
 
 struct BlendArgs {
     BatchDesc B;
+    const FrameCounters *ctr;        // status of the frame (a timed-out sort leaves nothing to blend)
     const Rec *recs;
     const unsigned *vals;
     const unsigned *starts;
@@ -413,6 +432,7 @@ void launch_blend(const BlendArgs &a, cudaStream_t s);
 int blend_variant_count();
 
 struct BwdArgs {
+    const FrameCounters *ctr;        // status of the forward's frame
     const Rec *recs;
     const unsigned *vals;
     const unsigned *starts;

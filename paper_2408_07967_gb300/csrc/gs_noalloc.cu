@@ -76,9 +76,14 @@ extern "C" gs_status gs_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint6
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         snprintf(g_msg, sizeof(g_msg), "cudaGetDevice: %s", cudaGetErrorString(e));
         return report(GS_ERR_CUDA);
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        snprintf(g_msg, sizeof(g_msg), "device %d: the allocation-free sort serves devices 0..%d", dev,
+                 kMaxDevices - 1);
+        return report(GS_ERR_INVALID_ARG);
     }
     unsigned long long *base = nullptr;
     {
@@ -122,5 +127,38 @@ extern "C" gs_status gs_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint6
         return report(GS_ERR_CUDA);
     }
     *in_tmp = passes & 1;
+    return GS_OK;
+}
+
+extern "C" gs_status gs_sort_pairs_noalloc_status(gs_stream stream) {
+    g_msg[0] = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        snprintf(g_msg, sizeof(g_msg), "no usable current device");
+        return report(GS_ERR_CUDA);
+    }
+    unsigned long long *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_setup_mu);
+        base = g_scratch_dev[dev];
+    }
+    if (!base) {
+        snprintf(g_msg, sizeof(g_msg), "no allocation-free sort has run on device %d", dev);
+        return report(GS_ERR_INVALID_ARG);
+    }
+    e = cudaStreamSynchronize((cudaStream_t)stream);
+    unsigned status = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&status, (const char *)base + offsetof(FrameCounters, status), sizeof(status),
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        snprintf(g_msg, sizeof(g_msg), "reading the sort status: %s", cudaGetErrorString(e));
+        return report(GS_ERR_CUDA);
+    }
+    if (status & kStTimeout) {
+        snprintf(g_msg, sizeof(g_msg), "a bounded wait of the last allocation-free sort gave up: its output is invalid");
+        return report(GS_ERR_DEVICE_TIMEOUT);
+    }
     return GS_OK;
 }

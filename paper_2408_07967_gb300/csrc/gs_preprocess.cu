@@ -137,7 +137,7 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
         s = fadd(s, fmul(R[3 * i + 2], po.z));
         p[i] = fadd(s, cam.t[i]);
     }
-    float alpha0 = S.activated ? po.w : fdiv(1.0f, fadd(1.0f, exp_rn(-po.w)));
+    float alpha0 = S.activated ? po.w : sigmoid_rn(po.w);
     if (!(p[2] > cam.near_z)) return false;
     if (!(alpha0 > o.tau)) return false;
     passed_cull = true;
@@ -185,7 +185,7 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
             return false;
     }
     // Eq. 3: alpha0 exp(-q/2) >= tau  <=>  q <= 2 ln(alpha0 / tau)
-    const float t_full = fmul(2.0f, log_rn(fdiv(alpha0, o.tau)));
+    const float t_full = threshold_t(alpha0, o.tau);
     float t = t_full;
     if (o.cap_3sigma && t > 9.0f) t = 9.0f;
     // Sigma = R_q diag(s^2) R_q^T
@@ -611,6 +611,7 @@ __global__ void __launch_bounds__(kPreBlock) k_vis_compact(const __grid_constant
 
 // Two-level order, step 2: pairs per chunk of 256 depth-sorted Gaussians.
 __global__ void __launch_bounds__(kPreBlock) k_emit_sum(const __grid_constant__ PreprocessArgs A) {
+    if (upstream_timed_out(A.ctr)) return;   // the depth sort gave up: its ids may be garbage
     const long long r = (long long)blockIdx.x * kPreBlock + threadIdx.x;
     const long long V = (long long)A.ctr->n_vis64;
     const unsigned c = r < V ? A.counts[A.dsorted[r]] : 0u;
@@ -638,6 +639,7 @@ template <bool DEPTH>
 __global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
     __shared__ EmitSmem E;
     PreSmem &S = E.P;
+    if (DEPTH && upstream_timed_out(A.ctr)) return;   // the depth sort gave up: its ids may be garbage
     const int tid = threadIdx.x;
     const long long chunk = blockIdx.x;
     long long gid;                    // here: the record index (request rec0 + Gaussian id)
@@ -983,15 +985,16 @@ void launch_req_pairs(const PreprocessArgs &a, unsigned long long *out, cudaStre
 }
 
 __global__ void k_make_keys(const unsigned *tkeys, const unsigned *vals, const float4 *geo1, long long n,
-                            unsigned long long *out) {
+                            unsigned long long *out, const FrameCounters *ctr) {
+    if (upstream_timed_out(ctr)) return;     // the sort gave up: its ids may be garbage
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = ((unsigned long long)tkeys[i] << 32) | __float_as_uint(geo1[vals[i]].z);
 }
 
 void launch_make_keys(const unsigned *tkeys, const unsigned *vals, const float4 *geo1, long long n,
-                      unsigned long long *out, cudaStream_t s) {
+                      unsigned long long *out, const FrameCounters *ctr, cudaStream_t s) {
     if (n <= 0) return;
-    k_make_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tkeys, vals, geo1, n, out);
+    k_make_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tkeys, vals, geo1, n, out, ctr);
 }
 
 }  // namespace gs

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
     using WR = WarpRegion<PX>;
     static_assert(BATCH % NT == 0 && BATCH % 32 == 0, "batch must be a multiple of the thread count");
     __shared__ BlendSmem<PX, BATCH> S;
+    if (upstream_timed_out(A.ctr)) return;   // the sort gave up: its ids may be garbage
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtile = A.order ? (int)A.order[blockIdx.x] : (int)blockIdx.x;   // global tile of the batch
     const ReqDesc &R = A.B.r[req_of_tile(A.B, gtile)];

@@ -18,8 +18,9 @@
 //   * Reduce-then-scan (k_rts_count, k_rts_scan, k_rts_scatter): per pass, per-tile digit counts,
 //     a scan across tiles, then the scatter at the scanned positions; no tile waits on another.
 // For 32-bit keys the next tile's keys and values arrive by bulk copy (cp.async.bulk on an
-// mbarrier) while the current tile is written out.  Every wait is bounded by kSpinLimit polls
-// and reports a timeout in the frame's status word.
+// mbarrier) while the current tile is written out.  Every wait is bounded (waits on other CTAs by
+// wait_limit() polls, waits on the CTA's own copies by kSpinLimit) and reports a timeout in the
+// frame's status word; a pass or a consumer launched after a timeout writes nothing.
 //
 // Ranges: the first position of every tile id in the sorted keys, by one pass over the keys or a
 // binary search per tile; tile t spans [start[t], start[t+1]).
@@ -50,6 +51,12 @@ long long sort_desc_words(long long max_tiles) {
     return (max_tiles + (max_tiles + kLookBlock - 1) / kLookBlock) * 256;
 }
 
+// Digit mask of pass p of a sort over bits [0, end_bit): 8 bits, and end_bit - 8 (passes - 1) bits in
+// the last pass (top_mask), so that bits at or above end_bit never take part in the order.
+__device__ __forceinline__ unsigned digit_mask(int p, int passes, unsigned top_mask) {
+    return p == passes - 1 ? top_mask : 0xffu;
+}
+
 __device__ __forceinline__ long long pair_count(const unsigned long long *n_dev, long long n_host, long long cap) {
     long long n = n_dev ? (long long)*(const volatile unsigned long long *)n_dev : n_host;
     return n < cap ? n : cap;
@@ -62,8 +69,8 @@ __device__ __forceinline__ long long pair_count(const unsigned long long *n_dev,
 // Gaussian share their depth bytes: neighbouring keys would collide on one counter).  Keys are
 // 16-byte aligned whenever the base is; a misaligned base falls back to single keys.
 template <class K>
-__device__ __forceinline__ void hist_accumulate(const K *keys, long long n, int passes, unsigned *s_h, long long gtid,
-                                                long long stride) {
+__device__ __forceinline__ void hist_accumulate(const K *keys, long long n, int passes, unsigned top_mask,
+                                                unsigned *s_h, long long gtid, long long stride) {
     constexpr int V = 4;
     const bool vec = ((uintptr_t)keys & 15u) == 0;
     const long long nv = vec ? n / V : 0;
@@ -73,22 +80,25 @@ __device__ __forceinline__ void hist_accumulate(const K *keys, long long n, int 
         for (int j = 0; j < V; ++j) k[j] = __ldcg(keys + c * V + j);
 #pragma unroll
         for (int j = 0; j < V; ++j)
-            for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k[j] >> (8 * p)) & 0xffu)], 1u);
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&s_h[p * 256 + ((unsigned)(k[j] >> (8 * p)) & digit_mask(p, passes, top_mask))], 1u);
     }
     for (long long i = nv * V + gtid; i < n; i += stride) {
         const K k = __ldcg(keys + i);
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (unsigned)((k >> (8 * p)) & 0xffu)], 1u);
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&s_h[p * 256 + ((unsigned)(k >> (8 * p)) & digit_mask(p, passes, top_mask))], 1u);
     }
 }
 
 template <class K>
 __global__ void __launch_bounds__(512) k_sort_hist(const K *keys, const unsigned long long *n_dev,
-                                                   long long n_host, long long cap, int passes, unsigned *hist) {
+                                                   long long n_host, long long cap, int passes, unsigned top_mask,
+                                                   unsigned *hist) {
     __shared__ unsigned s_h[8 * 256];
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
     const long long n = pair_count(n_dev, n_host, cap);
-    hist_accumulate(keys, n, passes, s_h, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+    hist_accumulate(keys, n, passes, top_mask, s_h, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                     (long long)gridDim.x * blockDim.x);
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
@@ -180,7 +190,8 @@ struct ScatterSmem {
 // walk, 0 when it ran past lo on aggregates alone, 2 on a timeout (status flagged).  The first
 // round reads `span` entries.
 __device__ __forceinline__ int look_back(const unsigned long long *base, long long j, long long lo,
-                                         unsigned long long tag, int span, unsigned &sum, FrameCounters *ctr) {
+                                         unsigned long long tag, int span, unsigned &sum, FrameCounters *ctr,
+                                         unsigned limit) {
     unsigned spins = 0;
     while (j >= lo) {
         unsigned long long d[kLookWindow];
@@ -202,7 +213,7 @@ __device__ __forceinline__ int look_back(const unsigned long long *base, long lo
         if (done) return 1;
         j -= w;
         if (w == 0) {
-            if (++spins > kSpinLimit) {
+            if (++spins > limit) {
                 atomicOr(&ctr->status, kStTimeout);
                 return 2;
             }
@@ -242,7 +253,8 @@ template <class K, class Publish, class Resolve, class Next>
 __device__ __forceinline__ bool sort_tile(ScatterSmem<K> &S, int b, long long tile, const K *__restrict__ kin,
                                           const unsigned *__restrict__ vin, K *__restrict__ kout,
                                           unsigned *__restrict__ vout, long long n, int items, int shift,
-                                          FrameCounters *ctr, unsigned &phases, Publish publish, Resolve resolve,
+                                          unsigned dmask, FrameCounters *ctr, unsigned &phases, Publish publish,
+                                          Resolve resolve,
                                           Next next) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
@@ -297,7 +309,7 @@ __device__ __forceinline__ bool sort_tile(ScatterSmem<K> &S, int b, long long ti
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i >= items) break;
-        const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+        const unsigned d = (unsigned)(k[i] >> shift) & dmask;
         // The lanes holding the same digit: a hardware match costs about as much per distinct
         // value as a shared-memory OR costs per lane colliding on one digit, so the match serves
         // warps whose digits come in few runs (keys of one Gaussian, nearly sorted bytes) and the
@@ -339,9 +351,10 @@ __device__ __forceinline__ bool sort_tile(ScatterSmem<K> &S, int b, long long ti
         if (lane >= o) incl += y;
     }
     if (lane == 31) S.wsum[warp] = incl;
-    // the tile's count of valid items for digit tid (padding keys all have digit 255)
+    // the tile's count of valid items for digit tid (padding keys all have the largest digit, dmask,
+    // and rank after every valid key of that digit)
     const long long valid_here = min((long long)tsize, n - tbase);
-    const unsigned cnt_valid = tid == 255 ? cnt - (unsigned)(tsize - valid_here) : cnt;
+    const unsigned cnt_valid = tid == (int)dmask ? cnt - (unsigned)(tsize - valid_here) : cnt;
     publish(cnt_valid);
     __syncthreads();
     unsigned wex = 0;
@@ -354,7 +367,7 @@ __device__ __forceinline__ bool sort_tile(ScatterSmem<K> &S, int b, long long ti
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         if (i >= items) break;
-        const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+        const unsigned d = (unsigned)(k[i] >> shift) & dmask;
         const unsigned pos = S.local_off[d] + S.whist[warp][d] + ((rank[i >> 1] >> (16 * (i & 1))) & 0xffffu);
         S.keys[db][pos] = k[i];
         S.vals[db][pos] = v[i];
@@ -364,7 +377,7 @@ __device__ __forceinline__ bool sort_tile(ScatterSmem<K> &S, int b, long long ti
     __syncthreads();
     for (int s = tid; s < valid_here; s += kSortThreads) {
         const K key = S.keys[db][s];
-        const unsigned d = (unsigned)(key >> shift) & 0xffu;
+        const unsigned d = (unsigned)(key >> shift) & dmask;
         const unsigned long long dst = S.gbase[d] + (unsigned long long)(s - S.local_off[d]);
         kout[dst] = key;
         vout[dst] = S.vals[db][s];
@@ -387,18 +400,18 @@ __device__ __forceinline__ void onesweep_publish(unsigned long long *desc, long 
 
 __device__ __forceinline__ unsigned long long onesweep_resolve(unsigned long long *desc, unsigned long long *bdesc,
                                                                long long tile, unsigned long long tag, unsigned goff,
-                                                               unsigned cnt, FrameCounters *ctr) {
+                                                               unsigned cnt, FrameCounters *ctr, unsigned limit) {
     const int tid = threadIdx.x;
     unsigned excl = 0;
     if (tile > 0) {
         static_assert(kLookBlock <= kLookWindow, "one round trip covers a block");
         const long long blk = tile / kLookBlock, lo = blk * kLookBlock;
         const bool last_in_block = tile - lo == kLookBlock - 1;
-        int r = look_back(desc + tid, tile - 1, lo, tag, tile < gridDim.x ? kLookWindow : 1, excl, ctr);
+        int r = look_back(desc + tid, tile - 1, lo, tag, tile < gridDim.x ? kLookWindow : 1, excl, ctr, limit);
         if (r == 0 && blk > 0) {
             if (last_in_block)
                 *(volatile unsigned long long *)(bdesc + blk * 256 + tid) = tag | kDescAgg | (excl + cnt);
-            r = look_back(bdesc + tid, blk - 1, 0, tag, kLookWindow, excl, ctr);
+            r = look_back(bdesc + tid, blk - 1, 0, tag, kLookWindow, excl, ctr, limit);
         }
         (void)r;   // a timeout has flagged the status; the pass's output is then void
         *(volatile unsigned long long *)(desc + tile * 256 + tid) = tag | kDescPrefix | (excl + cnt);
@@ -433,10 +446,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
                                                                const unsigned long long *n_dev, long long n_host,
                                                                long long cap, int pass, const unsigned *offs,
                                                                unsigned long long *desc, unsigned long long *bdesc,
-                                                               FrameCounters *ctr, int bulk_ok) {
+                                                               FrameCounters *ctr, int bulk_ok, unsigned limit,
+                                                               unsigned dmask) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int tid = threadIdx.x;
+    // an earlier pass gave up waiting: its output is incomplete and this pass's digit offsets
+    // (from the first histogram) no longer match it -- write nothing (status already flagged)
+    if (__syncthreads_or(tid == 0 && upstream_timed_out(ctr))) return;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
     const long long nfull = n / kSortTile;
@@ -467,9 +484,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const K *__res
         // once this tile has published its prefix, take the next ticket, so its copy overlaps
         // the writes while no later tile waits on a ticket that is not being worked on
         if (!sort_tile(
-                S, b, tile, kin, vin, kout, vout, n, kSortItems, 8 * pass, ctr, phases,
+                S, b, tile, kin, vin, kout, vout, n, kSortItems, 8 * pass, dmask, ctr, phases,
                 [&](unsigned c) { onesweep_publish(desc, tile, tag, c); },
-                [&](unsigned c) { return onesweep_resolve(desc, bdesc, tile, tag, goff, c, ctr); },
+                [&](unsigned c) { return onesweep_resolve(desc, bdesc, tile, tag, goff, c, ctr, limit); },
                 [&] { fetch(b ^ 1); })) {
             drain_staging(S, phases);
             return;
@@ -498,9 +515,9 @@ static int scatter_grid() {
 // Grid-wide barrier of a cooperative launch (every CTA resident) on a counter that starts at zero
 // and serves this one barrier: after a CTA-wide barrier one thread makes the CTA's writes visible,
 // adds its arrival without waiting for the result, and polls until every CTA has arrived.
-// Bounded: false after kSpinLimit polls, or as soon as another CTA has flagged a timeout (the
+// Bounded: false after `limit` polls, or as soon as another CTA has flagged a timeout (the
 // status then carries kStTimeout).
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned ncta, FrameCounters *ctr) {
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned ncta, FrameCounters *ctr, unsigned limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -509,7 +526,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned ncta, Fra
         atomicAdd(count, 1u);
         unsigned it = 0;
         while (*(volatile unsigned *)count < ncta) {
-            if (++it > kSpinLimit || (*(volatile unsigned *)&ctr->status & kStTimeout)) {
+            if (++it > limit || (*(volatile unsigned *)&ctr->status & kStTimeout)) {
                 atomicOr(&ctr->status, kStTimeout);
                 ok = 0;
                 break;
@@ -544,11 +561,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_fused(K *k0, unsigned 
                                                              const unsigned long long *n_dev, long long n_host,
                                                              long long cap, int passes, unsigned *hist,
                                                              unsigned long long *desc, unsigned long long *bdesc,
-                                                             FrameCounters *ctr, unsigned *bars, int bulk_ok) {
+                                                             FrameCounters *ctr, unsigned *bars, int bulk_ok,
+                                                             unsigned limit, unsigned top_mask) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FusedSmem<K> &F = *reinterpret_cast<FusedSmem<K> *>(smem_raw);
     ScatterSmem<K> &S = F.s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // an earlier sort of the frame gave up waiting: its output (this sort's input) is incomplete
+    if (__syncthreads_or(tid == 0 && upstream_timed_out(ctr))) return;
     const long long n = pair_count(n_dev, n_host, cap);
     // items per thread: the fewest (>= kSortItems) that give every CTA at most one tile, if any do
     int items = kSortItems;
@@ -569,12 +589,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_fused(K *k0, unsigned 
     static_assert(sizeof(S.whist) >= 8 * 256 * sizeof(unsigned), "histograms of 8 passes fit the warp counters");
     for (int i = tid; i < passes * 256; i += kSortThreads) s_h[i] = 0;
     __syncthreads();
-    hist_accumulate((const K *)k0, n, passes, s_h, (long long)blockIdx.x * kSortThreads + tid,
+    hist_accumulate((const K *)k0, n, passes, top_mask, s_h, (long long)blockIdx.x * kSortThreads + tid,
                     (long long)gridDim.x * kSortThreads);
     __syncthreads();
     for (int i = tid; i < passes * 256; i += kSortThreads)
         if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
-    if (!grid_barrier(&bars[0], gridDim.x, ctr)) failed = true;
+    if (!grid_barrier(&bars[0], gridDim.x, ctr, limit)) failed = true;
     if (!failed && blockIdx.x == 0 && tid == 0) atomicMax(&ctr->sort_epoch, epoch);
     unsigned hc[8];
 #pragma unroll
@@ -618,9 +638,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_fused(K *k0, unsigned 
             __syncthreads();
             const long long nxt = tile + gridDim.x;
             if (!sort_tile(
-                    S, b, tile, kin, vin, kout, vout, n, items, 8 * pass, ctr, phases,
+                    S, b, tile, kin, vin, kout, vout, n, items, 8 * pass, digit_mask(pass, passes, top_mask), ctr,
+                    phases,
                     [&](unsigned c) { onesweep_publish(desc, tile, tag, c); },
-                    [&](unsigned c) { return onesweep_resolve(desc, bdesc, tile, tag, goff, c, ctr); },
+                    [&](unsigned c) { return onesweep_resolve(desc, bdesc, tile, tag, goff, c, ctr, limit); },
                     [&] {
                         if (tid == 0 && nxt < ntiles) stage_tile(S, b ^ 1, nxt, tsize, kin, vin, nfull, bulk_ok);
                     })) {
@@ -630,7 +651,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_fused(K *k0, unsigned 
             tile = nxt;
             b ^= 1;
         }
-        if (!failed && pass + 1 < passes && !grid_barrier(&bars[pass + 1], gridDim.x, ctr)) failed = true;
+        if (!failed && pass + 1 < passes && !grid_barrier(&bars[pass + 1], gridDim.x, ctr, limit)) failed = true;
     }
     if (failed) {
         // Some CTAs may have tagged descriptors with this epoch while others gave up before it
@@ -675,9 +696,11 @@ constexpr int kCountGroup = 8;
 template <class K>
 __global__ void __launch_bounds__(kSortThreads) k_rts_count(const K *__restrict__ kin, const unsigned long long *n_dev,
                                                             long long n_host, long long cap, int pass,
-                                                            unsigned *counts, long long stride) {
+                                                            unsigned *counts, long long stride,
+                                                            const FrameCounters *ctr, unsigned dmask) {
     __shared__ unsigned s_h[kCountGroup][256];
     const int tid = threadIdx.x;
+    if (upstream_timed_out(ctr)) return;    // the frame's depth sort gave up: nothing valid to count
     const int shift = 8 * pass;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
@@ -705,7 +728,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rts_count(const K *__restrict_
             const long long base = (t0 + j) * kSortTile;
 #pragma unroll
             for (int i = 0; i < kSortItems; ++i)
-                if (base + i * kSortThreads + tid < n) atomicAdd(&s_h[j][(unsigned)(cur[i] >> shift) & 0xffu], 1u);
+                if (base + i * kSortThreads + tid < n) atomicAdd(&s_h[j][(unsigned)(cur[i] >> shift) & dmask], 1u);
         }
         __syncthreads();
         uint4 *dst = reinterpret_cast<uint4 *>(counts + (long long)tid * stride + t0);
@@ -785,10 +808,11 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__rest
                                                               const unsigned long long *n_dev, long long n_host,
                                                               long long cap, int pass, const unsigned *offs_t,
                                                               long long stride, const unsigned *tot,
-                                                              int bulk_ok, FrameCounters *ctr) {
+                                                              int bulk_ok, FrameCounters *ctr, unsigned dmask) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (__syncthreads_or(tid == 0 && upstream_timed_out(ctr))) return;
     const long long n = pair_count(n_dev, n_host, cap);
     const long long ntiles = (n + kSortTile - 1) / kSortTile;
     const long long nfull = n / kSortTile;
@@ -824,7 +848,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_rts_scatter(const K *__rest
         // the other buffer was released at the end of the last tile
         if (tid == 0 && tile + gridDim.x < ntiles)
             stage_tile(S, b ^ 1, tile + gridDim.x, kSortTile, kin, vin, nfull, bulk_ok);
-        if (!sort_tile(S, b, tile, kin, vin, kout, vout, n, kSortItems, 8 * pass, ctr, phases, [](unsigned) {},
+        if (!sort_tile(S, b, tile, kin, vin, kout, vout, n, kSortItems, 8 * pass, dmask, ctr, phases, [](unsigned) {},
                        [&](unsigned) { return gb; }, [] {})) {
             drain_staging(S, phases);
             return;
@@ -854,6 +878,10 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
                          cudaStream_t s) {
     const int passes = (end_bit + 7) / 8;
     const int sgrid = scatter_grid<K>();
+    const unsigned limit = wait_limit();
+    // the last digit covers bits [8 (passes - 1), end_bit) only
+    const unsigned top_mask = (1u << (end_bit - 8 * (passes - 1))) - 1u;
+    auto dmask_of = [&](int p) { return p == passes - 1 ? top_mask : 0xffu; };
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -868,11 +896,13 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
         unsigned *va = vals, *vb = vals_tmp;
         const long long stride = rts_stride(scr.max_tiles);
         for (int p = 0; p < passes; ++p) {
-            k_rts_count<K><<<cgrid, kSortThreads, 0, s>>>(ka, n_dev, n_host, cap, p, scr.counts, stride);
+            k_rts_count<K><<<cgrid, kSortThreads, 0, s>>>(ka, n_dev, n_host, cap, p, scr.counts, stride, ctr,
+                                                          dmask_of(p));
             k_rts_scan<<<256, kRtsScanThreads, 0, s>>>(scr.counts, stride, n_dev, n_host, cap, scr.offs + p * 256);
             k_rts_scatter<K><<<rgrid, kSortThreads, sizeof(ScatterSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
                                                                                scr.counts, stride,
-                                                                               scr.offs + p * 256, bulk_ok, ctr);
+                                                                               scr.offs + p * 256, bulk_ok, ctr,
+                                                                               dmask_of(p));
             K *tk = ka;
             ka = kb;
             kb = tk;
@@ -896,13 +926,13 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
         const cudaError_t e = cudaLaunchKernelEx(&cfg, k_sort_fused<K>, keys, vals, keys_tmp, vals_tmp, n_dev, n_host,
                                                  cap, passes, scr.hist, scr.desc, scr.desc + scr.max_tiles * 256, ctr,
                                                  (unsigned *)((char *)ctr + offsetof(FrameCounters, sort_bar)),
-                                                 bulk_ok);
+                                                 bulk_ok, limit, top_mask);
         if (e == cudaSuccess) return passes;
         // a cooperative launch refused (e.g. by a device or mode that does not allow it): the
         // error is not sticky, so clear it and run the per-pass form below instead
         cudaGetLastError();
     }
-    k_sort_hist<K><<<sms * 2, 512, 0, s>>>(keys, n_dev, n_host, cap, passes, scr.hist);
+    k_sort_hist<K><<<sms * 2, 512, 0, s>>>(keys, n_dev, n_host, cap, passes, top_mask, scr.hist);
     k_sort_offsets<<<passes, 256, 0, s>>>(scr.hist, scr.offs, ctr);
     int grid = (int)min((long long)sgrid, max_tiles > 0 ? max_tiles : 1);
     K *ka = keys, *kb = keys_tmp;
@@ -911,7 +941,7 @@ static int launch_sort_t(K *keys, unsigned *vals, K *keys_tmp, unsigned *vals_tm
         k_sort_scatter<K><<<grid, kSortThreads, sizeof(ScatterSmem<K>), s>>>(ka, va, kb, vb, n_dev, n_host, cap, p,
                                                                              scr.offs, scr.desc,
                                                                              scr.desc + scr.max_tiles * 256, ctr,
-                                                                             bulk_ok);
+                                                                             bulk_ok, limit, dmask_of(p));
         K *tk = ka;
         ka = kb;
         kb = tk;
@@ -944,7 +974,8 @@ int launch_sort32(unsigned *keys, unsigned *vals, unsigned *keys_tmp, unsigned *
 constexpr long long kScanPairsPerTile = 512;
 template <class K, int SHIFT>
 __global__ void __launch_bounds__(256) k_tile_starts(const K *keys, const unsigned long long *n_dev, long long cap,
-                                                     int ntiles, unsigned *starts) {
+                                                     int ntiles, unsigned *starts, const FrameCounters *ctr) {
+    if (upstream_timed_out(ctr)) return;    // the sort gave up: its keys may name tiles out of range
     const long long n = pair_count(n_dev, 0, cap);
     const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -982,13 +1013,13 @@ static int ranges_grid() {
 }
 
 void launch_ranges(const unsigned long long *keys, const unsigned long long *n_dev, long long cap, int ntiles,
-                   unsigned *starts, cudaStream_t s) {
-    k_tile_starts<unsigned long long, 32><<<ranges_grid(), 256, 0, s>>>(keys, n_dev, cap, ntiles, starts);
+                   unsigned *starts, const FrameCounters *ctr, cudaStream_t s) {
+    k_tile_starts<unsigned long long, 32><<<ranges_grid(), 256, 0, s>>>(keys, n_dev, cap, ntiles, starts, ctr);
 }
 
 void launch_ranges32(const unsigned *keys, const unsigned long long *n_dev, long long cap, int ntiles,
-                     unsigned *starts, cudaStream_t s) {
-    k_tile_starts<unsigned, 0><<<ranges_grid(), 256, 0, s>>>(keys, n_dev, cap, ntiles, starts);
+                     unsigned *starts, const FrameCounters *ctr, cudaStream_t s) {
+    k_tile_starts<unsigned, 0><<<ranges_grid(), 256, 0, s>>>(keys, n_dev, cap, ntiles, starts, ctr);
 }
 
 }  // namespace gs
