@@ -173,6 +173,39 @@ def pair_capacity(name, P=None):
     return min(full, 1 << max(21, math.ceil(math.log2(16 * P))))
 
 
+L2_BYTES = 126 * (1 << 20)          # GB300 L2 (about 126 MiB usable)
+L2_NOTE = "GPU arm: a 256 MiB write flushes L2 before every step (host arm: not applicable)"
+
+
+def bench_config(desc, ncam, ws):
+    """The `config` object of the JSON line -- the same for both arms, so that the driver compares
+    like with like."""
+    return {"workload": desc, "camera_cycle": ncam, "parallelism": f"replicas x{ws}", "l2": L2_NOTE}
+
+
+def host_info():
+    """Host cores (nproc) and CPU model of the machine running the oracle."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown", "machine": platform.machine()}
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -230,10 +263,11 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1000 * dt / n, "higher_is_better": True, "frames_timed": n,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": desc, "camera_cycle": len(cams)},
-            "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{n} of the {args.steps} requested steps timed (cap {cap_s:.0f} s), "
-                                       "each one full frame of the workload on the host cores"},
+            "config": bench_config(desc, len(cams), ws),
+            "cpu_baseline": dict({"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"{n} of the {args.steps} requested steps timed (cap {cap_s:.0f} s), "
+                                            "each one full frame of the workload on the host cores"},
+                                 **host_info()),
             "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -249,9 +283,20 @@ def cpu_baseline(args, scene, cams):
         if time.perf_counter() - t0 >= args.cpu_seconds or n >= len(cams):
             break
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} full frame(s) (cameras 0..{n - 1}) of the workload, oracle binary32 mode, "
-                      f"OpenMP over tiles, {dt:.1f} s"}
+    return dict({"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                 "sample": f"{n} full frame(s) (cameras 0..{n - 1}) of the workload, oracle binary32 mode, "
+                           f"OpenMP over tiles, {dt:.1f} s"}, **host_info())
+
+
+def cpu_baseline_city(city_scene, city_cams):
+    """The oracle on one camera of the city 10M @3840x2160 workload (its frames take seconds each)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.render(city_scene, city_cams[0], mode=32)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "frames/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"1 full frame (camera 0, {r['N']} pairs) of the city 10M @3840x2160 workload, "
+                      f"oracle binary32 mode, {dt:.1f} s"}
 
 
 # ------------------------------------------------------------------------------------ serving
@@ -484,14 +529,25 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
     else:
         alu_peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T lane-ops/s
         alu_src = f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz median SM clock sampled in this run"
-    pre_bytes = 16 * P + 32 * Pc + 192 * V + 48 * V + 12 * N
-    if tuning.get("sort_mode", 0) == 1:
+    two_level = tuning.get("sort_mode", 0) == 1
+    pair_bytes = 8 if two_level else 12          # (32-bit tile key or 64-bit key) + 32-bit id per pair
+    pre_bytes = 16 * P + 32 * Pc + 192 * V + 48 * V + pair_bytes * N
+    if two_level:
         sort_bytes = 4 * N + passes * 16 * N + V * (4 + 4 * 16)     # tile sort (32-bit keys) + depth sort
+        sort_set = 16 * N                                            # key + id, both ping-pong buffers
     else:
         sort_bytes = 8 * N + passes * 24 * N
+        sort_set = 24 * N
+    sort_l2 = sort_set < L2_BYTES
     ntiles = ((W + 15) // 16) * ((H + 15) // 16)
-    # one read of the sorted keys and the (start, end) words of every tile
-    ranges_bytes = (4 if tuning.get("sort_mode", 0) == 1 else 8) * N + 8 * ntiles
+    key_bytes = 4 if two_level else 8
+    ranges_scan = ntiles <= N <= 512 * ntiles       # the library's choice between its two forms
+    if ranges_scan:
+        # one read of the sorted keys and the start word of every tile
+        ranges_bytes = key_bytes * N + 4 * (ntiles + 1)
+    else:
+        # a binary search per tile: ceil(log2(N + 1)) dependent probes, each one 32-byte sector
+        ranges_bytes = (ntiles + 1) * max(1, math.ceil(math.log2(N + 1))) * 32
     blend_ops = E * BLEND_OPS_PER_EVAL
     ex2_peak = (alu or {}).get("ex2_tops")
     if ex2_peak:
@@ -501,19 +557,26 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
     per_stage = {
         "preprocess": {"ms": stage_ms[0], "bound": "hbm", "achieved": pre_bytes / (stage_ms[0] * 1e-3) / 1e9,
                        "peak": hbm_peak, "unit": "GB/s"},
-        "sort": {"ms": stage_ms[1], "bound": "hbm", "achieved": sort_bytes / (stage_ms[1] * 1e-3) / 1e9,
-                 "peak": hbm_peak, "unit": "GB/s"},
-        "ranges": {"ms": stage_ms[2], "bound": "hbm", "achieved": ranges_bytes / (stage_ms[2] * 1e-3) / 1e9,
-                   "peak": hbm_peak, "unit": "GB/s"},
+        "sort": {"ms": stage_ms[1], "bound": "latency (L2-resident)" if sort_l2 else "hbm",
+                 "achieved": sort_bytes / (stage_ms[1] * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                 "l2_resident": sort_l2},
+        "ranges": {"ms": stage_ms[2], "bound": "hbm" if ranges_scan else "latency (binary search per tile)",
+                   "achieved": ranges_bytes / (stage_ms[2] * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                   "form": "one pass over the keys" if ranges_scan else "binary search per tile, 32 B per probe"},
         "blend": ({"ms": stage_ms[3], "bound": "alu", "achieved": E / (stage_ms[3] * 1e-3) / 1e12,
                    "peak": ex2_peak, "unit": "T ex2/s"} if mufu_bound else
                   {"ms": stage_ms[3], "bound": "alu", "achieved": blend_ops / (stage_ms[3] * 1e-3) / 1e12,
                    "peak": alu_peak, "unit": "TOP/s"}),
     }
-    for v in per_stage.values():
+    for name, v in per_stage.items():
         v["frac"] = v["achieved"] / v["peak"]
         for k in ("ms", "achieved", "frac"):
             v[k] = round(v[k], 4)
+        # DRAM bytes per launch of the stage's main kernel, from the recorded ncu capture (null when
+        # its sources or launch shape changed since)
+        tr = traffic_for(config, name, tuning) if config else None
+        if tr is not None:
+            v["traffic"] = tr
     per_stage["blend"]["frac_contributing"] = round(
         Ec * BLEND_OPS_PER_CONTRIB / (stage_ms[3] * 1e-3) / 1e12 / alu_peak, 4)
     dom = max(per_stage, key=lambda k: per_stage[k]["ms"])
@@ -524,9 +587,10 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
     kernel = {"preprocess": "k_pre_count + k_pre_emit (+ depth order: k_sort_fused, k_emit_mid, k_emit_big)",
               "sort": sort_kernels, "ranges": "k_tile_starts",
               "blend": f"k_blend<variant {tuning.get('blend_variant')}>"}[dom]
-    algo = {"preprocess": "16P + 32 P_culled_in + 240 V + 12 N bytes",
+    algo = {"preprocess": "16P + 32 P_culled_in + 240 V + 12 N (8 N two-level) bytes",
             "sort": "8N + 24N per pass (64-bit keys) / 4N + 16N per pass + 68V (two-level)",
-            "ranges": "8N (4N for 32-bit keys) + 8 x tiles bytes",
+            "ranges": "8N (4N for 32-bit keys) + 4 x (tiles + 1) bytes, or (tiles + 1) x ceil(log2(N+1)) x 32 B "
+                      "for the binary search",
             "blend": f"{BLEND_OPS_PER_EVAL} FP32 ops (+1 ex2) x evaluations, E = {E:.4g} (pixel, entry) pairs "
                      f"evaluated per frame before early stop, as the oracle counts them; of these E_c = {Ec:.4g} "
                      f"contribute (frac_contributing: {BLEND_OPS_PER_CONTRIB} ops x E_c)"}[dom]
@@ -537,6 +601,8 @@ def time_frames(gs, ctx, dev_scene, P, cams, steps, warmup, stream, flush, cap, 
                 "algorithmic": algo}
     if "frac_contributing" in d:
         roofline["frac_contributing"] = d["frac_contributing"]
+    # every stage of this workload, compact (the dominant one is the object above)
+    roofline["stages"] = {k: {"ms": v["ms"], "bound": v["bound"], "frac": v["frac"]} for k, v in per_stage.items()}
     res = {"frames": K, "ms_total": tot_ms, "frames_per_s": K / (tot_ms / 1000.0), "ms_per_frame": tot_ms / K,
            "ms_median": med_ms, "frames_per_s_median": 1000.0 / med_ms,
            "wall_s": wall, "clocks": clocks, "gpu_launches": kernels, "tuning": tuning, "roofline": roofline,
@@ -707,6 +773,14 @@ def run_ours(args):
             cfr.close()
             city_res = dict(workload="city-scale 10M Gaussians @3840x2160, 16 aerial + 16 street cameras "
                                      "(synthetic, seed 2)", **res)
+            # the metric's second half, inside the object the driver keeps
+            main["roofline"]["city_4k"] = {"frames_per_s": round(res["frames_per_s"], 2),
+                                           "ms_per_frame": round(res["ms_per_frame"], 4),
+                                           "pairs_per_frame": round(res["frame"]["pairs"]),
+                                           "dominant": res["roofline"]["stage"],
+                                           "stages": res["roofline"]["stages"]}
+            if cpu is not None:
+                cpu["city_4k"] = cpu_baseline_city(city_scene, city_cams)
             if study is not None:
                 study["city"] = pair_study(gs, ctx, city, city_scene.P, city_cams, pair_capacity("city"), stream,
                                            flush, res["tuning"])
@@ -718,17 +792,18 @@ def run_ours(args):
         serving = run_serving(args, gs, ctx, scene, cams, city, city_cams)
 
     if rank == 0:
+        # the driver keeps the contract's keys; the rest follows, the serving comparison last (it is
+        # what the tail of the line shows)
         line = {"metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": desc, "l2": "flushed (256 MiB write) before every step",
-                           "camera_cycle": len(cams), "graph": True, "parallelism": f"replicas x{ws}",
-                           "tuning": main["tuning"]},
-                "clocks": main["clocks"], "gpu_launches": main["gpu_launches"], "alu_peaks": alu,
-                "roofline": main["roofline"], "stages": main["stages"], "frame": main["frame"],
-                "wall_s": main["wall_s"], "e2e": e2e, "cpu_baseline": cpu, "city_4k": city_res,
-                "serving": serving, "differentiable": training, "pair_study": study,
-                "reduced_precision": reduced}
+                "config": bench_config(desc, len(cams), ws),
+                "clocks": main["clocks"], "gpu_launches": main["gpu_launches"],
+                "roofline": main["roofline"], "e2e": e2e, "cpu_baseline": cpu,
+                "run": {"graph": True, "tuning": main["tuning"], "wall_s": main["wall_s"]},
+                "alu_peaks": alu, "stages": main["stages"], "frame": main["frame"],
+                "pair_study": study, "reduced_precision": reduced, "city_4k": city_res,
+                "differentiable": training, "serving": serving}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
