@@ -123,13 +123,14 @@ struct Geom {
     int tx0, tx1, ty0, ty1;
 };
 
-// Cull, project and build the conic of one Gaussian; false if it is culled or has no
-// candidate tile.  Binary32 evaluation order of the definition (see the header).
-__device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long gid, const Cam &cam,
-                                                  const Opts &o, Geom &G, bool &passed_cull) {
+// Phase 1 of a Gaussian's geometry, run by every thread of the count pass: the cull (Alg. 4: z >
+// near, opacity > tau) and a conservative off-screen bound.  Returns true when the Gaussian may
+// have a candidate tile; p (camera-space mean) and alpha0 are left for phase 2.  Binary32
+// evaluation order of the definition (see the header).
+__device__ __forceinline__ bool cull_and_bound(const SceneView &S, long long gid, const Cam &cam, const Opts &o,
+                                               float p[3], float &alpha0, bool &passed_cull) {
     const float4 po = __ldg(S.pos_opa + gid);
     const float *R = cam.R;
-    float p[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         float s = fmul(R[3 * i], po.x);
@@ -137,53 +138,59 @@ __device__ __forceinline__ bool gaussian_geometry(const SceneView &S, long long 
         s = fadd(s, fmul(R[3 * i + 2], po.z));
         p[i] = fadd(s, cam.t[i]);
     }
-    float alpha0 = S.activated ? po.w : sigmoid_rn(po.w);
+    alpha0 = S.activated ? po.w : sigmoid_rn(po.w);
     if (!(p[2] > cam.near_z)) return false;
     if (!(alpha0 > o.tau)) return false;
     passed_cull = true;
     const float4 sc = __ldg(rs_of(S, gid));
-    {
-        // Conservative screen-extent test, before any exact arithmetic of the covariance.
-        // Sigma <= s_max^2 I, so Sigma'00 <= s_max^2 |M0|^2 + dilation (M0 = first row of J W) and
-        // {q <= t} lies within u +- sqrt(t Sigma'00).  Every factor here is an upper estimate from
-        // the fast approximate unit (relative errors near 1e-6), padded by 2% and two pixels: a
-        // Gaussian whose bound misses the image can have no candidate tile, and skipping it
-        // changes no result.  (NaN bounds compare false and keep the Gaussian.)
-        float tb = 2.0f * __logf(__fdividef(alpha0, o.tau)) * 1.01f + 0.01f;
-        if (o.cap_3sigma && tb > 9.01f) tb = 9.01f;
-        const float sraw = fmaxf(fmaxf(sc.x, sc.y), sc.z);
-        const float smax = S.activated ? sraw : __expf(sraw) * 1.01f;
-        const float iz = __fdividef(1.0f, p[2]);
-        float rx = p[0] * iz, ry = p[1] * iz;
-        if (o.clamp_fov) {
-            rx = fminf(fmaxf(rx, -cam.limx), cam.limx);
-            ry = fminf(fmaxf(ry, -cam.limy), cam.limy);
-        }
-        const float a00 = cam.fx * iz, a02 = -cam.fx * rx * iz;
-        const float a11 = cam.fy * iz, a12 = -cam.fy * ry * iz;
-        float m0 = 0.0f, m1 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float e0 = a00 * R[k] + a02 * R[6 + k];
-            const float e1 = a11 * R[3 + k] + a12 * R[6 + k];
-            m0 += e0 * e0;
-            m1 += e1 * e1;
-        }
-        const float x2 = tb * (smax * smax * m0 + o.dilation), y2 = tb * (smax * smax * m1 + o.dilation);
-        float hxb = (x2 > 0.0f ? x2 * rsqrtf(x2) : 0.0f) * 1.02f + 2.0f;
-        float hyb = (y2 > 0.0f ? y2 * rsqrtf(y2) : 0.0f) * 1.02f + 2.0f;
-        if (o.intersect == 1) {
-            // 3DGS square: r <= ceil(3 sqrt(trace Sigma')), trace <= s_max^2 (|M0|^2 + |M1|^2) + 2 dilation
-            const float r2 = smax * smax * (m0 + m1) + 2.0f * o.dilation;
-            const float rb = 3.0f * (r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f) * 1.02f + 3.0f;
-            hxb = rb;
-            hyb = rb;
-        }
-        const float uu = cam.fx * p[0] * iz + cam.cx, vv = cam.fy * p[1] * iz + cam.cy;
-        if (uu + hxb < 0.0f || uu - hxb >= (float)(kTile * cam.tiles_x) || vv + hyb < 0.0f ||
-            vv - hyb >= (float)(kTile * cam.tiles_y))
-            return false;
+    // Conservative screen-extent test, before any exact arithmetic of the covariance.
+    // Sigma <= s_max^2 I, so Sigma'00 <= s_max^2 |M0|^2 + dilation (M0 = first row of J W) and
+    // {q <= t} lies within u +- sqrt(t Sigma'00).  Every factor here is an upper estimate from
+    // the fast approximate unit (relative errors near 1e-6), padded by 2% and two pixels: a
+    // Gaussian whose bound misses the image can have no candidate tile, and skipping it
+    // changes no result.  (NaN bounds compare false and keep the Gaussian.)
+    float tb = 2.0f * __logf(__fdividef(alpha0, o.tau)) * 1.01f + 0.01f;
+    if (o.cap_3sigma && tb > 9.01f) tb = 9.01f;
+    const float sraw = fmaxf(fmaxf(sc.x, sc.y), sc.z);
+    const float smax = S.activated ? sraw : __expf(sraw) * 1.01f;
+    const float iz = __fdividef(1.0f, p[2]);
+    float rx = p[0] * iz, ry = p[1] * iz;
+    if (o.clamp_fov) {
+        rx = fminf(fmaxf(rx, -cam.limx), cam.limx);
+        ry = fminf(fmaxf(ry, -cam.limy), cam.limy);
     }
+    const float a00 = cam.fx * iz, a02 = -cam.fx * rx * iz;
+    const float a11 = cam.fy * iz, a12 = -cam.fy * ry * iz;
+    float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float e0 = a00 * R[k] + a02 * R[6 + k];
+        const float e1 = a11 * R[3 + k] + a12 * R[6 + k];
+        m0 += e0 * e0;
+        m1 += e1 * e1;
+    }
+    const float x2 = tb * (smax * smax * m0 + o.dilation), y2 = tb * (smax * smax * m1 + o.dilation);
+    float hxb = (x2 > 0.0f ? x2 * rsqrtf(x2) : 0.0f) * 1.02f + 2.0f;
+    float hyb = (y2 > 0.0f ? y2 * rsqrtf(y2) : 0.0f) * 1.02f + 2.0f;
+    if (o.intersect == 1) {
+        // 3DGS square: r <= ceil(3 sqrt(trace Sigma')), trace <= s_max^2 (|M0|^2 + |M1|^2) + 2 dilation
+        const float r2 = smax * smax * (m0 + m1) + 2.0f * o.dilation;
+        const float rb = 3.0f * (r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f) * 1.02f + 3.0f;
+        hxb = rb;
+        hyb = rb;
+    }
+    const float uu = cam.fx * p[0] * iz + cam.cx, vv = cam.fy * p[1] * iz + cam.cy;
+    return !(uu + hxb < 0.0f || uu - hxb >= (float)(kTile * cam.tiles_x) || vv + hyb < 0.0f ||
+             vv - hyb >= (float)(kTile * cam.tiles_y));
+}
+
+// Phase 2, run only for the Gaussians that passed phase 1 (compacted across the CTA): the exact
+// threshold, 3D covariance, EWA projection, conic and candidate tile box; false if the conic is
+// degenerate or the box is empty.
+__device__ __forceinline__ bool exact_geometry(const SceneView &S, long long gid, const Cam &cam, const Opts &o,
+                                               const float p[3], float alpha0, Geom &G) {
+    const float *R = cam.R;
+    const float4 sc = __ldg(rs_of(S, gid));
     // Eq. 3: alpha0 exp(-q/2) >= tau  <=>  q <= 2 ln(alpha0 / tau)
     const float t_full = threshold_t(alpha0, o.tau);
     float t = t_full;
@@ -445,144 +452,280 @@ __device__ __forceinline__ int block_scan_cand(PreSmem &S, int ncand) {
     return total;
 }
 
+// Shared state of the count pass.  The exact work is done on compact slots: slot k holds the k-th
+// Gaussian of the chunk (in id order) that passed the cull and the off-screen bound, so warps
+// running the exact geometry, the tile tests and the colour are full however sparse the
+// survivors are (a city frame keeps about one Gaussian in six of a chunk).
+struct CountSmem {
+    float u[kPreBlock], v[kPreBlock], a[kPreBlock], b[kPreBlock], c[kPreBlock], t[kPreBlock];
+    int tx0[kPreBlock], ty0[kPreBlock], w[kPreBlock];
+    int cstart[kPreBlock + 1];        // exclusive scan of the slots' unit counts
+    unsigned cnt[kPreBlock];          // pairs of each slot
+    float4 pa[kPreBlock];             // slot: camera-space mean and opacity from phase 1
+    float z[kPreBlock], gl[kPreBlock];    // slot: depth and log2(alpha0) (the record's G)
+    float2 hxy[kPreBlock];                // slot: half extents of the {q <= t} box
+    int h[kPreBlock];                     // slot: candidate rows
+    short sl[kPreBlock];              // slot -> Gaussian (thread) of the chunk
+    short slot_of[kPreBlock];         // Gaussian -> slot, -1 when it has none
+    unsigned wsum[kPreBlock / 32];
+    unsigned long long mbase;         // first hit-mask byte of the chunk
+};
+
+// Slot of unit `s` among the chunk's units: the last slot k with cstart[k] <= s.
+__device__ __forceinline__ Unit count_unit(const CountSmem &S, int s) {
+    int lo = 0, hi = kPreBlock - 1;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.cstart[mid] <= s)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    Unit U;
+    U.g = lo;
+    const int k = s - S.cstart[lo];
+    const int w = S.w[lo];
+    const int segs = (w + kSeg - 1) / kSeg;
+    const int dy = k / segs;
+    const int seg = k - dy * segs;
+    U.tx = S.tx0[lo] + seg * kSeg;
+    U.ty = S.ty0[lo] + dy;
+    U.n = min(kSeg, w - seg * kSeg);
+    return U;
+}
+
 // Pass 1: geometry, exact tests counted over all candidate tiles of the chunk (load-balanced),
 // render records of paired Gaussians, the chunk's pair count, and each paired Gaussian's
-// geometry for pass 3.
+// geometry for emission.  Phase 1 (cull and off-screen bound) runs on every thread; the survivors
+// are compacted into slots; phase 2 (exact geometry), the tile tests and the records run on slots.
 __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constant__ PreprocessArgs A) {
-    __shared__ PreSmem S;
-    const int tid = threadIdx.x;
+    __shared__ CountSmem S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long chunk = blockIdx.x;
     const int ri = req_of_chunk(A.B, chunk);
     const ReqDesc &R = A.B.r[ri];
-    const long long gid = (chunk - R.chunk0) * kPreBlock + tid;
-    const long long rec = R.rec0 + gid;
+    const long long g0 = (chunk - R.chunk0) * kPreBlock;     // first Gaussian of the chunk
     const Cam &cam = R.cam;
-    S.req[tid] = (unsigned char)ri;
 
-    Geom G;
-    bool valid = false, passed_cull = false;
-    if (gid < R.scene.P) valid = gaussian_geometry(R.scene, gid, cam, R.opt, G, passed_cull);
-    const unsigned n_in_block = (unsigned)__syncthreads_count(passed_cull);   // one atomic per CTA below
-    const int w = valid ? G.tx1 - G.tx0 + 1 : 0;
-    const int h = valid ? G.ty1 - G.ty0 + 1 : 0;
-    if (valid) {
-        S.u[tid] = G.u;
-        S.v[tid] = G.v;
-        S.a[tid] = G.a;
-        S.b[tid] = G.b;
-        S.c[tid] = G.c;
-        S.t[tid] = G.t;
-        S.tx0[tid] = G.tx0;
-        S.ty0[tid] = G.ty0;
+    // ---- phase 1 on every Gaussian, then compaction of the survivors (id order kept)
+    float p[3] = {0.f, 0.f, 0.f}, alpha0 = 0.f;
+    bool passed_cull = false, cand = false;
+    if (g0 + tid < R.scene.P) cand = cull_and_bound(R.scene, g0 + tid, cam, R.opt, p, alpha0, passed_cull);
+    const unsigned bal = __ballot_sync(0xffffffffu, cand);
+    if (lane == 0) S.wsum[warp] = __popc(bal);
+    const unsigned n_in_block = (unsigned)__syncthreads_count(passed_cull);
+    int before = 0, ns = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
+        const int x = (int)S.wsum[w2];
+        before += w2 < warp ? x : 0;
+        ns += x;
     }
-    S.w[tid] = w > 0 ? w : 1;
-    S.cnt[tid] = 0;
-    const int ctotal = block_scan_cand(S, valid ? units_of(w, h) : 0);
-    // one range of mask bytes per chunk (kept only while the area lasts)
-    if (tid == 0) S.mbase = ctotal > 0 ? atomicAdd(&A.ctr->mask_used, (unsigned long long)ctotal) : 0ull;
+    const int myslot = cand ? before + __popc(bal & ((1u << lane) - 1u)) : -1;
+    S.slot_of[tid] = (short)myslot;
+    if (cand) {
+        S.sl[myslot] = (short)tid;
+        S.pa[myslot] = make_float4(p[0], p[1], p[2], alpha0);
+    }
     __syncthreads();
+
+    // ---- phase 2 on slot tid; its geometry goes to shared memory (registers stay free for the tests)
+    int units = 0;
+    if (tid < ns) {
+        Geom G;
+        const float4 pa = S.pa[tid];
+        const float pp[3] = {pa.x, pa.y, pa.z};
+        if (exact_geometry(R.scene, g0 + S.sl[tid], cam, R.opt, pp, pa.w, G)) {
+            const int w = G.tx1 - G.tx0 + 1, h = G.ty1 - G.ty0 + 1;
+            S.u[tid] = G.u;
+            S.v[tid] = G.v;
+            S.a[tid] = G.a;
+            S.b[tid] = G.b;
+            S.c[tid] = G.c;
+            S.t[tid] = G.t;
+            S.tx0[tid] = G.tx0;
+            S.ty0[tid] = G.ty0;
+            S.w[tid] = w;
+            S.h[tid] = h;
+            S.z[tid] = G.z;
+            S.gl[tid] = log_rn(G.alpha0) * 1.4426950408889634f;     // log2(alpha0)
+            S.hxy[tid] = make_float2(G.hx, G.hy);
+            units = units_of(w, h);
+        }
+    }
+    if (units == 0) S.w[tid] = 1;
+    S.cnt[tid] = 0;
+    // block scan of the slots' units (uses wsum: every read of phase 1's counts is behind the barrier)
+    int ctotal;
+    {
+        int incl = units;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) S.wsum[warp] = (unsigned)incl;
+        __syncthreads();
+        int wex = 0;
+        ctotal = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
+            const int x = (int)S.wsum[w2];
+            wex += w2 < warp ? x : 0;
+            ctotal += x;
+        }
+        S.cstart[tid] = wex + incl - units;
+        if (tid == 0) {
+            S.cstart[kPreBlock] = ctotal;
+            // one range of mask bytes per chunk (kept only while the area lasts)
+            S.mbase = ctotal > 0 ? atomicAdd(&A.ctr->mask_used, (unsigned long long)ctotal) : 0ull;
+        }
+        __syncthreads();
+    }
     const bool keep = S.mbase + (unsigned long long)ctotal <= (unsigned long long)A.mask_cap;
 
+    // ---- exact tile tests, 256 units per step over all slots
+    const bool square = R.opt.intersect == 1;
     for (int base = 0; base < ctotal; base += kPreBlock) {
-        const int slot = base + tid;
-        if (slot < ctotal) {
-            const Unit U = unit_of(S, slot);
-            const unsigned m = unit_hits(S, A.B, U);
-            if (keep) A.masks[S.mbase + slot] = (unsigned char)m;
+        const int s = base + tid;
+        if (s < ctotal) {
+            const Unit U = count_unit(S, s);
+            const unsigned m = square ? (1u << U.n) - 1u
+                                      : run_hits(cam.W, cam.H, S.u[U.g], S.v[U.g], S.a[U.g], S.b[U.g], S.c[U.g],
+                                                 S.t[U.g], U.tx, U.n, U.ty);
+            if (keep) A.masks[S.mbase + s] = (unsigned char)m;
             if (m) atomicAdd(&S.cnt[U.g], (unsigned)__popc(m));
         }
     }
     __syncthreads();
+    const unsigned mine = S.cnt[tid];                  // pairs of slot tid (0 beyond ns)
     unsigned hits = 0;
-    block_excl(S, S.cnt[tid], &hits);
-    const bool vis = S.cnt[tid] != 0;
+    {
+        unsigned v = mine;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) S.wsum[warp] = v;
+    }
+    const bool vis = mine != 0;
     const unsigned nvis_block = (unsigned)__syncthreads_count(vis);
+#pragma unroll
+    for (int w2 = 0; w2 < kPreBlock / 32; ++w2) hits += S.wsum[w2];
     if (tid == 0) {
         A.chunk_hits[chunk] = hits;
         A.chunk_vis[chunk] = nvis_block;
         if (nvis_block) atomicAdd(&A.ctr->n_visible, nvis_block);
         if (n_in_block) atomicAdd(&A.ctr->n_culled_in, n_in_block);
     }
-    if (gid < R.scene.P) A.counts[rec] = S.cnt[tid];
+    // pairs of every Gaussian of the chunk (id order, coalesced)
+    if (g0 + tid < R.scene.P) {
+        const int k = S.slot_of[tid];
+        A.counts[R.rec0 + g0 + tid] = k >= 0 ? S.cnt[k] : 0u;
+    }
     if (vis) {
-        A.geo2[rec] = make_int4(G.tx0, G.ty0, w, h);
-        A.geo0[rec] = make_float4(G.u, G.v, G.a, G.b);
+        const long long gid = g0 + S.sl[tid];
+        const long long rec = R.rec0 + gid;
+        const float u = S.u[tid], v = S.v[tid], a = S.a[tid], b = S.b[tid], c = S.c[tid], t = S.t[tid];
+        A.geo2[rec] = make_int4(S.tx0[tid], S.ty0[tid], S.w[tid], S.h[tid]);
+        A.geo0[rec] = make_float4(u, v, a, b);
         const unsigned moff = keep ? (unsigned)(S.mbase + (unsigned long long)S.cstart[tid]) : kNoMasks;
-        A.geo1[rec] = make_float4(G.c, G.t, __uint_as_float(__float_as_uint(G.z)), __uint_as_float(moff));
+        A.geo1[rec] = make_float4(c, t, S.z[tid], __uint_as_float(moff));
         const float4 po = __ldg(R.scene.pos_opa + gid);
         float rgb[3];
         sh_colour(R.scene, gid, cam, po.x, po.y, po.z, rgb);
-        const float LOG2E = 1.4426950408889634f;
-        const float Gl = log_rn(G.alpha0) * LOG2E;
+        const float2 hxy = S.hxy[tid];
         Rec rc;
-        rc.r0 = make_float4(G.u, G.v, G.a, G.b + G.b);
-        rc.r1 = make_float4(G.c, G.t, Gl, rgb[0]);
-        rc.r2 = make_float4(rgb[1], rgb[2], G.hx + 1.0f, G.hy + 1.0f);
+        rc.r0 = make_float4(u, v, a, b + b);
+        rc.r1 = make_float4(c, t, S.gl[tid], rgb[0]);
+        rc.r2 = make_float4(rgb[1], rgb[2], hxy.x + 1.0f, hxy.y + 1.0f);
         A.recs[rec] = rc;
     }
 }
 
-// Exclusive scan of up to two arrays of chunk counts (one CTA; each thread sums a run of chunks).
-// Writes the totals to *tot_a / *tot_b.
-constexpr int kScanThreads = 1024;
-// Exclusive scan (64-bit sums) of n per-chunk counts, four per thread and 4096 per step (16-byte
-// loads and stores, coalesced), with a block scan of the threads' sums and a running carry.
+// Exclusive scans of chunk counts (one CTA of kScanThreads).  Each step covers kScanVec x
+// kScanThreads x 4 counts: every thread issues all kScanVec of its 16-byte loads (coalesced: load j
+// of thread i is uint4 j kScanThreads + i of the step) before any is summed, so one memory latency
+// covers the step; then one block scan of the per-thread sums of each load row, and coalesced
+// 16-byte stores of the 64-bit prefixes.  A city frame's 39k chunks take three steps.
+constexpr int kScanThreads = 512;
+constexpr int kScanVec = 8;
 __device__ void chunk_scan(const unsigned *in, unsigned long long *out, long long n, unsigned long long *total) {
-    __shared__ unsigned long long s_w[kScanThreads / 32];
+    __shared__ unsigned long long s_w[kScanVec][kScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n4 = (n + 3) / 4;
     unsigned long long carry = 0;
-    for (long long c0 = 0; c0 < n4; c0 += kScanThreads) {
-        const long long i = c0 + tid, e = 4 * i;
-        const bool whole = e + 3 < n;
-        unsigned x0 = 0, x1 = 0, x2 = 0, x3 = 0;
-        if (whole) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(in) + i);
-            x0 = v.x, x1 = v.y, x2 = v.z, x3 = v.w;
-        } else if (e < n) {
-            x0 = __ldg(in + e);
-            if (e + 1 < n) x1 = __ldg(in + e + 1);
-            if (e + 2 < n) x2 = __ldg(in + e + 2);
-        }
-        const unsigned long long sum = (unsigned long long)x0 + x1 + x2 + x3;
-        unsigned long long incl = sum;
+    for (long long c0 = 0; c0 < n4; c0 += (long long)kScanVec * kScanThreads) {
+        uint4 v[kScanVec];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_w[warp] = incl;
-        __syncthreads();
-        unsigned long long wex = 0, tot = 0;
-#pragma unroll
-        for (int w2 = 0; w2 < kScanThreads / 32; ++w2) {
-            const unsigned long long y = s_w[w2];
-            wex += w2 < warp ? y : 0ull;
-            tot += y;
-        }
-        if (out && e < n) {
-            const unsigned long long o0 = carry + wex + incl - sum, o1 = o0 + x0, o2 = o1 + x1, o3 = o2 + x2;
-            if (whole) {
-                reinterpret_cast<ulonglong2 *>(out)[2 * i] = make_ulonglong2(o0, o1);
-                reinterpret_cast<ulonglong2 *>(out)[2 * i + 1] = make_ulonglong2(o2, o3);
-            } else {
-                out[e] = o0;
-                if (e + 1 < n) out[e + 1] = o1;
-                if (e + 2 < n) out[e + 2] = o2;
+        for (int j = 0; j < kScanVec; ++j) {
+            const long long i = c0 + (long long)j * kScanThreads + tid, e = 4 * i;
+            v[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (e + 3 < n) {
+                v[j] = __ldcg(reinterpret_cast<const uint4 *>(in) + i);
+            } else if (e < n) {
+                v[j].x = __ldcg(in + e);
+                if (e + 1 < n) v[j].y = __ldcg(in + e + 1);
+                if (e + 2 < n) v[j].z = __ldcg(in + e + 2);
             }
         }
-        carry += tot;
+        unsigned long long incl[kScanVec], sum[kScanVec];
+#pragma unroll
+        for (int j = 0; j < kScanVec; ++j) {
+            sum[j] = (unsigned long long)v[j].x + v[j].y + v[j].z + v[j].w;
+            incl[j] = sum[j];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl[j], o);
+                if (lane >= o) incl[j] += y;
+            }
+            if (lane == 31) s_w[j][warp] = incl[j];
+        }
+        __syncthreads();
+        unsigned long long row_base = carry;
+#pragma unroll
+        for (int j = 0; j < kScanVec; ++j) {
+            unsigned long long wex = 0, tot = 0;
+#pragma unroll 8
+            for (int w2 = 0; w2 < kScanThreads / 32; ++w2) {
+                const unsigned long long y = s_w[j][w2];
+                wex += w2 < warp ? y : 0ull;
+                tot += y;
+            }
+            const long long i = c0 + (long long)j * kScanThreads + tid, e = 4 * i;
+            if (out && e < n) {
+                const unsigned long long o0 = row_base + wex + incl[j] - sum[j], o1 = o0 + v[j].x, o2 = o1 + v[j].y,
+                                         o3 = o2 + v[j].z;
+                if (e + 3 < n) {
+                    reinterpret_cast<ulonglong2 *>(out)[2 * i] = make_ulonglong2(o0, o1);
+                    reinterpret_cast<ulonglong2 *>(out)[2 * i + 1] = make_ulonglong2(o2, o3);
+                } else {
+                    out[e] = o0;
+                    if (e + 1 < n) out[e + 1] = o1;
+                    if (e + 2 < n) out[e + 2] = o2;
+                }
+            }
+            row_base += tot;
+        }
+        carry = row_base;
         __syncthreads();
     }
     if (tid == 0) *total = carry;
     __syncthreads();
 }
 
+// n_items (nullable, device): when given, array a holds counts of ceil(*n_items / kPreBlock) chunks
+// only (at most n), e.g. the rank chunks of the paired Gaussians.
 __global__ void __launch_bounds__(kScanThreads) k_chunk_scan(const unsigned *in_a, unsigned long long *out_a,
                                                              unsigned long long *tot_a, const unsigned *in_b,
                                                              unsigned long long *out_b, unsigned long long *tot_b,
-                                                             long long n, long long pair_cap, unsigned *status) {
-    chunk_scan(in_a, out_a, n, tot_a);
+                                                             long long n, long long pair_cap, unsigned *status,
+                                                             const unsigned long long *n_items) {
+    long long na = n;
+    if (n_items) {
+        const long long c = ((long long)*(const volatile unsigned long long *)n_items + kPreBlock - 1) / kPreBlock;
+        na = c < n ? c : n;
+    }
+    chunk_scan(in_a, out_a, na, tot_a);
     if (in_b) chunk_scan(in_b, out_b, n, tot_b);
     if (threadIdx.x == 0 && status && (long long)*tot_a > pair_cap) atomicOr(status, kStPairOverflow);
 }
@@ -590,41 +733,48 @@ __global__ void __launch_bounds__(kScanThreads) k_chunk_scan(const unsigned *in_
 // Two-level order, step 1: the paired Gaussians of each chunk, compacted in id order, as
 // (depth bits, id) for the depth sort.
 __global__ void __launch_bounds__(kPreBlock) k_vis_compact(const __grid_constant__ PreprocessArgs A) {
-    const long long chunk = blockIdx.x;
-    const ReqDesc &R = A.B.r[req_of_chunk(A.B, chunk)];
-    const long long gid = (chunk - R.chunk0) * kPreBlock + threadIdx.x;
-    const long long rec = R.rec0 + gid;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ unsigned s_w[kPreBlock / 32];
-    const bool vis = gid < R.scene.P && A.counts[rec] != 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, vis);
-    if (lane == 0) s_w[warp] = __popc(bal);
-    __syncthreads();
-    unsigned pre = 0;
-    for (int w2 = 0; w2 < warp; ++w2) pre += s_w[w2];
-    if (vis) {
-        const unsigned long long pos = A.vis_base[chunk] + pre + __popc(bal & ((1u << lane) - 1u));
-        A.dkey[pos] = __float_as_uint(A.geo1[rec].z);
-        A.dval[pos] = (unsigned)rec;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // a resident grid walks the chunks; chunks without paired Gaussians are skipped whole
+    for (long long chunk = blockIdx.x; chunk < A.n_chunks; chunk += gridDim.x) {
+        if (A.chunk_vis[chunk] == 0) continue;
+        const ReqDesc &R = A.B.r[req_of_chunk(A.B, chunk)];
+        const long long gid = (chunk - R.chunk0) * kPreBlock + threadIdx.x;
+        const long long rec = R.rec0 + gid;
+        const bool vis = gid < R.scene.P && A.counts[rec] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, vis);
+        if (lane == 0) s_w[warp] = __popc(bal);
+        __syncthreads();
+        unsigned pre = 0;
+        for (int w2 = 0; w2 < warp; ++w2) pre += s_w[w2];
+        if (vis) {
+            const unsigned long long pos = A.vis_base[chunk] + pre + __popc(bal & ((1u << lane) - 1u));
+            A.dkey[pos] = __float_as_uint(A.geo1[rec].z);
+            A.dval[pos] = (unsigned)rec;
+        }
+        __syncthreads();
     }
 }
 
 // Two-level order, step 2: pairs per chunk of 256 depth-sorted Gaussians.
 __global__ void __launch_bounds__(kPreBlock) k_emit_sum(const __grid_constant__ PreprocessArgs A) {
     if (upstream_timed_out(A.ctr)) return;   // the depth sort gave up: its ids may be garbage
-    const long long r = (long long)blockIdx.x * kPreBlock + threadIdx.x;
-    const long long V = (long long)A.ctr->n_vis64;
-    const unsigned c = r < V ? A.counts[A.dsorted[r]] : 0u;
-    unsigned v = c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __shared__ unsigned s_w[kPreBlock / 32];
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = 0;
-        for (int w2 = 0; w2 < kPreBlock / 32; ++w2) t += s_w[w2];
-        A.chunk_hits2[blockIdx.x] = t;
+    const long long V = (long long)A.ctr->n_vis64;
+    const long long nch = (V + kPreBlock - 1) / kPreBlock;
+    for (long long c = blockIdx.x; c < nch; c += gridDim.x) {
+        const long long r = c * kPreBlock + threadIdx.x;
+        unsigned v = r < V ? A.counts[A.dsorted[r]] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned t = 0;
+            for (int w2 = 0; w2 < kPreBlock / 32; ++w2) t += s_w[w2];
+            A.chunk_hits2[c] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -636,12 +786,9 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_sum(const __grid_constant__ 
 // order with the tile id alone as a 32-bit key -- a stable sort by tile then yields exactly the
 // (tile, depth, id) order of the 64-bit keys.
 template <bool DEPTH>
-__global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
-    __shared__ EmitSmem E;
+__device__ __forceinline__ void emit_chunk(const PreprocessArgs &A, EmitSmem &E, const long long chunk) {
     PreSmem &S = E.P;
-    if (DEPTH && upstream_timed_out(A.ctr)) return;   // the depth sort gave up: its ids may be garbage
     const int tid = threadIdx.x;
-    const long long chunk = blockIdx.x;
     long long gid;                    // here: the record index (request rec0 + Gaussian id)
     bool in_range;
     int ri;
@@ -781,6 +928,23 @@ __global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __g
     }
 }
 
+// DEPTH = false: one CTA per chunk of 256 Gaussians.  DEPTH = true: a resident grid walks the rank
+// chunks that hold paired Gaussians (ceil(V / 256) of them, V known only on the device).
+template <bool DEPTH>
+__global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __grid_constant__ PreprocessArgs A) {
+    __shared__ EmitSmem E;
+    if (!DEPTH) {
+        emit_chunk<false>(A, E, blockIdx.x);
+        return;
+    }
+    if (upstream_timed_out(A.ctr)) return;   // the depth sort gave up: its ids may be garbage
+    const long long V = (long long)A.ctr->n_vis64;
+    for (long long chunk = blockIdx.x; chunk * kPreBlock < V; chunk += gridDim.x) {
+        emit_chunk<true>(A, E, chunk);
+        __syncthreads();
+    }
+}
+
 // Depth order, medium Gaussians: one warp per Gaussian (warps take items in ticket order), its
 // units tested 32 at a time, hits staged per warp and written as coalesced runs from the
 // Gaussian's base.
@@ -915,6 +1079,18 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
     }
 }
 
+// k CTAs per SM of the current device.
+static int resident_grid(int k) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return k * sms;
+}
+
 void launch_pre_count(const PreprocessArgs &a, cudaStream_t s) {
     if (a.n_chunks <= 0) return;
     k_pre_count<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
@@ -924,7 +1100,7 @@ void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted) {
     if (a.n_chunks <= 0) return;
     if (!counted) k_pre_count<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
     k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, a.chunk_base, &a.ctr->n_pairs, nullptr, nullptr, nullptr,
-                                            a.n_chunks, a.pair_cap, &a.ctr->status);
+                                            a.n_chunks, a.pair_cap, &a.ctr->status, nullptr);
     k_pre_emit<false><<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
 }
 
@@ -932,8 +1108,8 @@ int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cud
     if (a.n_chunks <= 0) return 0;
     if (!counted) k_pre_count<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
     k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, nullptr, &a.ctr->n_pairs, a.chunk_vis, a.vis_base,
-                                            &a.ctr->n_vis64, a.n_chunks, a.pair_cap, &a.ctr->status);
-    k_vis_compact<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
+                                            &a.ctr->n_vis64, a.n_chunks, a.pair_cap, &a.ctr->status, nullptr);
+    k_vis_compact<<<(unsigned)min(a.n_chunks, (long long)resident_grid(8)), kPreBlock, 0, s>>>(a);
     // depth sort of the paired Gaussians: 32-bit float bits of z (positive, so bit order = value order)
     // (always the fused onesweep: a few hundred thousand to a few million keys, where its single
     // launch beats the per-pass forms; the frame's sort_algo applies to the pair sort)
@@ -944,20 +1120,14 @@ int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cud
     (void)dp;   // four passes: the result is back in dkey / dval
     // depth ranks run over all records of the batch: size the rank chunks by total_recs
     const long long rank_chunks = (a.B.total_recs + kPreBlock - 1) / kPreBlock;
-    k_emit_sum<<<(unsigned)rank_chunks, kPreBlock, 0, s>>>(a);
+    k_emit_sum<<<(unsigned)min(rank_chunks, (long long)resident_grid(8)), kPreBlock, 0, s>>>(a);
     unsigned long long *unused_total = &a.ctr->scratch64;
+    // only the rank chunks that hold paired Gaussians: ceil(V / 256) of them
     k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits2, a.chunk_base2, unused_total, nullptr, nullptr, nullptr,
-                                            rank_chunks, 1ll << 62, nullptr);
-    k_pre_emit<true><<<(unsigned)rank_chunks, kPreBlock, 0, s>>>(a);
-    static int big_grid = 0;
-    if (big_grid == 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        big_grid = 8 * sms;
-    }
-    k_emit_mid<<<big_grid, kPreBlock, 0, s>>>(a);
-    k_emit_big<<<big_grid, kPreBlock, 0, s>>>(a);
+                                            rank_chunks, 1ll << 62, nullptr, &a.ctr->n_vis64);
+    k_pre_emit<true><<<(unsigned)min(rank_chunks, (long long)resident_grid(4)), kPreBlock, 0, s>>>(a);
+    k_emit_mid<<<resident_grid(8), kPreBlock, 0, s>>>(a);
+    k_emit_big<<<resident_grid(8), kPreBlock, 0, s>>>(a);
     return 4;
 }
 
