@@ -324,6 +324,114 @@ __device__ __forceinline__ unsigned run_hits(int W, int H, float u, float v, flo
     return mask;
 }
 
+// run_hits with most decisions taken without evaluating the test.  A tile spans its row's whole
+// band [y0, y1], so it meets the ellipse {q <= t} iff its x-range [x0, x1] meets the x-range of the
+// ellipse within the band -- an interval [xmin, xmax] about u, found in closed form: x as a function
+// of dy on the ellipse's left boundary, (-b dy - sqrt(a t - det dy^2)) / a with det = a c - b^2, is
+// convex with its minimum at dy = b hx / c (hx = the half width, sqrt(t c / det)), so its least value
+// over the band is at that dy clamped into the band (likewise the right boundary, concave, greatest
+// at dy = -b hx / c).  A tile that overlaps [xmin, xmax] by more than a margin eps meets the ellipse
+// with room to spare, and so does the binary32 test (one of its edge chords or its centre test holds
+// with a slack far above binary32 rounding); one that misses the interval, or whose band misses
+// [-hy, hy], by more than eps fails every part of the test likewise.  Only tiles within eps of the
+// interval's ends (at most two or three a row end) are tested, with tile_hits, which equals each bit
+// of run_hits.  eps = 1/2 pixel plus 2^-8 of hx + hy bounds the interval's own error (approximate
+// division and square root, relative ~1e-6; cancellation in a t - det dy^2 near the band ends, about
+// 3.5e-4 hx) many times over.  Ellipses with det < 2^-12 a c (thin ones, where det cancels) and
+// non-finite extents take run_hits.
+__device__ __forceinline__ unsigned run_hits_banded(int W, int H, float u, float v, float a, float b, float c,
+                                                    float t, float hx, float hy, int tx_begin, int n, int ty) {
+    const float det = a * c - b * b;
+    if (!(det > 2.44140625e-4f * a * c) || !(hx + hy < 1.0e6f)) return run_hits(W, H, u, v, a, b, c, t, tx_begin, n, ty);
+    const float y0 = (float)(16 * ty), y1 = (float)min(16 * ty + 16, H);
+    const float eps = 0.5f + 3.90625e-3f * (hx + hy);
+    const float p0 = y0 - v, p1 = y1 - v;
+    if (p0 > hy + eps || p1 < -hy - eps) return 0u;             // the band misses the ellipse
+    const bool band_in = p0 < hy - eps && p1 > -hy + eps;        // ... or crosses it with room
+    const float lo_dy = fmaxf(p0, -hy), hi_dy = fminf(p1, hy);
+    const float ia = __fdividef(1.0f, a);
+    const float ky = __fdividef(b * hx, c);
+    const float dl = fminf(fmaxf(ky, lo_dy), hi_dy), dr = fminf(fmaxf(-ky, lo_dy), hi_dy);
+    const float rl = fmaxf(a * t - det * dl * dl, 0.0f), rr = fmaxf(a * t - det * dr * dr, 0.0f);
+    const float sl = rl > 0.0f ? rl * rsqrtf(rl) : 0.0f, sr = rr > 0.0f ? rr * rsqrtf(rr) : 0.0f;
+    const float xmin = u + (-b * dl - sl) * ia, xmax = u + (-b * dr + sr) * ia;
+    unsigned mask = 0;
+    for (int j = 0; j < n; ++j) {
+        const int tx = tx_begin + j;
+        const float x0 = (float)(16 * tx), x1 = (float)min(16 * tx + 16, W);
+        bool h;
+        if (x1 < xmin - eps || x0 > xmax + eps)
+            h = false;
+        else if (band_in && x1 > xmin + eps && x0 < xmax - eps)
+            h = true;
+        else
+            h = tile_hits(u, v, a, b, c, t, x0, x1, y0, y1);
+        mask |= (unsigned)h << j;
+    }
+    return mask;
+}
+
+// The decisions of n <= 64 consecutive tiles tx_begin .. of row ty as a 64-bit mask, by the band
+// interval of run_hits_banded turned into tile-index ranges: with y = x + eps, z = x - eps,
+//   tiles tx >= floor((xmin + eps) / 16) have x1 > xmin + eps and tiles tx <= ceil((xmax - eps)/16) - 1
+//   have x0 < xmax - eps (certain hits between, when the band crosses the ellipse with room);
+//   tiles tx <= ceil((xmin - eps) / 16) - 2 have x1 < xmin - eps and tiles tx >= floor((xmax + eps)/16)
+//   + 1 have x0 > xmax + eps (certain misses);
+// the last image column's x1 is W, not 16 tx + 16, so its certain hit is checked directly.  Only the
+// tiles between the two ranges (a few a row end) take tile_hits.  Thin ellipses take run_hits.
+__device__ __forceinline__ unsigned long long run_hits_long(int W, int H, float u, float v, float a, float b,
+                                                            float c, float t, float hx, float hy, int tx_begin,
+                                                            int n, int ty) {
+    const float det = a * c - b * b;
+    if (!(det > 2.44140625e-4f * a * c) || !(hx + hy < 1.0e6f)) {
+        unsigned long long m = 0;
+        for (int k = 0; k < n; k += 8)
+            m |= (unsigned long long)run_hits(W, H, u, v, a, b, c, t, tx_begin + k, min(8, n - k), ty) << k;
+        return m;
+    }
+    const float y0 = (float)(16 * ty), y1 = (float)min(16 * ty + 16, H);
+    const float eps = 0.5f + 3.90625e-3f * (hx + hy);
+    const float p0 = y0 - v, p1 = y1 - v;
+    if (p0 > hy + eps || p1 < -hy - eps) return 0ull;
+    const bool band_in = p0 < hy - eps && p1 > -hy + eps;
+    const float lo_dy = fmaxf(p0, -hy), hi_dy = fminf(p1, hy);
+    const float ia = __fdividef(1.0f, a);
+    const float ky = __fdividef(b * hx, c);
+    const float dl = fminf(fmaxf(ky, lo_dy), hi_dy), dr = fminf(fmaxf(-ky, lo_dy), hi_dy);
+    const float rl = fmaxf(a * t - det * dl * dl, 0.0f), rr = fmaxf(a * t - det * dr * dr, 0.0f);
+    const float sl = rl > 0.0f ? rl * rsqrtf(rl) : 0.0f, sr = rr > 0.0f ? rr * rsqrtf(rr) : 0.0f;
+    const float xmin = u + (-b * dl - sl) * ia, xmax = u + (-b * dr + sr) * ia;
+    const int tx_end = tx_begin + n - 1;
+    const int last_col = (W - 1) / 16;
+    int m0 = (int)ceilf((xmin - eps) * 0.0625f) - 2;   // tiles <= m0 miss
+    int m1 = (int)floorf((xmax + eps) * 0.0625f) + 1;  // tiles >= m1 miss
+    int h0 = (int)floorf((xmin + eps) * 0.0625f);      // tiles in [h0, h1] hit (band_in)
+    int h1 = (int)ceilf((xmax - eps) * 0.0625f) - 1;
+    if (h0 == last_col && !((float)W > xmin + eps)) h0 = last_col + 1;
+    if (!band_in || h1 < h0) {
+        h0 = m1;                                       // no certain hits: [m0 + 1, m1 - 1] is open
+        h1 = m1 - 1;
+    }
+    unsigned long long mask = 0;
+    const int a0 = max(h0, tx_begin), a1 = min(h1, tx_end);
+    if (a0 <= a1) {
+        const int len = a1 - a0 + 1;
+        mask = (len == 64 ? ~0ull : ((1ull << len) - 1ull)) << (a0 - tx_begin);
+    }
+    // the open tiles: (m0, h0) and (h1, m1), clipped to the run
+    const int o0 = max(m0 + 1, tx_begin), o1 = min(h0 - 1, tx_end);
+    for (int tx = o0; tx <= o1; ++tx) {
+        const float x0 = (float)(16 * tx), x1 = (float)min(16 * tx + 16, W);
+        if (tile_hits(u, v, a, b, c, t, x0, x1, y0, y1)) mask |= 1ull << (tx - tx_begin);
+    }
+    const int q0 = max(max(h1 + 1, h0), tx_begin), q1 = min(m1 - 1, tx_end);
+    for (int tx = q0; tx <= q1; ++tx) {
+        const float x0 = (float)(16 * tx), x1 = (float)min(16 * tx + 16, W);
+        if (tile_hits(u, v, a, b, c, t, x0, x1, y0, y1)) mask |= 1ull << (tx - tx_begin);
+    }
+    return mask;
+}
+
 // Pixel-area rectangle of tile (tx, ty), clipped to the image.
 __device__ __forceinline__ void tile_rect(const Cam &cam, int tx, int ty, float &x0, float &x1,
                                           float &y0, float &y1) {

@@ -459,7 +459,8 @@ __device__ __forceinline__ int block_scan_cand(PreSmem &S, int ncand) {
 struct CountSmem {
     float u[kPreBlock], v[kPreBlock], a[kPreBlock], b[kPreBlock], c[kPreBlock], t[kPreBlock];
     int tx0[kPreBlock], ty0[kPreBlock], w[kPreBlock];
-    int cstart[kPreBlock + 1];        // exclusive scan of the slots' unit counts
+    int cstart[kPreBlock + 1];        // exclusive scan of the slots' unit counts (mask bytes)
+    int istart[kPreBlock + 1];        // exclusive scan of the slots' work items
     unsigned cnt[kPreBlock];          // pairs of each slot
     float4 pa[kPreBlock];             // slot: camera-space mean and opacity from phase 1
     float z[kPreBlock], gl[kPreBlock];    // slot: depth and log2(alpha0) (the record's G)
@@ -467,33 +468,16 @@ struct CountSmem {
     int h[kPreBlock];                     // slot: candidate rows
     short sl[kPreBlock];              // slot -> Gaussian (thread) of the chunk
     short slot_of[kPreBlock];         // Gaussian -> slot, -1 when it has none
-    unsigned wsum[kPreBlock / 32];
+    unsigned wsum[kPreBlock / 32], wsum2[kPreBlock / 32];
     unsigned long long mbase;         // first hit-mask byte of the chunk
 };
 
-// Slot of unit `s` among the chunk's units: the last slot k with cstart[k] <= s.
-__device__ __forceinline__ Unit count_unit(const CountSmem &S, int s) {
-    int lo = 0, hi = kPreBlock - 1;
-#pragma unroll
-    for (int it = 0; it < 8; ++it) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (S.cstart[mid] <= s)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    Unit U;
-    U.g = lo;
-    const int k = s - S.cstart[lo];
-    const int w = S.w[lo];
-    const int segs = (w + kSeg - 1) / kSeg;
-    const int dy = k / segs;
-    const int seg = k - dy * segs;
-    U.tx = S.tx0[lo] + seg * kSeg;
-    U.ty = S.ty0[lo] + dy;
-    U.n = min(kSeg, w - seg * kSeg);
-    return U;
-}
+// Work items of the count pass: a box at least kWideBox tiles wide is cut into items of up to
+// kLong tiles of one row (kLong / kSeg mask bytes, decided by run_hits_long); narrower boxes into
+// the units themselves.  The mask bytes keep the unit layout either way.
+constexpr int kLong = 64;
+constexpr int kWideBox = 16;
+static_assert(kLong % kSeg == 0, "a long item covers whole units");
 
 // Pass 1: geometry, exact tests counted over all candidate tiles of the chunk (load-balanced),
 // render records of paired Gaussians, the chunk's pair count, and each paired Gaussian's
@@ -531,7 +515,7 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
     __syncthreads();
 
     // ---- phase 2 on slot tid; its geometry goes to shared memory (registers stay free for the tests)
-    int units = 0;
+    int units = 0, items = 0;
     if (tid < ns) {
         Geom G;
         const float4 pa = S.pa[tid];
@@ -552,32 +536,46 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
             S.gl[tid] = log_rn(G.alpha0) * 1.4426950408889634f;     // log2(alpha0)
             S.hxy[tid] = make_float2(G.hx, G.hy);
             units = units_of(w, h);
+            items = w >= kWideBox ? h * ((w + kLong - 1) / kLong) : units;
         }
     }
     if (units == 0) S.w[tid] = 1;
     S.cnt[tid] = 0;
-    // block scan of the slots' units (uses wsum: every read of phase 1's counts is behind the barrier)
-    int ctotal;
+    // block scans of the slots' units and items (wsum and wsum2: every read of phase 1's counts is
+    // behind the barrier)
+    int ctotal, itotal;
     {
-        int incl = units;
+        int incl = units, incl2 = items;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+            const int y2 = __shfl_up_sync(0xffffffffu, incl2, o);
+            if (lane >= o) {
+                incl += y;
+                incl2 += y2;
+            }
         }
-        if (lane == 31) S.wsum[warp] = (unsigned)incl;
+        if (lane == 31) {
+            S.wsum[warp] = (unsigned)incl;
+            S.wsum2[warp] = (unsigned)incl2;
+        }
         __syncthreads();
-        int wex = 0;
+        int wex = 0, wex2 = 0;
         ctotal = 0;
+        itotal = 0;
 #pragma unroll
         for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
-            const int x = (int)S.wsum[w2];
+            const int x = (int)S.wsum[w2], x2 = (int)S.wsum2[w2];
             wex += w2 < warp ? x : 0;
+            wex2 += w2 < warp ? x2 : 0;
             ctotal += x;
+            itotal += x2;
         }
         S.cstart[tid] = wex + incl - units;
+        S.istart[tid] = wex2 + incl2 - items;
         if (tid == 0) {
             S.cstart[kPreBlock] = ctotal;
+            S.istart[kPreBlock] = itotal;
             // one range of mask bytes per chunk (kept only while the area lasts)
             S.mbase = ctotal > 0 ? atomicAdd(&A.ctr->mask_used, (unsigned long long)ctotal) : 0ull;
         }
@@ -585,18 +583,53 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
     }
     const bool keep = S.mbase + (unsigned long long)ctotal <= (unsigned long long)A.mask_cap;
 
-    // ---- exact tile tests, 256 units per step over all slots
+    // ---- exact tile tests, 256 work items per step over all slots
     const bool square = R.opt.intersect == 1;
-    for (int base = 0; base < ctotal; base += kPreBlock) {
+    for (int base = 0; base < itotal; base += kPreBlock) {
         const int s = base + tid;
-        if (s < ctotal) {
-            const Unit U = count_unit(S, s);
-            const unsigned m = square ? (1u << U.n) - 1u
-                                      : run_hits(cam.W, cam.H, S.u[U.g], S.v[U.g], S.a[U.g], S.b[U.g], S.c[U.g],
-                                                 S.t[U.g], U.tx, U.n, U.ty);
-            if (keep) A.masks[S.mbase + s] = (unsigned char)m;
-            if (m) atomicAdd(&S.cnt[U.g], (unsigned)__popc(m));
+        if (s >= itotal) continue;
+        // slot of item s: the last slot g with istart[g] <= s
+        int g = 0, hi = kPreBlock - 1;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int mid = (g + hi + 1) >> 1;
+            if (S.istart[mid] <= s)
+                g = mid;
+            else
+                hi = mid - 1;
         }
+        const int k = s - S.istart[g];
+        const int w = S.w[g];
+        const float2 hxy = S.hxy[g];
+        unsigned pc;
+        if (w >= kWideBox) {
+            const int ipr = (w + kLong - 1) / kLong;
+            const int dy = k / ipr, j = k - dy * ipr;
+            const int tx = S.tx0[g] + kLong * j, n = min(kLong, w - kLong * j);
+            const unsigned long long m =
+                square ? (n == 64 ? ~0ull : (1ull << n) - 1ull)
+                       : run_hits_long(cam.W, cam.H, S.u[g], S.v[g], S.a[g], S.b[g], S.c[g], S.t[g], hxy.x, hxy.y,
+                                       tx, n, S.ty0[g] + dy);
+            if (keep) {
+                const unsigned long long mo =
+                    S.mbase + (unsigned long long)(S.cstart[g] + dy * ((w + kSeg - 1) / kSeg) + (kLong / kSeg) * j);
+                for (int q = 0; q * kSeg < n; ++q) A.masks[mo + q] = (unsigned char)(m >> (kSeg * q));
+            }
+            pc = (unsigned)__popcll(m);
+        } else {
+            const int segs = (w + kSeg - 1) / kSeg;
+            const int dy = k / segs, seg = k - dy * segs;
+            const int tx = S.tx0[g] + seg * kSeg, ty = S.ty0[g] + dy, n = min(kSeg, w - seg * kSeg);
+            // boxes three or more tiles wide: most tiles decided by the band interval
+            const unsigned m = square ? (1u << n) - 1u
+                               : w >= 3 ? run_hits_banded(cam.W, cam.H, S.u[g], S.v[g], S.a[g], S.b[g], S.c[g], S.t[g],
+                                                          hxy.x, hxy.y, tx, n, ty)
+                                        : run_hits(cam.W, cam.H, S.u[g], S.v[g], S.a[g], S.b[g], S.c[g], S.t[g], tx, n,
+                                                   ty);
+            if (keep) A.masks[S.mbase + (unsigned long long)(S.cstart[g] + k)] = (unsigned char)m;
+            pc = (unsigned)__popc(m);
+        }
+        if (pc) atomicAdd(&S.cnt[g], pc);
     }
     __syncthreads();
     const unsigned mine = S.cnt[tid];                  // pairs of slot tid (0 beyond ns)

@@ -190,6 +190,24 @@ def test_elongated_gaussians_row_runs(ctx, sort_mode, sort_algo):
     check(run_gpu(ctx, scene, cam, sort_mode=sort_mode, sort_algo=sort_algo), ref)
 
 
+@pytest.mark.parametrize("seed,mu", [(0, -1.6), (1, -3.0)])
+def test_large_ellipses_every_tile_decision(ctx, seed, mu):
+    """Thousands of ellipses from tens to hundreds of pixels across, axis ratios from 1 to about
+    60 (on both sides of the count pass's switch to the full test for thin ellipses), centres on
+    and off the image: every tile decision, taken by the band interval or by the binary32 test,
+    must equal the oracle's binary32 test of that tile (the emission-order pair lists are
+    compared element by element)."""
+    scene, cam = synth.random_small_scene(2500, 40 + seed, 1920, 1080, log_scale_mu=mu, log_scale_sigma=0.6)
+    rng = np.random.Generator(np.random.PCG64(60 + seed))
+    s = scene.scales.astype(np.float64)
+    s[np.arange(scene.P), rng.integers(0, 3, scene.P)] *= rng.uniform(0.015, 1.0, scene.P)
+    scene.scales = s.astype(np.float32)
+    ref = oracle.Frame(scene, cam, mode=32)
+    ncand = (ref.rect[:, 1] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 2] + 1) * (ref.valid > 0)
+    assert (ncand > 400).sum() >= 100 and ref.N > 300_000
+    check(run_gpu(ctx, scene, cam, sort_mode=0, max_pairs=1 << 24), ref)
+
+
 @pytest.mark.parametrize("sort_mode", [0, 1])
 def test_offscreen_centres_reaching_in(ctx, sort_mode):
     """Centres projected just outside every image edge, footprints from a few pixels to far
