@@ -36,6 +36,14 @@ BLEND_OPS_PER_EVAL = 14
 # Stricter secondary figure: only the contributing evaluations, at the 15 FP32-pipe operations a
 # contributing one costs (entries below tau are work a culler may avoid).
 BLEND_OPS_PER_CONTRIB = 15
+# Backward (the paper describes none): the reverse blend evaluates q for every walked (pixel,
+# entry) (6 FP32 ops: offsets, the quadratic form, the test) and, for a contributing one, recovers
+# alpha and T and forms the nine 2D gradient terms and the running colour sum (34 more, counting a
+# division as one); the per-Gaussian chain rule reads the scene (240 B) and the 2D gradients (40 B)
+# and writes the 59 parameter gradients (236 B).
+BWD_OPS_PER_EVAL = 6
+BWD_OPS_PER_CONTRIB = 34
+BWD_BYTES_PER_GAUSSIAN = 240 + 40 + 236
 
 
 def parse():
@@ -52,7 +60,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-training", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=600)
+    ap.add_argument("--serving-requests", type=int, default=600, help="requests per mode and rate")
     ap.add_argument("--no-city", action="store_true")
     ap.add_argument("--no-pair-study", action="store_true")
     ap.add_argument("--no-reduced-precision", action="store_true",
@@ -305,12 +313,13 @@ def pct(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
 
 
-def serve_run(gs, srv_kw, scenes, poses, schedule, ring):
-    """Submit `schedule` (arrival offset s, scene idx, camera idx, (W, H)) open loop; returns the
-    per-request stats.  ring: page-locked host buffers reused once their request has finished."""
+def serve_run(gs, server, scenes, poses, schedule, ring):
+    """Submit `schedule` (arrival offset s, scene idx, camera idx, (W, H)) open loop to `server`;
+    returns the per-request stats, the wall time and the server's counters accumulated by this
+    run.  ring: page-locked host buffers reused once their request has finished."""
     import threading
     from paper_2408_07967_gb300 import synth
-    server = gs.Server(srv_kw.pop("ctx"), **srv_kw)
+    st0 = server.stats()
     n = len(schedule)
     stats = [None] * n
     tickets = [None] * n
@@ -341,12 +350,16 @@ def serve_run(gs, srv_kw, scenes, poses, schedule, ring):
         submitted.release()
     th.join()
     wall = max(s["done_s"] for s in stats) - t0
-    st = server.stats()
-    server.close()
+    st = {k: v - st0[k] for k, v in server.stats().items()}
     return stats, wall, st
 
 
 def run_serving(args, gs, ctx, room_scene, room_cams, city, city_cams):
+    """Batched server against the plain one-at-a-time loop, both long-lived, on the same request
+    schedules.  Latencies on this host drift upward over a process's run by tens of percent
+    whichever server is measured (SM clocks stay at their maximum), so each rate runs in the order
+    plain, batched, batched, plain (half the requests each time) and each mode's latencies are
+    pooled: a drift linear in time then weighs on both equally."""
     import torch
     from paper_2408_07967_gb300 import synth
     stream = torch.cuda.Stream()
@@ -358,38 +371,42 @@ def run_serving(args, gs, ctx, room_scene, room_cams, city, city_cams):
     # a city view at 3840x2160 reaches ~230M pairs (street cameras), so both loops get 2^28 pairs;
     # batches are bounded by two 1080p images of pixels (the server's default), so two city
     # requests at most: 21M Gaussians cover them
-    batched = dict(slots=3, max_batch=8, pair_capacity=(1 << 28), max_gaussians=21_000_000, max_width=3840,
-                   max_height=2160)
-    plain = dict(plain=True, pair_capacity=(1 << 28), max_gaussians=11_000_000, max_width=3840, max_height=2160)
+    servers = {"batched": gs.Server(ctx, slots=3, max_batch=8, pair_capacity=(1 << 28), max_gaussians=21_000_000,
+                                    max_width=3840, max_height=2160),
+               "plain": gs.Server(ctx, plain=True, pair_capacity=(1 << 28), max_gaussians=11_000_000,
+                                  max_width=3840, max_height=2160)}
+    half = max(1, args.serving_requests // 2)
     out = {"workload": "resident room 1M + city 10M scenes, requests 50/50 over scenes, random pose of the "
                        "scene's 32, resolution uniform over 1280x720 / 1920x1080 / 3840x2160",
-           "requests_per_run": args.serving_requests}
-    for rate in (60, 240):
-        sched = synth.poisson_requests(args.serving_requests, rate, seed=3)
-        for name, kw in (("plain", plain), ("batched", batched)):
-            st, wall, sst = serve_run(gs, dict(kw, ctx=ctx), scenes, poses, sched, ring)
-            lat = [1000.0 * (s["done_s"] - s["arrival_s"]) for s in st]
-            ok = sum(s["status"] == 0 for s in st)
-            out[f"{name}@{rate}"] = {"frames_per_s": ok / wall, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
-                                     "mean_batch": sst["batched_requests"] / max(1, sst["batches"]),
-                                     "failed": len(st) - ok}
-            if len(st) != ok:
-                raise RuntimeError(f"serving {name}@{rate}: {len(st) - ok} requests failed")
-    # saturation: every request available at once
-    sched = [(0.0, si, ci, wh) for (_, si, ci, wh) in synth.poisson_requests(args.serving_requests, 1e9, seed=4)]
-    for name, kw in (("plain", plain), ("batched", batched)):
-        st, wall, sst = serve_run(gs, dict(kw, ctx=ctx), scenes, poses, sched, ring)
-        lat = [1000.0 * (s["done_s"] - s["arrival_s"]) for s in st]
-        if any(s["status"] != 0 for s in st):
-            raise RuntimeError(f"serving {name}@saturated: requests failed")
-        out[f"{name}@saturated"] = {"frames_per_s": sum(s["status"] == 0 for s in st) / wall,
-                                    "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
-                                    "mean_batch": sst["batched_requests"] / max(1, sst["batches"])}
+           "requests_per_mode": 2 * half, "order": "plain, batched, batched, plain per rate (latencies pooled)"}
+    for rate in (60, 240, "saturated"):
+        if rate == "saturated":     # every request available at once
+            scheds = [[(0.0, si, ci, wh) for (_, si, ci, wh) in synth.poisson_requests(half, 1e9, seed=4 + k)]
+                      for k in range(2)]
+        else:
+            scheds = [synth.poisson_requests(half, rate, seed=3 + k) for k in range(2)]
+        res = {"plain": [], "batched": []}
+        for name, k in (("plain", 0), ("batched", 0), ("batched", 1), ("plain", 1)):
+            st, wall, sst = serve_run(gs, servers[name], scenes, poses, scheds[k], ring)
+            failed = sum(s["status"] != 0 for s in st)
+            if failed:
+                raise RuntimeError(f"serving {name}@{rate}: {failed} requests failed")
+            res[name].append((st, wall, sst))
+        for name, runs in res.items():
+            lat = [1000.0 * (s["done_s"] - s["arrival_s"]) for st, _, _ in runs for s in st]
+            n = sum(len(st) for st, _, _ in runs)
+            wall = sum(w for _, w, _ in runs)
+            b = sum(x["batches"] for _, _, x in runs)
+            br = sum(x["batched_requests"] for _, _, x in runs)
+            out[f"{name}@{rate}"] = {"frames_per_s": round(n / wall, 2), "p50_ms": round(pct(lat, 50), 3),
+                                     "p99_ms": round(pct(lat, 99), 3), "mean_batch": round(br / max(1, b), 3)}
+    for sv in servers.values():
+        sv.close()
     room.close()
     return out
 
 
-def run_training(args, gs, ctx, room_scene, room_cams, steps=10):
+def run_training(args, gs, ctx, room_scene, room_cams, steps=10, alu=None):
     """Forward + backward over 4-camera batches on the 1M room at 1920x1080, L1 loss against images
     rendered from perturbed Gaussians (seed 4)."""
     import numpy as np
@@ -423,9 +440,47 @@ def run_training(args, gs, ctx, room_scene, room_cams, steps=10):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # per-kernel backward times of one batch (events around the two backward kernels), and the
+    # forward's evaluation counts of the same cameras for the reverse blend's algorithmic work
+    for fr in rast.frames:
+        fr.gs_frame_enable_timing(True)
+    for p in params:
+        p.grad = None
+    loss = (rast(*params, batches[2]) - targets[2]).abs().mean()
+    loss.backward()
+    torch.cuda.synchronize()
+    bwd = np.array([fr.gs_frame_backward_ms() for fr in rast.frames])
+    for fr in rast.frames:
+        fr.gs_frame_enable_timing(False)
+    counter = gs.Frame(ctx, raw.P, 1 << 25, W, H)
+    counter.gs_frame_set_counting(True)
+    E = Ec = 0
+    for cam in batches[2]:
+        counter.render(rast.scene, cam)
+        stc = counter.stats()
+        E += stc["evaluations"]
+        Ec += stc["contributions"]
+    counter.close()
+    blend_ms, gauss_ms = bwd[:, 0].mean(), bwd[:, 1].mean()
+    ops = (BWD_OPS_PER_EVAL * E + BWD_OPS_PER_CONTRIB * Ec) / len(batches[2])
+    gbytes = BWD_BYTES_PER_GAUSSIAN * raw.P
+    peaks = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    fma = (alu or {}).get("fma_tops") or SM_COUNT_GB300 * FP32_LANES_PER_SM * 2070e6 / 1e12
+    roof = {"k_blend_backward": {"ms": round(float(blend_ms), 4), "bound": "alu",
+                                 "achieved": round(ops / (blend_ms * 1e-3) / 1e12, 4), "peak": fma, "unit": "TOP/s",
+                                 "frac": round(ops / (blend_ms * 1e-3) / 1e12 / fma, 4),
+                                 "algorithmic": f"{BWD_OPS_PER_EVAL} FP32 ops per walked (pixel, entry) + "
+                                                f"{BWD_OPS_PER_CONTRIB} per contributing one, E = {E / 4:.4g}, "
+                                                f"E_c = {Ec / 4:.4g} per camera"},
+            "k_gauss_backward": {"ms": round(float(gauss_ms), 4), "bound": "hbm",
+                                 "achieved": round(gbytes / (gauss_ms * 1e-3) / 1e9, 1), "peak": hbm_peak,
+                                 "unit": "GB/s", "frac": round(gbytes / (gauss_ms * 1e-3) / 1e9 / hbm_peak, 4),
+                                 "algorithmic": f"{BWD_BYTES_PER_GAUSSIAN} B per Gaussian x P = {raw.P}"}}
     return {"workload": "room 1M @1920x1080, 4-camera batches, L1 vs perturbed-Gaussian targets (seed 4)",
             "ms_per_step": ms, "frames_per_s": 4000.0 / ms, "loss": float(loss.item()),
-            "grad_finite": bool(all(torch.isfinite(p.grad).all().item() for p in params))}
+            "grad_finite": bool(all(torch.isfinite(p.grad).all().item() for p in params)),
+            "backward_per_camera": roof}
 
 
 # ------------------------------------------------------------------------------------ timed frames
@@ -787,7 +842,7 @@ def run_ours(args):
         del city_scene
     training = serving = None
     if rank == 0 and not args.no_training and args.config == "room":
-        training = run_training(args, gs, ctx, scene, cams)
+        training = run_training(args, gs, ctx, scene, cams, alu=alu)
     if rank == 0 and not args.no_serving and args.config == "room":
         serving = run_serving(args, gs, ctx, scene, cams, city, city_cams)
 

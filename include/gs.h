@@ -303,6 +303,12 @@ gs_status gs_frame_set_counting(gs_frame *frame, int32_t enable);
    the graph when graphs are enabled). */
 gs_status gs_frame_enable_timing(gs_frame *frame, int32_t enable);
 
+/* Waits for the last gs_render_backward run with timing enabled and writes the device time of its
+   two kernels in milliseconds: ms[0] the reverse blend (per tile, back to front, per-Gaussian 2D
+   gradients), ms[1] the per-Gaussian chain rule to the 3D parameters.  GS_ERR_INVALID_ARG when
+   timing is off or no backward was timed.  The paper describes no backward (abstract only). */
+gs_status gs_frame_backward_ms(gs_frame *frame, float ms[2]);
+
 /* Waits for the last timed gs_render and writes the device time of its stages in milliseconds:
    ms[0] preprocess, ms[1] sort, ms[2] ranges, ms[3] blend.  GS_ERR_INVALID_ARG when timing is
    off or nothing was timed yet. */
@@ -372,7 +378,8 @@ uint32_t gs_get_wait_limit(void);
    at most max_gaussians Gaussians together) are admitted by pair-buffer memory: one count pass
    (geometry + exact pair counts) gives each request's pairs, and the oldest requests whose
    pairs fit pair_capacity run as one batch through gs_render_batch's single pass per stage with
-   per-request tile ranges; the rest wait for the next free slot.  A lone request skips the
+   per-request tile ranges; the rest wait for the next free slot (at light load, see fifo_load_pct,
+   requests instead run one at a time in arrival order).  A lone request skips the
    admission round trip (it has nothing to defer; if it alone exceeds pair_capacity it completes
    with GS_ERR_PAIR_OVERFLOW).  Batches run on streams prioritised by age: a batch launched while
    k others are in flight gets the k-th highest stream priority, so the oldest batch keeps the
@@ -396,6 +403,14 @@ typedef struct {
                                  a larger request runs alone -- batching amortises launches and
                                  small kernels, while a request that fills the GPU by itself only
                                  waits longer in a batch */
+    int32_t overlap_pending;  /* under load, a batch starts beside batches in flight when at least this
+                                 many requests are waiting (0: the default, 1) */
+    int32_t fifo_load_pct;    /* while the estimated load -- the recent arrival rate times the mean
+                                 service time of recent requests -- is below this percentage, requests
+                                 run one at a time in arrival order with nothing beside them, as in the
+                                 plain loop (at light load a batch or an overlap only makes its first
+                                 request wait for the others' work); above it they are batched and
+                                 overlapped.  0: the default, 30; -1: always batch. */
 } gs_server_cfg;
 typedef struct {
     int32_t status;           /* GS_OK, GS_ERR_PAIR_OVERFLOW (alone over the pair capacity), ... */

@@ -268,6 +268,12 @@ class Frame:
         _check(lib().gs_frame_stage_ms(self.h, ms))
         return list(ms)
 
+    def gs_frame_backward_ms(self):
+        """[reverse blend ms, per-Gaussian chain rule ms] of the last timed backward."""
+        ms = (C.c_float * 2)()
+        _check(lib().gs_frame_backward_ms(self.h, ms))
+        return [ms[0], ms[1]]
+
     def gs_render_host(self, scene: Scene, cam, rgb_host, T_host=None, last_host=None, opts=None, stream=None):
         """Render and copy into host tensors (page-locked for asynchronous copies)."""
         o = opts or gs_opts()

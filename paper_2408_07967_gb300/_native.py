@@ -44,7 +44,8 @@ class gs_gaussian_grads(C.Structure):
 class gs_server_cfg(C.Structure):
     _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("pair_capacity", C.c_int64),
                 ("max_gaussians", C.c_int64), ("max_width", C.c_int32), ("max_height", C.c_int32),
-                ("sort_mode", C.c_int32), ("blend_variant", C.c_int32), ("plain", C.c_int32), ("batch_pixels", C.c_int32)]
+                ("sort_mode", C.c_int32), ("blend_variant", C.c_int32), ("plain", C.c_int32), ("batch_pixels", C.c_int32),
+                ("overlap_pending", C.c_int32), ("fifo_load_pct", C.c_int32)]
 
 
 class gs_request_stats(C.Structure):
@@ -137,6 +138,7 @@ PROTOTYPES = {
     "gs_set_wait_limit": (_st, [C.c_uint32]),
     "gs_get_wait_limit": (C.c_uint32, []),
     "gs_sort_pairs_noalloc_status": (_st, [_vp]),
+    "gs_frame_backward_ms": (_st, [_vp, C.POINTER(C.c_float)]),
 }
 
 

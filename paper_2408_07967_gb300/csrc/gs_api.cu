@@ -149,8 +149,9 @@ struct gs_frame {
     int use_graph = 0;
     cudaGraphExec_t exec = nullptr;
     // stage timing
-    int timing = 0, timed = 0;
+    int timing = 0, timed = 0, bwd_timed = 0;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t evb[3] = {nullptr, nullptr, nullptr};   // backward: start, between the kernels, end
     // frame-owned outputs for gs_render_host (allocated on first use)
     void *out_mem = nullptr;
     gs_tuning tuning{1, 1, 0, {0, 0, 0, 0, 0}};
@@ -395,6 +396,8 @@ gs_status gs_frame_destroy(gs_frame *f) {
     if (f->exec) cudaGraphExecDestroy(f->exec);
     for (int i = 0; i < 5; ++i)
         if (f->ev[i]) cudaEventDestroy(f->ev[i]);
+    for (int i = 0; i < 3; ++i)
+        if (f->evb[i]) cudaEventDestroy(f->evb[i]);
     cudaFree(f->out_mem);
     cudaFree(f->grad2d);
     cudaFree(f->mem);
@@ -449,6 +452,7 @@ gs_status gs_frame_enable_timing(gs_frame *f, int32_t enable) {
     if (enable && !f->ev[0]) {
         GS_CUDA(cudaSetDevice(f->device));
         for (int i = 0; i < 5; ++i) GS_CUDA(cudaEventCreate(&f->ev[i]));
+        for (int i = 0; i < 3; ++i) GS_CUDA(cudaEventCreate(&f->evb[i]));
     }
     if (f->timing != (enable ? 1 : 0) && f->exec) {   // topology changes: re-instantiate the graph
         cudaGraphExecDestroy(f->exec);
@@ -456,6 +460,15 @@ gs_status gs_frame_enable_timing(gs_frame *f, int32_t enable) {
     }
     f->timing = enable ? 1 : 0;
     f->timed = 0;
+    f->bwd_timed = 0;
+    return GS_OK;
+}
+
+gs_status gs_frame_backward_ms(gs_frame *f, float ms[2]) {
+    if (!f || !ms) return fail(GS_ERR_INVALID_ARG, "NULL frame or ms");
+    if (!f->timing || !f->bwd_timed) return fail(GS_ERR_INVALID_ARG, "no timed backward on this frame");
+    GS_CUDA(cudaEventSynchronize(f->evb[2]));
+    for (int i = 0; i < 2; ++i) GS_CUDA(cudaEventElapsedTime(&ms[i], f->evb[i], f->evb[i + 1]));
     return GS_OK;
 }
 
@@ -1115,7 +1128,12 @@ extern "C" gs_status gs_render_backward(gs_frame *f, const gs_scene *s, const fl
     a.g_opacity = g->opacity;
     a.g_sh = g->sh;
     a.accumulate = accumulate ? 1 : 0;
-    launch_backward(a, st);
+    if (f->timing) GS_CUDA(cudaEventRecord(f->evb[0], st));
+    launch_backward(a, st, f->timing ? f->evb[1] : nullptr);
+    if (f->timing) {
+        GS_CUDA(cudaEventRecord(f->evb[2], st));
+        f->bwd_timed = 1;
+    }
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

@@ -407,9 +407,10 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
     for (int i = 0; i < 48; ++i) A.g_sh[48 * gid + i] = add ? A.g_sh[48 * gid + i] + gsh[i] : gsh[i];
 }
 
-void launch_backward(const BwdArgs &a, cudaStream_t s) {
+void launch_backward(const BwdArgs &a, cudaStream_t s, cudaEvent_t between) {
     const int ntiles = a.tiles_x * a.tiles_y;
     if (ntiles > 0) k_blend_backward<<<ntiles, kBwdThreads, 0, s>>>(a);
+    if (between) cudaEventRecord(between, s);
     const long long P = a.scene.P;
     if (P > 0) k_gauss_backward<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(a);
 }

@@ -557,7 +557,8 @@ struct BwdArgs {
     float *g_means, *g_scales, *g_quats, *g_opacity, *g_sh;
     int accumulate;
 };
-void launch_backward(const BwdArgs &a, cudaStream_t s);
+// between (nullable): recorded after the reverse blend, before the per-Gaussian chain rule.
+void launch_backward(const BwdArgs &a, cudaStream_t s, cudaEvent_t between);
 int grad2d_floats();
 
 }  // namespace gs

@@ -66,7 +66,11 @@ struct Request {
 };
 
 constexpr int kPrioLevels = 3;
-constexpr long long kBacklog = 2;        // pending requests that justify overlapping batches
+constexpr long long kBacklog = 1;        // default: pending requests that justify overlapping batches
+constexpr int kFifoLoadPct = 30;         // default: below this load, one request at a time
+constexpr int kArrivalRing = 64;         // recent arrivals kept for the rate estimate
+constexpr double kRateWindow = 0.25;     // seconds of arrivals that count
+constexpr long long kBurst = 4;          // waiting requests that count as load whatever the estimate
 
 struct Slot {
     cudaStream_t stream = nullptr;              // the stream of the batch in flight
@@ -101,6 +105,10 @@ struct gs_server {
     uint64_t next_ticket = 1;
     long long completed = 0, batches = 0, batched_requests = 0;
     gs_status fatal = GS_OK;
+    // load estimate: recent arrival times and the mean service time (admission to completion)
+    double arrivals[kArrivalRing] = {};
+    long long n_arrivals = 0;
+    double svc_ema = 0;
 };
 
 namespace {
@@ -135,6 +143,8 @@ void reap(gs_server *sv) {
             it->second.done = s.done_time;
             it->second.finished = true;
             ++sv->completed;
+            const double svc = s.done_time - it->second.admit;
+            if (svc > 0) sv->svc_ema = sv->svc_ema > 0 ? 0.9 * sv->svc_ema + 0.1 * svc : svc;
         }
         s.inflight.clear();
         s.busy = false;
@@ -263,6 +273,24 @@ std::vector<uint64_t> launch_batch(gs_server *sv, Slot &s, std::vector<uint64_t>
     return back;
 }
 
+// Estimated load: the arrival rate over the last kRateWindow seconds (at most kArrivalRing
+// arrivals) times the mean service time.  Called with the lock held.
+double estimate_load(const gs_server *sv, double now) {
+    const long long n = sv->n_arrivals < kArrivalRing ? sv->n_arrivals : kArrivalRing;
+    if (n < 2 || sv->svc_ema <= 0) return 0.0;
+    const double newest = sv->arrivals[(sv->n_arrivals - 1) % kArrivalRing];
+    if (now - newest > kRateWindow) return 0.0;
+    long long k = 1;
+    double oldest = newest;
+    for (; k < n; ++k) {
+        const double t = sv->arrivals[(sv->n_arrivals - 1 - k) % kArrivalRing];
+        if (now - t > kRateWindow) break;
+        oldest = t;
+    }
+    const double span = now - oldest;
+    return span > 0 ? (double)k / span * sv->svc_ema : 0.0;
+}
+
 void worker_main(gs_server *sv) {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->mu);
@@ -274,10 +302,17 @@ void worker_main(gs_server *sv) {
             if (!s.busy && !free_slot) free_slot = &s;
             busy += s.busy ? 1 : 0;
         }
-        // Overlapping batches buy throughput at the price of the older batch's latency (younger
-        // kernels, persistent ones in particular, hold SMs it needs).  So a second batch starts
-        // beside a running one only when a backlog has formed.
-        const bool backlog = (long long)sv->pending.size() >= kBacklog;
+        // At light load one request at a time in arrival order is the fastest for every request:
+        // a batch makes its first request wait for the others' work, and an overlapping batch
+        // slows the older one (younger kernels, persistent and cooperative ones in particular,
+        // hold SMs it needs).  Under load (estimated from arrivals and service times, or a queue
+        // of kBurst), requests are batched, and a batch starts beside running ones once
+        // overlap_pending requests wait.
+        const int fifo_pct = sv->cfg.fifo_load_pct ? sv->cfg.fifo_load_pct : kFifoLoadPct;
+        const bool fifo = !sv->cfg.plain && fifo_pct > 0 && (long long)sv->pending.size() < kBurst &&
+                          estimate_load(sv, now_s()) * 100.0 < fifo_pct;
+        const long long need = sv->cfg.overlap_pending > 0 ? sv->cfg.overlap_pending : kBacklog;
+        const bool backlog = !fifo && (long long)sv->pending.size() >= need;
         if (!free_slot || sv->pending.empty() || sv->hold || (busy > 0 && !backlog)) {
             sv->cv.notify_all();
             sv->cv.wait_for(lk, std::chrono::microseconds(200));
@@ -286,7 +321,7 @@ void worker_main(gs_server *sv) {
         // candidates: oldest requests, bounded by max_batch and the frame's Gaussian capacity
         std::vector<uint64_t> cand;
         long long g = 0, px = 0;
-        const int maxb = sv->cfg.plain ? 1 : sv->cfg.max_batch;
+        const int maxb = sv->cfg.plain || fifo ? 1 : sv->cfg.max_batch;
         const long long max_px = sv->cfg.batch_pixels > 0 ? sv->cfg.batch_pixels : 2ll * 1920 * 1080;
         while (!sv->pending.empty() && (int)cand.size() < maxb) {
             const uint64_t t = sv->pending.front();
@@ -339,7 +374,7 @@ gs_status gs_server_create(gs_context *ctx, const gs_server_cfg *cfg, gs_server 
     }
     if (c.slots < 1 || c.slots > 8 || c.max_batch < 1 || c.max_batch > gs::kMaxBatch || c.pair_capacity <= 0 ||
         c.pair_capacity >= (1ll << 30) || c.max_gaussians <= 0 || c.max_width <= 0 || c.max_height <= 0 ||
-        c.batch_pixels < 0)
+        c.batch_pixels < 0 || c.overlap_pending < 0 || c.fifo_load_pct < -1)
         return err(GS_ERR_INVALID_ARG, "server configuration out of range");
     gs_server *sv = new (std::nothrow) gs_server();
     if (!sv) return err(GS_ERR_OOM, "host allocation failed");
@@ -430,6 +465,8 @@ gs_status gs_server_submit(gs_server *sv, const gs_scene *scene, const gs_camera
         *ticket = r.ticket;
         sv->reqs.emplace(r.ticket, r);
         sv->pending.push_back(r.ticket);
+        sv->arrivals[sv->n_arrivals % kArrivalRing] = now_s();
+        ++sv->n_arrivals;
     }
     sv->cv.notify_all();
     return GS_OK;
