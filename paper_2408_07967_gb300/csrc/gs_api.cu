@@ -1128,6 +1128,7 @@ extern "C" gs_status gs_render_backward(gs_frame *f, const gs_scene *s, const fl
     a.g_opacity = g->opacity;
     a.g_sh = g->sh;
     a.accumulate = accumulate ? 1 : 0;
+    a.vec16 = (((uintptr_t)g->quats | (uintptr_t)g->sh) & 15u) == 0 ? 1 : 0;
     if (f->timing) GS_CUDA(cudaEventRecord(f->evb[0], st));
     launch_backward(a, st, f->timing ? f->evb[1] : nullptr);
     if (f->timing) {

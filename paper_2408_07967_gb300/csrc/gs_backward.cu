@@ -10,9 +10,10 @@
 //     dL/dalpha  = T (g . rgb) - S / (1 - alpha),   S = g . (sum of later contributions + T_final bg)
 //     alpha = alpha0 e^(-q/2):  dL/dalpha0 = dL/dalpha e^(-q/2),  dL/dq = -alpha/2 dL/dalpha
 //     q = a dx^2 + 2 b dx dy + c dy^2 with dx = px - u, dy = py - v.
-//   The nine per-Gaussian sums (u, v, a, b, c, alpha0, r, g, b) of a warp are reduced with
-//   shuffles, accumulated over the CTA in shared memory, then added to global memory once per
-//   CTA and entry (warp-level reduction before atomics, the idea DISTWAR applies to 3DGS).
+//   Each thread takes PX pixels of a row; the nine per-Gaussian sums (u, v, a, b, c, alpha0, r, g,
+//   b) of its pixels are added in the thread, reduced over the warp with shuffles, accumulated
+//   over the CTA in shared memory, then added to global memory once per CTA and entry (warp-level
+//   reduction before atomics, the idea DISTWAR applies to 3DGS).
 // k_gauss_backward: per Gaussian, the chain from those 2D gradients to the parameters: colour ->
 //   SH coefficients and the view direction; alpha0 -> opacity (logit); conic -> Sigma'
 //   (dQ = -Q dSigma' Q) -> Sigma and J W -> scales, quaternion and the camera-space mean; (u, v)
@@ -21,7 +22,7 @@
 
 namespace gs {
 
-constexpr int kBwdThreads = 256;
+constexpr int kBwdPx = 2;  // pixels per thread of the reverse blend
 constexpr int kG2 = 10;   // floats per Gaussian in the 2D-gradient buffer
 
 __device__ __forceinline__ float ex2_approx_b(float x) {
@@ -30,113 +31,189 @@ __device__ __forceinline__ float ex2_approx_b(float x) {
     return y;
 }
 
-__global__ void __launch_bounds__(kBwdThreads) k_blend_backward(const __grid_constant__ BwdArgs A) {
-    __shared__ float4 s_r0[kBwdThreads];
-    __shared__ float4 s_r1[kBwdThreads];
-    __shared__ float2 s_r2[kBwdThreads];
-    __shared__ unsigned s_gid[kBwdThreads];
-    __shared__ float s_acc[kBwdThreads][9];
+// Reverse blend, laid out like the forward blend: PX pixels per thread along a row (256 / PX
+// threads per tile), each warp owning an RR x RC pixel region; entries are staged kBwdBatch at a
+// time, each warp keeps those whose {q <= t} meets its region (the exact test of Algorithm 3 on the
+// region's rectangle: an entry that meets none of the warp's pixel samples changes none of their
+// states) and walks them from the highest list position down.  A thread sums its pixels' terms
+// before the warp reduction, so a (warp, entry) pays one nine-value reduction for 32 PX pixels.
+template <int PX>
+struct BwdRegion {
+    static constexpr int RC = PX == 4 ? 16 : 8;
+    static constexpr int RR = 32 * PX / RC;
+    static constexpr int LANES_PER_ROW = RC / PX;
+};
+constexpr int kBwdBatch = 128;
+
+template <int PX>
+__global__ void __launch_bounds__(256 / PX) k_blend_backward(const __grid_constant__ BwdArgs A) {
+    constexpr int NT = 256 / PX;
+    constexpr int PER = kBwdBatch / NT;
+    constexpr int WORDS = kBwdBatch / 32;
+    using WR = BwdRegion<PX>;
+    __shared__ float4 s_r0[kBwdBatch], s_r1[kBwdBatch], s_r2[kBwdBatch];
+    __shared__ unsigned s_gid[kBwdBatch];
+    __shared__ float s_acc[kBwdBatch][9];
     __shared__ unsigned s_maxlast;
     if (upstream_timed_out(A.ctr)) return;   // the forward's sort gave up: its ids may be garbage
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const int tile = blockIdx.x;
     const int tx = tile % A.tiles_x, ty = tile / A.tiles_x;
-    const int px = tx * kTile + (tid & 15), py = ty * kTile + (tid >> 4);
-    const bool inside = px < A.W && py < A.H;
+    constexpr int REGIONS_PER_ROW = 16 / WR::RC;
+    const int rx0 = tx * kTile + (warp % REGIONS_PER_ROW) * WR::RC;
+    const int ry0 = ty * kTile + (warp / REGIONS_PER_ROW) * WR::RR;
+    const int py = ry0 + lane / WR::LANES_PER_ROW;
+    const int px0 = rx0 + (lane % WR::LANES_PER_ROW) * PX;
+    const float qx0 = (float)rx0, qx1 = (float)(rx0 + WR::RC), qy0 = (float)ry0, qy1 = (float)(ry0 + WR::RR);
     long long n = (long long)*A.n_dev;
     if (n > A.cap) n = A.cap;
     const long long start = min((long long)A.starts[tile], n);
-    const long long o = (long long)py * A.W + px;
     const long long npx = (long long)A.W * A.H;
-    unsigned my_last = inside ? A.last[o] : 0u;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f, T = 1.f;
-    if (inside) {
-        g0 = A.dL_drgb[o];
-        g1 = A.dL_drgb[npx + o];
-        g2 = A.dL_drgb[2 * npx + o];
-        T = A.T_final[o];
+    float fpx[PX], T[PX], S[PX], g0[PX], g1[PX], g2[PX];
+    unsigned last[PX];
+    unsigned my_max = 0;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) {
+        const bool inside = px0 + k < A.W && py < A.H;
+        const long long o = (long long)py * A.W + px0 + k;
+        fpx[k] = (float)(px0 + k) + 0.5f;
+        last[k] = inside ? A.last[o] : 0u;
+        g0[k] = inside ? A.dL_drgb[o] : 0.f;
+        g1[k] = inside ? A.dL_drgb[npx + o] : 0.f;
+        g2[k] = inside ? A.dL_drgb[2 * npx + o] : 0.f;
+        T[k] = inside ? A.T_final[o] : 1.f;
+        S[k] = T[k] * (g0[k] * A.opt.bg[0] + g1[k] * A.opt.bg[1] + g2[k] * A.opt.bg[2]);
+        my_max = max(my_max, last[k]);
     }
-    float Sg = T * (g0 * A.opt.bg[0] + g1 * A.opt.bg[1] + g2 * A.opt.bg[2]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(FULL, my_max, o));
     if (tid == 0) s_maxlast = 0;
     __syncthreads();
-    if (my_last) atomicMax(&s_maxlast, my_last);
+    if (lane == 0) atomicMax(&s_maxlast, my_max);
     __syncthreads();
     const int max_last = (int)s_maxlast;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float fpy = (float)py + 0.5f;
     const float HALF_LOG2E = 0.72134752044448170f;
     const float amax = A.opt.alpha_max;
 
-    for (int hi = max_last; hi > 0; hi -= kBwdThreads) {
-        const int lo = max(0, hi - kBwdThreads);
-        __syncthreads();
-        const int e = lo + tid;
-        if (e < hi) {
-            const unsigned g = A.vals[start + e];
-            const Rec r = A.recs[g];
-            s_r0[tid] = r.r0;
-            s_r1[tid] = r.r1;
-            s_r2[tid] = make_float2(r.r2.x, r.r2.y);
-            s_gid[tid] = g;
+    for (int hi = max_last; hi > 0; hi -= kBwdBatch) {
+        const int lo = max(0, hi - kBwdBatch);
+        const int cnt = hi - lo;
+        __syncthreads();                     // the previous batch has been flushed
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int e = r * NT + tid;
+            if (e < cnt) {
+                const unsigned g = A.vals[start + lo + e];
+                const Rec rc = A.recs[g];
+                s_r0[e] = rc.r0;
+                s_r1[e] = rc.r1;
+                s_r2[e] = make_float4(rc.r2.x, rc.r2.y, ex2_approx_b(rc.r1.z), 0.f);   // alpha0
+                s_gid[e] = g;
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) s_acc[e][k] = 0.0f;
         }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) s_acc[tid][k] = 0.0f;
         __syncthreads();
-        for (int j = hi - 1; j >= lo; --j) {
-            const int jj = j - lo;
-            const float4 r0 = s_r0[jj];
-            const float4 r1 = s_r1[jj];
-            const float dx = fsub(fpx, r0.x), dy = fsub(fpy, r0.y);
-            const float q = pixel_q(r0.z, r0.w, r1.x, dx, dy);
-            const bool pass = (unsigned)j < my_last && q <= r1.y;
-            if (!__any_sync(FULL, pass)) continue;
-            float d[9];
+        unsigned mask[WORDS];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) d[k] = 0.0f;
-            if (pass) {
-                const float2 r2 = s_r2[jj];
-                const float e2 = ex2_approx_b(fmaf(q, -HALF_LOG2E, r1.z));   // alpha0 e^(-q/2), as forward
-                const float al = fminf(amax, e2);
-                const float Tb = T / (1.0f - al);
-                const float gc = g0 * r1.w + g1 * r2.x + g2 * r2.y;
-                const float w = al * Tb;
-                d[6] = w * g0;
-                d[7] = w * g1;
-                d[8] = w * g2;
-                const float dal = Tb * gc - Sg / (1.0f - al);
-                Sg = fmaf(gc, w, Sg);
-                T = Tb;
-                if (e2 <= amax) {
-                    const float a0 = ex2_approx_b(r1.z);
-                    d[5] = dal * (al / a0);
-                    const float dq = -0.5f * al * dal;
-                    const float a = r0.z, b2 = r0.w, c = r1.x;
-                    d[0] = -dq * (2.0f * a * dx + b2 * dy);
-                    d[1] = -dq * (b2 * dx + 2.0f * c * dy);
-                    d[2] = dq * dx * dx;
-                    d[3] = dq * 2.0f * dx * dy;
-                    d[4] = dq * dy * dy;
+        for (int w = 0; w < WORDS; ++w) {
+            const int e = w * 32 + lane;
+            bool rel = false;
+            if (e < cnt) {
+                const float4 a0 = s_r0[e], a1 = s_r1[e];
+                rel = tile_hits(a0.x, a0.y, a0.z, 0.5f * a0.w, a1.x, a1.y, qx0, qx1, qy0, qy1);
+            }
+            mask[w] = __ballot_sync(FULL, rel);
+        }
+        // back to front: highest list position first
+#pragma unroll
+        for (int w = WORDS - 1; w >= 0; --w) {
+            unsigned m = mask[w];
+            while (m) {
+                const int bit = 31 - __clz(m);
+                m &= ~(1u << bit);
+                const int jj = w * 32 + bit;
+                const unsigned j = (unsigned)(lo + jj);
+                const float4 r0 = s_r0[jj], r1 = s_r1[jj];
+                const float dy = fsub(fpy, r0.y);
+                const float By = fmul(r0.w, dy);
+                const float Cy = fmul(fmul(r1.x, dy), dy);
+                float q[PX], dx[PX];
+                bool pass[PX];
+                bool anyp = false;
+#pragma unroll
+                for (int k = 0; k < PX; ++k) {
+                    dx[k] = fsub(fpx[k], r0.x);
+                    q[k] = ffma(ffma(r0.z, dx[k], By), dx[k], Cy);
+                    pass[k] = j < last[k] && q[k] <= r1.y;
+                    anyp |= pass[k];
                 }
-            }
+                if (!__any_sync(FULL, anyp)) continue;
+                const float4 r2 = s_r2[jj];
+                float d[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                float v = d[k];
+                for (int k = 0; k < 9; ++k) d[k] = 0.0f;
 #pragma unroll
-                for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(FULL, v, s);
-                d[k] = v;
-            }
-            if (lane == 0) {
+                for (int k = 0; k < PX; ++k) {
+                    if (!pass[k]) continue;
+                    const float e2 = ex2_approx_b(fmaf(q[k], -HALF_LOG2E, r1.z));   // alpha0 e^(-q/2), as forward
+                    const float al = fminf(amax, e2);
+                    const float inv = __fdividef(1.0f, 1.0f - al);      // 1 - al >= 0.01
+                    const float Tb = T[k] * inv;
+                    const float gc = g0[k] * r1.w + g1[k] * r2.x + g2[k] * r2.y;
+                    const float wgt = al * Tb;
+                    d[6] += wgt * g0[k];
+                    d[7] += wgt * g1[k];
+                    d[8] += wgt * g2[k];
+                    const float dal = Tb * gc - S[k] * inv;
+                    S[k] = fmaf(gc, wgt, S[k]);
+                    T[k] = Tb;
+                    if (e2 <= amax) {
+                        d[5] += dal * (al / r2.z);
+                        const float dq = -0.5f * al * dal;
+                        const float ddy = dy, ddx = dx[k];
+                        d[0] += -dq * (2.0f * r0.z * ddx + r0.w * ddy);
+                        d[1] += -dq * (r0.w * ddx + 2.0f * r1.x * ddy);
+                        d[2] += dq * ddx * ddx;
+                        d[3] += dq * 2.0f * ddx * ddy;
+                        d[4] += dq * ddy * ddy;
+                    }
+                }
+                // warp sums of d[0..7] by halving exchanges: across lanes 16 apart each lane keeps
+                // four values (its half's) and adds its partner's copy of them, then two, then one;
+                // two butterfly steps finish, leaving value 4 b4 + 2 b3 + b2 (bits of the lane) in
+                // every lane of a group of four -- 9 shuffles instead of 40; d[8] by a butterfly
+                const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+                float k4[4];
 #pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    if (d[k] != 0.0f) atomicAdd(&s_acc[jj][k], d[k]);
+                for (int i = 0; i < 4; ++i) {
+                    const float send = h4 ? d[i] : d[i + 4];
+                    k4[i] = (h4 ? d[i + 4] : d[i]) + __shfl_xor_sync(FULL, send, 16);
+                }
+                float k2[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const float send = h3 ? k4[i] : k4[i + 2];
+                    k2[i] = (h3 ? k4[i + 2] : k4[i]) + __shfl_xor_sync(FULL, send, 8);
+                }
+                float v = (h2 ? k2[1] : k2[0]) + __shfl_xor_sync(FULL, h2 ? k2[0] : k2[1], 4);
+                v += __shfl_xor_sync(FULL, v, 2);
+                v += __shfl_xor_sync(FULL, v, 1);
+                float v8 = d[8];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(FULL, v8, o);
+                if ((lane & 3) == 0 && v != 0.0f) atomicAdd(&s_acc[jj][lane >> 2], v);
+                if (lane == 0 && v8 != 0.0f) atomicAdd(&s_acc[jj][8], v8);
             }
         }
         __syncthreads();
-        if (lo + tid < hi) {
-            float *dst = A.grad2d + (long long)s_gid[tid] * kG2;
+        for (int e = tid; e < cnt; e += NT) {
+            float *dst = A.grad2d + (long long)s_gid[e] * kG2;
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                const float v = s_acc[tid][k];
+                const float v = s_acc[e][k];
                 if (v != 0.0f) atomicAdd(dst + k, v);
             }
         }
@@ -400,16 +477,37 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
         A.g_means[3 * gid + a] = add ? A.g_means[3 * gid + a] + gm[a] : gm[a];
         A.g_scales[3 * gid + a] = add ? A.g_scales[3 * gid + a] + gsc[a] : gsc[a];
     }
+    A.g_opacity[gid] = add ? A.g_opacity[gid] + gop : gop;
+    if (A.vec16) {
+        // quaternion and SH gradients as 16-byte stores (the arrays are 16-byte aligned)
+        float4 *gq4 = reinterpret_cast<float4 *>(A.g_quats) + gid;
+        float4 v = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        if (add) {
+            const float4 o = *gq4;
+            v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+        }
+        *gq4 = v;
+        float4 *gs4 = reinterpret_cast<float4 *>(A.g_sh) + 12 * gid;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float4 w4 = make_float4(gsh[4 * k], gsh[4 * k + 1], gsh[4 * k + 2], gsh[4 * k + 3]);
+            if (add) {
+                const float4 o = gs4[k];
+                w4 = make_float4(o.x + w4.x, o.y + w4.y, o.z + w4.z, o.w + w4.w);
+            }
+            gs4[k] = w4;
+        }
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < 4; ++a) A.g_quats[4 * gid + a] = add ? A.g_quats[4 * gid + a] + gq[a] : gq[a];
-    A.g_opacity[gid] = add ? A.g_opacity[gid] + gop : gop;
 #pragma unroll
     for (int i = 0; i < 48; ++i) A.g_sh[48 * gid + i] = add ? A.g_sh[48 * gid + i] + gsh[i] : gsh[i];
 }
 
 void launch_backward(const BwdArgs &a, cudaStream_t s, cudaEvent_t between) {
     const int ntiles = a.tiles_x * a.tiles_y;
-    if (ntiles > 0) k_blend_backward<<<ntiles, kBwdThreads, 0, s>>>(a);
+    if (ntiles > 0) k_blend_backward<kBwdPx><<<ntiles, 256 / kBwdPx, 0, s>>>(a);
     if (between) cudaEventRecord(between, s);
     const long long P = a.scene.P;
     if (P > 0) k_gauss_backward<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(a);

@@ -556,6 +556,7 @@ struct BwdArgs {
     float *grad2d;                   // [P][10]: u, v, a, b, c, alpha0, r, g, b, -
     float *g_means, *g_scales, *g_quats, *g_opacity, *g_sh;
     int accumulate;
+    int vec16;                       // g_quats and g_sh are 16-byte aligned: vector stores
 };
 // between (nullable): recorded after the reverse blend, before the per-Gaussian chain rule.
 void launch_backward(const BwdArgs &a, cudaStream_t s, cudaEvent_t between);

@@ -79,6 +79,37 @@ def test_gradients_match_oracle_per_element(ctx, sort_mode):
         assert np.count_nonzero(r) > 100, k
 
 
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_unaligned_gradient_buffers(ctx, accumulate):
+    """Caller buffers that are not 16-byte aligned take scalar stores; the result is the same as
+    with aligned ones (and accumulation adds to what is there).  The 2D gradients are summed with
+    float atomics in no fixed order, so two runs agree to rounding, not bit for bit."""
+    scene, cam = synth.grad_subset(P=1200, seed=9, size=48)
+    sc = gs.Scene.from_numpy(ctx, scene)
+    fr = gs.Frame(ctx, scene.P, 1 << 22, cam.width, cam.height)
+    rgb, T, last = fr.render(sc, cam)
+    dl = torch.randn_like(rgb)
+    shapes = dict(means=(scene.P, 3), scales=(scene.P, 3), quats=(scene.P, 4), opacity=(scene.P,),
+                  sh=(scene.P, 16, 3))
+    base = {k: torch.randn(v, device="cuda") for k, v in shapes.items()}
+    aligned = {k: v.clone() for k, v in base.items()}
+    store = {k: torch.empty(int(np.prod(v)) + 1, device="cuda") for k, v in shapes.items()}
+    unaligned = {k: store[k][1:].view(shapes[k]) for k in shapes}
+    for k in shapes:
+        unaligned[k].copy_(base[k])
+    assert unaligned["sh"].data_ptr() % 16 != 0 and unaligned["quats"].data_ptr() % 16 != 0
+    a = fr.gs_render_backward(sc, dl, T, last, grads=aligned, accumulate=accumulate)
+    b = fr.gs_render_backward(sc, dl, T, last, grads=unaligned, accumulate=accumulate)
+    torch.cuda.synchronize()
+    for k in shapes:
+        scale = float(a[k].abs().max())
+        assert torch.allclose(a[k], b[k], rtol=1e-4, atol=1e-6 * scale), k
+    if accumulate:
+        fresh = fr.gs_render_backward(sc, dl, T, last)
+        torch.cuda.synchronize()
+        assert torch.allclose(a["sh"], base["sh"] + fresh["sh"], rtol=1e-4, atol=1e-5)
+
+
 def test_gradients_match_finite_differences(ctx):
     scene, cam = synth.grad_subset(P=2000, seed=7, size=64)
     fz = oracle.Frozen(scene, cam)
