@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256 / PX) k_blend_backward(const __grid_consta
 }
 
 // ------------------------------------------------------------------------------------------ per Gaussian
-__device__ __forceinline__ void sh_basis_and_grad(float x, float y, float z, float Y[16], float dY[16][3]) {
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
     const float K0 = 0.28209479177387814f, K1 = 0.48860251190291992f;
     const float K2a = 1.0925484305920792f, K2b = 0.31539156525252005f, K2c = 0.54627421529603959f;
     const float K3a = 0.59004358992664352f, K3b = 2.8906114426405538f, K3c = 0.45704579946446572f;
@@ -243,26 +243,46 @@ __device__ __forceinline__ void sh_basis_and_grad(float x, float y, float z, flo
     Y[13] = -K3c * x * (4.0f * zz - xx - yy);
     Y[14] = K3e * z * (xx - yy);
     Y[15] = -K3a * x * (xx - 3.0f * yy);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) dY[i][0] = dY[i][1] = dY[i][2] = 0.0f;
-    dY[1][1] = -K1;
-    dY[2][2] = K1;
-    dY[3][0] = -K1;
-    dY[4][0] = K2a * y; dY[4][1] = K2a * x;
-    dY[5][1] = -K2a * z; dY[5][2] = -K2a * y;
-    dY[6][0] = -2.0f * K2b * x; dY[6][1] = -2.0f * K2b * y; dY[6][2] = 4.0f * K2b * z;
-    dY[7][0] = -K2a * z; dY[7][2] = -K2a * x;
-    dY[8][0] = 2.0f * K2c * x; dY[8][1] = -2.0f * K2c * y;
-    dY[9][0] = -6.0f * K3a * x * y; dY[9][1] = -K3a * (3.0f * xx - 3.0f * yy);
-    dY[10][0] = K3b * y * z; dY[10][1] = K3b * x * z; dY[10][2] = K3b * x * y;
-    dY[11][0] = 2.0f * K3c * x * y; dY[11][1] = -K3c * (4.0f * zz - xx - 3.0f * yy); dY[11][2] = -8.0f * K3c * y * z;
-    dY[12][0] = -6.0f * K3d * x * z; dY[12][1] = -6.0f * K3d * y * z; dY[12][2] = K3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
-    dY[13][0] = -K3c * (4.0f * zz - 3.0f * xx - yy); dY[13][1] = 2.0f * K3c * x * y; dY[13][2] = -8.0f * K3c * x * z;
-    dY[14][0] = 2.0f * K3e * x * z; dY[14][1] = -2.0f * K3e * y * z; dY[14][2] = K3e * (xx - yy);
-    dY[15][0] = -K3a * (3.0f * xx - 3.0f * yy); dY[15][1] = 6.0f * K3a * x * y;
 }
 
-__global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ BwdArgs A) {
+// sum_i c_i grad Y_i(d) with respect to the (unnormalised) components of d, the partial derivatives
+// of the basis above written out.
+__device__ __forceinline__ void sh_dir_grad(float x, float y, float z, const float c[16], float g[3]) {
+    const float K1 = 0.48860251190291992f;
+    const float K2a = 1.0925484305920792f, K2b = 0.31539156525252005f, K2c = 0.54627421529603959f;
+    const float K3a = 0.59004358992664352f, K3b = 2.8906114426405538f, K3c = 0.45704579946446572f;
+    const float K3d = 0.3731763325901154f, K3e = 1.4453057213202769f;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    g[0] = -K1 * c[3] + K2a * y * c[4] - 2.0f * K2b * x * c[6] - K2a * z * c[7] + 2.0f * K2c * x * c[8] -
+           6.0f * K3a * x * y * c[9] + K3b * y * z * c[10] + 2.0f * K3c * x * y * c[11] - 6.0f * K3d * x * z * c[12] -
+           K3c * (4.0f * zz - 3.0f * xx - yy) * c[13] + 2.0f * K3e * x * z * c[14] - K3a * (3.0f * xx - 3.0f * yy) * c[15];
+    g[1] = -K1 * c[1] + K2a * x * c[4] - K2a * z * c[5] - 2.0f * K2b * y * c[6] - 2.0f * K2c * y * c[8] -
+           K3a * (3.0f * xx - 3.0f * yy) * c[9] + K3b * x * z * c[10] - K3c * (4.0f * zz - xx - 3.0f * yy) * c[11] -
+           6.0f * K3d * y * z * c[12] + 2.0f * K3c * x * y * c[13] - 2.0f * K3e * y * z * c[14] + 6.0f * K3a * x * y * c[15];
+    g[2] = K1 * c[2] - K2a * y * c[5] + 4.0f * K2b * z * c[6] - K2a * x * c[7] + K3b * x * y * c[10] -
+           8.0f * K3c * y * z * c[11] + K3d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * c[12] - 8.0f * K3c * x * z * c[13] +
+           K3e * (xx - yy) * c[14];
+}
+
+// SH gradients 4k .. 4k+3 of Gaussian gid: overwritten, or added to when accumulating; a 16-byte
+// store when the caller's array allows.
+__device__ __forceinline__ void store_sh_plane(const BwdArgs &A, long long gid, int k, const float g[4]) {
+    if (A.vec16) {
+        float4 *p = reinterpret_cast<float4 *>(A.g_sh) + 12 * gid + k;
+        float4 w4 = make_float4(g[0], g[1], g[2], g[3]);
+        if (A.accumulate) {
+            const float4 o = *p;
+            w4 = make_float4(o.x + w4.x, o.y + w4.y, o.z + w4.z, o.w + w4.w);
+        }
+        *p = w4;
+    } else {
+        float *p = A.g_sh + 48 * gid + 4 * k;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) p[j] = A.accumulate ? p[j] + g[j] : g[j];
+    }
+}
+
+__global__ void __launch_bounds__(128, 6) k_gauss_backward(const __grid_constant__ BwdArgs A) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= A.scene.P) return;
     const float *d2 = A.grad2d + gid * kG2;
@@ -274,9 +294,6 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
         any |= D[k] != 0.0f;
     }
     float gm[3] = {0, 0, 0}, gsc[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gop = 0.0f;
-    float gsh[48];
-#pragma unroll
-    for (int i = 0; i < 48; ++i) gsh[i] = 0.0f;
     if (any) {
         const Cam &cam = A.cam;
         const SceneView &S = A.scene;
@@ -340,39 +357,48 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
         const float det = S2[0] * S2[3] - S2[1] * S2[2];
         const float Q[4] = {S2[3] / det, -S2[1] / det, -S2[2] / det, S2[0] / det};
 
-        // colour -> SH and direction
+        // colour -> SH and direction.  Pass 1 over the SH planes: each channel's colour (a channel
+        // clamped at 0 passes no gradient).  Pass 2: the coefficient gradients Y_i dr, written plane
+        // by plane, and c_i = sum over the live channels of dr k_i, from which the direction's
+        // gradient is sum_i c_i grad Y_i -- no 48-value arrays held in registers.
         float dvec[3] = {po.x - cam.campos[0], po.y - cam.campos[1], po.z - cam.campos[2]};
         const float dlen = sqrtf(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
         const float dir[3] = {dvec[0] / dlen, dvec[1] / dlen, dvec[2] / dlen};
-        float Y[16], dY[16][3];
-        sh_basis_and_grad(dir[0], dir[1], dir[2], Y, dY);
+        float Y[16];
+        sh_basis(dir[0], dir[1], dir[2], Y);
         const int ncoef = (S.sh_degree + 1) * (S.sh_degree + 1);
-        float f[48];
+        float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < kShPlanes; ++k) {
             const float4 v4 = sh_plane(S, gid, k);
-            f[4 * k] = v4.x;
-            f[4 * k + 1] = v4.y;
-            f[4 * k + 2] = v4.z;
-            f[4 * k + 3] = v4.w;
-        }
-        float ddir[3] = {0, 0, 0};
+            const float e[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.f;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) acc += (i < ncoef ? Y[i] : 0.f) * f[3 * i + ch];
-            if (acc + 0.5f < 0.0f) continue;   // channel clamped at 0
-            const float dr = D[6 + ch];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                if (i < ncoef) {
-                    gsh[3 * i + ch] = Y[i] * dr;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) ddir[a] += dr * f[3 * i + ch] * dY[i][a];
-                }
+            for (int j = 0; j < 4; ++j) {
+                const int f = 4 * k + j, i = f / 3, ch = f - 3 * (f / 3);
+                if (i < ncoef) acc[ch] += Y[i] * e[j];
             }
         }
+        float dr[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) dr[ch] = acc[ch] + 0.5f < 0.0f ? 0.0f : D[6 + ch];
+        float cc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) cc[i] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kShPlanes; ++k) {
+            const float4 v4 = sh_plane(S, gid, k);
+            const float e[4] = {v4.x, v4.y, v4.z, v4.w};
+            float gk[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int f = 4 * k + j, i = f / 3, ch = f - 3 * (f / 3);
+                gk[j] = i < ncoef ? Y[i] * dr[ch] : 0.0f;
+                if (i < ncoef) cc[i] += dr[ch] * e[j];
+            }
+            store_sh_plane(A, gid, k, gk);
+        }
+        float ddir[3];
+        sh_dir_grad(dir[0], dir[1], dir[2], cc, ddir);
         const float dd = ddir[0] * dir[0] + ddir[1] * dir[1] + ddir[2] * dir[2];
         float dmean[3];
 #pragma unroll
@@ -479,7 +505,7 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
     }
     A.g_opacity[gid] = add ? A.g_opacity[gid] + gop : gop;
     if (A.vec16) {
-        // quaternion and SH gradients as 16-byte stores (the arrays are 16-byte aligned)
+        // the quaternion gradient as one 16-byte store (the array is 16-byte aligned)
         float4 *gq4 = reinterpret_cast<float4 *>(A.g_quats) + gid;
         float4 v = make_float4(gq[0], gq[1], gq[2], gq[3]);
         if (add) {
@@ -487,22 +513,16 @@ __global__ void __launch_bounds__(128) k_gauss_backward(const __grid_constant__ 
             v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
         }
         *gq4 = v;
-        float4 *gs4 = reinterpret_cast<float4 *>(A.g_sh) + 12 * gid;
+    } else {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            float4 w4 = make_float4(gsh[4 * k], gsh[4 * k + 1], gsh[4 * k + 2], gsh[4 * k + 3]);
-            if (add) {
-                const float4 o = gs4[k];
-                w4 = make_float4(o.x + w4.x, o.y + w4.y, o.z + w4.z, o.w + w4.w);
-            }
-            gs4[k] = w4;
-        }
-        return;
+        for (int a = 0; a < 4; ++a) A.g_quats[4 * gid + a] = add ? A.g_quats[4 * gid + a] + gq[a] : gq[a];
     }
+    if (!any) {
+        // an unused Gaussian's SH gradients (written here; a used one's went out with pass 2)
+        const float z4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int a = 0; a < 4; ++a) A.g_quats[4 * gid + a] = add ? A.g_quats[4 * gid + a] + gq[a] : gq[a];
-#pragma unroll
-    for (int i = 0; i < 48; ++i) A.g_sh[48 * gid + i] = add ? A.g_sh[48 * gid + i] + gsh[i] : gsh[i];
+        for (int k = 0; k < kShPlanes; ++k) store_sh_plane(A, gid, k, z4);
+    }
 }
 
 void launch_backward(const BwdArgs &a, cudaStream_t s, cudaEvent_t between) {
