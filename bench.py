@@ -413,7 +413,7 @@ def run_training(args, gs, ctx, room_scene, room_cams, steps=10, alu=None):
     import torch
     from paper_2408_07967_gb300 import synth
     from paper_2408_07967_gb300.autograd import GaussianRasterizer
-    raw = synth.room_scene(activated=False)
+    raw = synth.room_scene(P=args.gaussians or 1_000_000, activated=False)
     target = synth.perturbed(raw, seed=4)
     W, H = room_cams[0].width, room_cams[0].height
     rast = GaussianRasterizer(ctx, raw.P, W, H, batch=4, max_pairs=1 << 25)
@@ -477,7 +477,8 @@ def run_training(args, gs, ctx, room_scene, room_cams, steps=10, alu=None):
                                  "achieved": round(gbytes / (gauss_ms * 1e-3) / 1e9, 1), "peak": hbm_peak,
                                  "unit": "GB/s", "frac": round(gbytes / (gauss_ms * 1e-3) / 1e9 / hbm_peak, 4),
                                  "algorithmic": f"{BWD_BYTES_PER_GAUSSIAN} B per Gaussian x P = {raw.P}"}}
-    return {"workload": "room 1M @1920x1080, 4-camera batches, L1 vs perturbed-Gaussian targets (seed 4)",
+    return {"workload": f"room {raw.P} Gaussians @1920x1080, 4-camera batches, L1 vs perturbed-Gaussian targets "
+                        f"(seed 4)",
             "ms_per_step": ms, "frames_per_s": 4000.0 / ms, "loss": float(loss.item()),
             "grad_finite": bool(all(torch.isfinite(p.grad).all().item() for p in params)),
             "backward_per_camera": roof}
