@@ -54,10 +54,10 @@ struct WarpRegion {
 
 // PX pixels per thread along a row; 256/PX threads per 16x16 tile; BATCH records per stage.
 // Each warp owns an RR x RC pixel region of the tile.  Per staged batch, lane l tests entries
-// l, l+32, ... exactly against the region's pixel-area rectangle; the warp then walks only the
+// l, l+32, ... exactly against the region's rectangle shrunk by a quarter pixel; the warp then walks only the
 // entries that meet it, in list order, so a pixel's entries are still evaluated in order and
-// with the same arithmetic.  (A pixel sample passing q <= t lies inside the ellipse, half a
-// pixel inside the rectangle, so no contributing entry is filtered out.)  COUNT adds the
+// with the same arithmetic.  (A pixel sample passing q <= t lies inside the ellipse, a quarter
+// pixel inside the tested rectangle, so no contributing entry is filtered out.)  COUNT adds the
 // per-pixel evaluation and contribution counters used for the roofline (not in timed runs).
 template <int PX, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ BlendArgs A) {
@@ -79,8 +79,10 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
     const int ry0 = ty * kTile + (warp / REGIONS_PER_ROW) * WR::RR;
     const int py = ry0 + lane / WR::LANES_PER_ROW;
     const int px0 = rx0 + (lane % WR::LANES_PER_ROW) * PX;
-    // the region's pixel-area rectangle (its pixel samples lie half a pixel inside it)
-    const float qx0 = (float)rx0, qx1 = (float)(rx0 + WR::RC), qy0 = (float)ry0, qy1 = (float)(ry0 + WR::RR);
+    // the rectangle the filter tests: the region's pixel samples lie a quarter pixel inside it (far
+    // above binary32 rounding, so a sample that passes q <= t always finds its entry kept)
+    const float qx0 = (float)rx0 + 0.25f, qx1 = (float)(rx0 + WR::RC) - 0.25f, qy0 = (float)ry0 + 0.25f,
+                qy1 = (float)(ry0 + WR::RR) - 0.25f;
     long long n = (long long)*A.n_dev;
     if (n > A.cap) n = A.cap;
     const long long start = min((long long)A.starts[gtile], n);
@@ -189,25 +191,23 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
                     if (!__any_sync(FULL, anyp)) continue;
                     const float4 r2 = S.r2[buf][j];
                     const unsigned pos = pos0 + (unsigned)j + 1u;
+                    // branch-free: a pixel that does not pass adds a zero weight and keeps its state
 #pragma unroll
                     for (int k = 0; k < PX; ++k) {
-                        if (pass[k]) {
-                            const float al = fminf(amax, ex2_approx(fmaf(q[k], -HALF_LOG2E, r1.z)));
-                            const float Tn = fmaf(-al, T[k], T[k]);
-                            if (COUNT) ++contrib[k];
-                            if (Tn < tmin) {
-                                fpx[k] = INF;
-                                --alive_px;
-                                if (COUNT) stop[k] = pos;
-                            } else {
-                                const float w = al * T[k];
-                                C0[k] = fmaf(w, r1.w, C0[k]);
-                                C1[k] = fmaf(w, r2.x, C1[k]);
-                                C2[k] = fmaf(w, r2.y, C2[k]);
-                                T[k] = Tn;
-                                last[k] = pos;
-                            }
-                        }
+                        const float al = fminf(amax, ex2_approx(fmaf(q[k], -HALF_LOG2E, r1.z)));
+                        const float Tn = fmaf(-al, T[k], T[k]);
+                        const bool stp = pass[k] && Tn < tmin;
+                        const bool upd = pass[k] && !(Tn < tmin);
+                        if (COUNT) contrib[k] += pass[k];
+                        if (COUNT && stp) stop[k] = pos;
+                        const float w = upd ? al * T[k] : 0.0f;
+                        C0[k] = fmaf(w, r1.w, C0[k]);
+                        C1[k] = fmaf(w, r2.x, C1[k]);
+                        C2[k] = fmaf(w, r2.y, C2[k]);
+                        T[k] = upd ? Tn : T[k];
+                        last[k] = upd ? pos : last[k];
+                        fpx[k] = stp ? INF : fpx[k];
+                        alive_px -= stp;
                     }
                 }
             }
