@@ -116,8 +116,12 @@ class ClockSampler:
         self.idx = device_index
         self.proc = None
         self.lines = []
+        self.t_start = 0.0
 
     def start(self):
+        """Start nvidia-smi's 50 ms loop and wait (at most 3 s) for its first sample, so that the
+        loop is running when the timed region begins; samples taken before start() returns (the
+        idle GPU before the region) are left out of the statistics."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -126,10 +130,15 @@ class ClockSampler:
             self.th.start()
         except Exception:
             self.proc = None
+            return
+        t_end = time.perf_counter() + 3.0
+        while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.005)
+        self.t_start = time.perf_counter()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def stop(self):
         if self.proc is None:
@@ -142,7 +151,9 @@ class ClockSampler:
         self.th.join(timeout=2)
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if t < self.t_start:
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
