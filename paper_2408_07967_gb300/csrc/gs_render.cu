@@ -9,9 +9,14 @@
 //   * divergence control (Section 5.2.2): each warp filters every staged batch against its own
 //     pixel region with the exact ellipse/rectangle test of Algorithm 3 (one Gaussian per lane,
 //     one ballot per 32 entries) and walks only the entries that can reach its pixels -- the
-//     paper's tile-level exact intersection applied again at warp granularity; a warp-uniform vote skips an entry
-//     that passes q <= t at none of the warp's pixels; a saturated pixel is parked at x = +inf,
-//     and one CTA-wide count stops the tile when every pixel has saturated;
+//     paper's tile-level exact intersection applied again at warp granularity (with one pixel
+//     per thread, a warp-uniform vote also skips an entry that passes q <= t at none of the
+//     warp's pixels); a saturated pixel is parked at x = +inf, and one CTA-wide count stops the
+//     tile when every pixel has saturated;
+//   * with two or four pixels per thread, the pixels are processed in pairs by the packed
+//     binary32 operations of sm_100-class GPUs (add/mul/fma .f32x2: one instruction for both
+//     pixels, each lane rounded exactly as the scalar operation), halving the issue slots of the
+//     per-pixel arithmetic in this issue-bound loop;
 //   * the exponent is folded into one FMA in the log2 domain and evaluated by
 //     ex2.approx.ftz.f32 (Section 5.3.2).
 //
@@ -107,8 +112,19 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
         stop[k] = 0;
         contrib[k] = 0;
     }
+    // PX >= 2: the state of pixels 2h, 2h+1 as float2 pairs, updated by packed f32x2 operations
+    // (one instruction for both pixels; each lane of the pair is the binary32 operation above)
+    constexpr int NP = PX / 2 > 0 ? PX / 2 : 1;
+    float2 fx2[NP], T2[NP], C02[NP], C12[NP], C22[NP];
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+        fx2[h] = make_float2(fpx[2 * h < PX ? 2 * h : 0], fpx[2 * h + 1 < PX ? 2 * h + 1 : 0]);
+        T2[h] = make_float2(1.0f, 1.0f);
+        C02[h] = C12[h] = C22[h] = make_float2(0.0f, 0.0f);
+    }
     const float HALF_LOG2E = 0.72134752044448170f;
     const float amax = R.opt.alpha_max, tmin = R.opt.T_min;
+    const float2 nhl2 = make_float2(-HALF_LOG2E, -HALF_LOG2E);
     const unsigned FULL = 0xffffffffu;
 
     // ---- pipeline prologue: ids of batches 0 and 1, records of batch 0
@@ -170,14 +186,65 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
 #pragma unroll
             for (int w = 0; w < WORDS; ++w) {
                 unsigned m = mask[w];
-                while (m) {
-                    const int j = w * 32 + __ffs(m) - 1;
-                    m &= m - 1;
+                auto step = [&](const int j) {
                     const float4 r0 = S.r0[buf][j];
                     const float4 r1 = S.r1[buf][j];
                     const float dy = fsub(fpy, r0.y);
                     const float By = fmul(r0.w, dy);
                     const float Cy = fmul(fmul(r1.x, dy), dy);
+                    const unsigned pos = pos0 + (unsigned)j + 1u;
+                    if constexpr (PX >= 2) {
+                        // both pixels of a pair in one packed operation per step; the filter
+                        // already dropped the entries that reach no pixel of the warp, so with
+                        // two pixels per thread the rest are blended without a per-entry vote
+                        // (with four, the warp's 128 pixels leave more entries that reach none
+                        // of them and the vote pays)
+                        float2 q2[NP];
+                        bool pass[PX];
+#pragma unroll
+                        for (int h = 0; h < NP; ++h) {
+                            const float2 dx2 = __fadd2_rn(fx2[h], make_float2(-r0.x, -r0.x));
+                            q2[h] = __ffma2_rn(__ffma2_rn(make_float2(r0.z, r0.z), dx2, make_float2(By, By)), dx2,
+                                               make_float2(Cy, Cy));
+                            pass[2 * h] = q2[h].x <= r1.y;
+                            pass[2 * h + 1] = q2[h].y <= r1.y;
+                        }
+                        if (PX == 4) {
+                            bool anyp = false;
+#pragma unroll
+                            for (int k = 0; k < PX; ++k) anyp |= pass[k];
+                            if (!__any_sync(FULL, anyp)) return;
+                        }
+                        const float4 r2 = S.r2[buf][j];
+#pragma unroll
+                        for (int h = 0; h < NP; ++h) {
+                            const bool p0 = pass[2 * h], p1 = pass[2 * h + 1];
+                            const float2 e2 = __ffma2_rn(q2[h], nhl2, make_float2(r1.z, r1.z));
+                            // nal = -alpha and nau = -alpha where the pixel takes the entry, else 0:
+                            // T' = fma(nau, T, T) is the scalar fma(-alpha, T, T) or T itself, and
+                            // C += (nau T)(-rgb) is the scalar fma(alpha T, rgb, C) bit for bit
+                            const float2 nal2 =make_float2(fmaxf(-amax, -ex2_approx(e2.x)), fmaxf(-amax, -ex2_approx(e2.y)));
+                            const float2 Tn2 = __ffma2_rn(nal2, T2[h], T2[h]);
+                            const bool s0 = p0 && Tn2.x < tmin, s1 = p1 && Tn2.y < tmin;
+                            const bool u0 = p0 && !(Tn2.x < tmin), u1 = p1 && !(Tn2.y < tmin);
+                            if (COUNT) {
+                                contrib[2 * h] += p0;
+                                contrib[2 * h + 1] += p1;
+                                if (s0) stop[2 * h] = pos;
+                                if (s1) stop[2 * h + 1] = pos;
+                            }
+                            const float2 nau = make_float2(u0 ? nal2.x : 0.0f, u1 ? nal2.y : 0.0f);
+                            const float2 nw2 = __fmul2_rn(nau, T2[h]);
+                            C02[h] = __ffma2_rn(nw2, make_float2(-r1.w, -r1.w), C02[h]);
+                            C12[h] = __ffma2_rn(nw2, make_float2(-r2.x, -r2.x), C12[h]);
+                            C22[h] = __ffma2_rn(nw2, make_float2(-r2.y, -r2.y), C22[h]);
+                            T2[h] = __ffma2_rn(nau, T2[h], T2[h]);
+                            last[2 * h] = u0 ? pos : last[2 * h];
+                            last[2 * h + 1] = u1 ? pos : last[2 * h + 1];
+                            fx2[h] = make_float2(s0 ? INF : fx2[h].x, s1 ? INF : fx2[h].y);
+                        }
+                        return;
+                    }
                     float q[PX];
                     bool pass[PX];
                     bool anyp = false;
@@ -188,9 +255,8 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
                         pass[k] = q[k] <= r1.y;
                         anyp |= pass[k];
                     }
-                    if (!__any_sync(FULL, anyp)) continue;
+                    if (!__any_sync(FULL, anyp)) return;
                     const float4 r2 = S.r2[buf][j];
-                    const unsigned pos = pos0 + (unsigned)j + 1u;
                     // branch-free: a pixel that does not pass adds a zero weight and keeps its state
 #pragma unroll
                     for (int k = 0; k < PX; ++k) {
@@ -209,13 +275,43 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
                         fpx[k] = stp ? INF : fpx[k];
                         alive_px -= stp;
                     }
+                };
+                // four pixels per thread: two entries per trip (fewer loop steps a walked entry;
+                // measured faster there, slower with two pixels per thread)
+                while (m) {
+                    step(w * 32 + __ffs(m) - 1);
+                    m &= m - 1;
+                    if constexpr (PX == 4) {
+                        if (!m) break;
+                        step(w * 32 + __ffs(m) - 1);
+                        m &= m - 1;
+                    }
                 }
             }
+        }
+        if constexpr (PX >= 2) {
+            // pixels still running: the ones not parked at x = +inf (outside pixels start there)
+            alive_px = 0;
+#pragma unroll
+            for (int h = 0; h < NP; ++h) alive_px += (fx2[h].x != INF) + (fx2[h].y != INF);
         }
         if (__syncthreads_count(alive_px > 0) == 0) break;   // also orders buffer reuse
         buf ^= 1;
     }
     cp_async_wait<0>();
+    if constexpr (PX >= 2) {
+#pragma unroll
+        for (int h = 0; h < NP; ++h) {
+            T[2 * h] = T2[h].x;
+            T[2 * h + 1] = T2[h].y;
+            C0[2 * h] = C02[h].x;
+            C0[2 * h + 1] = C02[h].y;
+            C1[2 * h] = C12[h].x;
+            C1[2 * h + 1] = C12[h].y;
+            C2[2 * h] = C22[h].x;
+            C2[2 * h + 1] = C22[h].y;
+        }
+    }
 
     if (COUNT) {
         // entries walked per pixel (skipped ones included) and entries that passed q <= t
