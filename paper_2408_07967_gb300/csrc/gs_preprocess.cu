@@ -69,52 +69,73 @@ void launch_pack_scene(const gs_gaussians &g, float4 *pos_opa, float4 *rs, void 
 // Real SH basis through degree 3 (3DGS sign/order convention), constants are the closed forms
 // 1/(2 sqrt pi), sqrt(3/(4 pi)), sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4, sqrt(35/(2 pi))/4,
 // sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4 evaluated to float.
-__device__ __forceinline__ void sh_colour(const SceneView &S, long long gid, const Cam &cam, float mx, float my,
-                                          float mz, float rgb[3]) {
+//
+// A Gaussian's colour is evaluated by four consecutive lanes: lane `part` reads SH planes 3 part ..
+// 3 part + 2 (floats 12 part .. 12 part + 11, i.e. coefficients 4 part .. 4 part + 3 of the three
+// channels) -- three 16-byte loads in flight per lane instead of twelve in one lane, whose
+// registers the count pass does not have -- and its partial sums are added across the four
+// lanes in a fixed order.  Returns the clamped colour (identical on the four lanes).
+__device__ __forceinline__ void sh_colour4(const SceneView &S, long long gid, const Cam &cam, float mx, float my,
+                                           float mz, int part, unsigned gmask, float rgb[3]) {
+    const int deg = S.sh_degree;
+    const int ncoef = (deg + 1) * (deg + 1);
+    const int nplanes = (3 * ncoef + 3) / 4;
+    float4 pl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int plane = 3 * part + k;
+        pl[k] = plane < nplanes ? sh_plane(S, gid, plane) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const float K0 = 0.28209479177387814f;
     const float K1 = 0.48860251190291992f;
     const float K2a = 1.0925484305920792f, K2b = 0.31539156525252005f, K2c = 0.54627421529603959f;
     const float K3a = 0.59004358992664352f, K3b = 2.8906114426405538f, K3c = 0.45704579946446572f;
     const float K3d = 0.3731763325901154f, K3e = 1.4453057213202769f;
-    float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
-    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float x = dx * inv, y = dy * inv, z = dz * inv;
-    float Y[16];
-    Y[0] = K0;
-    Y[1] = -K1 * y;
-    Y[2] = K1 * z;
-    Y[3] = -K1 * x;
-    float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = K2a * x * y;
-    Y[5] = -K2a * y * z;
-    Y[6] = K2b * (2.0f * zz - xx - yy);
-    Y[7] = -K2a * x * z;
-    Y[8] = K2c * (xx - yy);
-    Y[9] = -K3a * y * (3.0f * xx - yy);
-    Y[10] = K3b * x * y * z;
-    Y[11] = -K3c * y * (4.0f * zz - xx - yy);
-    Y[12] = K3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
-    Y[13] = -K3c * x * (4.0f * zz - xx - yy);
-    Y[14] = K3e * z * (xx - yy);
-    Y[15] = -K3a * x * (xx - 3.0f * yy);
-    const int deg = S.sh_degree;
-    const int ncoef = (deg + 1) * (deg + 1);
-    const int nplanes = (3 * ncoef + 3) / 4;
-    // SH float f = 3 i + ch belongs to coefficient i of channel ch; each channel accumulates in
-    // ascending i as the planes stream in (float4 k holds floats 4k .. 4k+3)
+    const float dx = mx - cam.campos[0], dy = my - cam.campos[1], dz = mz - cam.campos[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    const float x = dx * inv, y = dy * inv, z = dz * inv;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    // the four basis functions of this lane's coefficients
+    float Y[4];
+    if (part == 0) {
+        Y[0] = K0;
+        Y[1] = -K1 * y;
+        Y[2] = K1 * z;
+        Y[3] = -K1 * x;
+    } else if (part == 1) {
+        Y[0] = K2a * x * y;
+        Y[1] = -K2a * y * z;
+        Y[2] = K2b * (2.0f * zz - xx - yy);
+        Y[3] = -K2a * x * z;
+    } else if (part == 2) {
+        Y[0] = K2c * (xx - yy);
+        Y[1] = -K3a * y * (3.0f * xx - yy);
+        Y[2] = K3b * x * y * z;
+        Y[3] = -K3c * y * (4.0f * zz - xx - yy);
+    } else {
+        Y[0] = K3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+        Y[1] = -K3c * x * (4.0f * zz - xx - yy);
+        Y[2] = K3e * z * (xx - yy);
+        Y[3] = -K3a * x * (xx - 3.0f * yy);
+    }
+    // float f = 12 part + j belongs to coefficient 4 part + j / 3 of channel j % 3
     float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int k = 0; k < kShPlanes; ++k) {
-        const float4 v = k < nplanes ? sh_plane(S, gid, k) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float e[4] = {v.x, v.y, v.z, v.w};
+    for (int k = 0; k < 3; ++k) {
+        const float e[4] = {pl[k].x, pl[k].y, pl[k].z, pl[k].w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int f = 4 * k + j, i = f / 3, ch = f - 3 * (f / 3);
-            acc[ch] += (i < ncoef ? Y[i] : 0.0f) * e[j];
+        for (int j4 = 0; j4 < 4; ++j4) {
+            const int j = 4 * k + j4, i = j / 3, ch = j - 3 * (j / 3);
+            acc[ch] += (4 * part + i < ncoef ? Y[i] : 0.0f) * e[j4];
         }
     }
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch] + 0.5f, 0.0f);
+    for (int ch = 0; ch < 3; ++ch) {
+        float a = acc[ch];
+        a += __shfl_xor_sync(gmask, a, 1);    // (p0 + p1), (p2 + p3)
+        a += __shfl_xor_sync(gmask, a, 2);    // (p0 + p1) + (p2 + p3) on every lane
+        rgb[ch] = fmaxf(a + 0.5f, 0.0f);
+    }
 }
 
 // ------------------------------------------------------------------------------------------ geometry
@@ -468,6 +489,7 @@ struct CountSmem {
     int h[kPreBlock];                     // slot: candidate rows
     short sl[kPreBlock];              // slot -> Gaussian (thread) of the chunk
     short slot_of[kPreBlock];         // Gaussian -> slot, -1 when it has none
+    short vlist[kPreBlock];           // paired slots in slot order
     unsigned wsum[kPreBlock / 32], wsum2[kPreBlock / 32];
     unsigned long long mbase;         // first hit-mask byte of the chunk
 };
@@ -633,17 +655,29 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
     }
     __syncthreads();
     const unsigned mine = S.cnt[tid];                  // pairs of slot tid (0 beyond ns)
-    unsigned hits = 0;
+    const bool vis = mine != 0;
+    unsigned hits = 0, nvis_block = 0;
     {
         unsigned v = mine;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) S.wsum[warp] = v;
-    }
-    const bool vis = mine != 0;
-    const unsigned nvis_block = (unsigned)__syncthreads_count(vis);
+        const unsigned vb = __ballot_sync(0xffffffffu, vis);
+        if (lane == 0) {
+            S.wsum[warp] = v;
+            S.wsum2[warp] = (unsigned)__popc(vb);
+        }
+        __syncthreads();
+        unsigned vbefore = 0;
 #pragma unroll
-    for (int w2 = 0; w2 < kPreBlock / 32; ++w2) hits += S.wsum[w2];
+        for (int w2 = 0; w2 < kPreBlock / 32; ++w2) {
+            const unsigned c = S.wsum2[w2];
+            hits += S.wsum[w2];
+            vbefore += w2 < warp ? c : 0u;
+            nvis_block += c;
+        }
+        // the paired slots in slot (= id) order
+        if (vis) S.vlist[vbefore + __popc(vb & ((1u << lane) - 1u))] = (short)tid;
+    }
     if (tid == 0) {
         A.chunk_hits[chunk] = hits;
         A.chunk_vis[chunk] = nvis_block;
@@ -655,23 +689,33 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
         const int k = S.slot_of[tid];
         A.counts[R.rec0 + g0 + tid] = k >= 0 ? S.cnt[k] : 0u;
     }
-    if (vis) {
-        const long long gid = g0 + S.sl[tid];
+    __syncthreads();
+    // render record and emission geometry of every paired slot, four lanes a slot: the colour's SH
+    // loads are spread over the lanes, then lane 0 writes the record and lanes 1-3 the geometry
+    for (int q = tid; q < 4 * (int)nvis_block; q += kPreBlock) {
+        const int slot = S.vlist[q >> 2], part = q & 3;
+        const unsigned gmask = 0xfu << (lane & ~3);
+        const long long gid = g0 + S.sl[slot];
         const long long rec = R.rec0 + gid;
-        const float u = S.u[tid], v = S.v[tid], a = S.a[tid], b = S.b[tid], c = S.c[tid], t = S.t[tid];
-        A.geo2[rec] = make_int4(S.tx0[tid], S.ty0[tid], S.w[tid], S.h[tid]);
-        A.geo0[rec] = make_float4(u, v, a, b);
-        const unsigned moff = keep ? (unsigned)(S.mbase + (unsigned long long)S.cstart[tid]) : kNoMasks;
-        A.geo1[rec] = make_float4(c, t, S.z[tid], __uint_as_float(moff));
         const float4 po = __ldg(R.scene.pos_opa + gid);
         float rgb[3];
-        sh_colour(R.scene, gid, cam, po.x, po.y, po.z, rgb);
-        const float2 hxy = S.hxy[tid];
-        Rec rc;
-        rc.r0 = make_float4(u, v, a, b + b);
-        rc.r1 = make_float4(c, t, S.gl[tid], rgb[0]);
-        rc.r2 = make_float4(rgb[1], rgb[2], hxy.x + 1.0f, hxy.y + 1.0f);
-        A.recs[rec] = rc;
+        sh_colour4(R.scene, gid, cam, po.x, po.y, po.z, part, gmask, rgb);
+        const float u = S.u[slot], v = S.v[slot], a = S.a[slot], b = S.b[slot], c = S.c[slot], t = S.t[slot];
+        if (part == 0) {
+            const float2 hxy = S.hxy[slot];
+            Rec rc;
+            rc.r0 = make_float4(u, v, a, b + b);
+            rc.r1 = make_float4(c, t, S.gl[slot], rgb[0]);
+            rc.r2 = make_float4(rgb[1], rgb[2], hxy.x + 1.0f, hxy.y + 1.0f);
+            A.recs[rec] = rc;
+        } else if (part == 1) {
+            A.geo0[rec] = make_float4(u, v, a, b);
+        } else if (part == 2) {
+            const unsigned moff = keep ? (unsigned)(S.mbase + (unsigned long long)S.cstart[slot]) : kNoMasks;
+            A.geo1[rec] = make_float4(c, t, S.z[slot], __uint_as_float(moff));
+        } else {
+            A.geo2[rec] = make_int4(S.tx0[slot], S.ty0[slot], S.w[slot], S.h[slot]);
+        }
     }
 }
 
