@@ -13,7 +13,7 @@
 //                (Section 5.1.2) to any mix of sizes.  It writes the chunk's hit count, the
 //                geometry of paired Gaussians, and their render records with the SH colour
 //                (Algorithm 4, last step: colour only for Gaussians that are used);
-//   k_chunk_scan exclusive scan of the chunk hit counts (one CTA);
+//   k_chunk_scan exclusive scan of the chunk hit counts (CTAs that each sum their predecessors' counts);
 //   k_pre_emit   repeats the tests and writes every hit at its chunk's base + its rank in unit
 //                order, so pairs land in (Gaussian id, tile row-major) order -- deterministic,
 //                unlike the paper's atomicAdd slots, and without any inter-CTA waiting, so a
@@ -719,79 +719,104 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
     }
 }
 
-// Exclusive scans of chunk counts (one CTA of kScanThreads).  Each step covers kScanVec x
-// kScanThreads x 4 counts: every thread issues all kScanVec of its 16-byte loads (coalesced: load j
-// of thread i is uint4 j kScanThreads + i of the step) before any is summed, so one memory latency
-// covers the step; then one block scan of the per-thread sums of each load row, and coalesced
-// 16-byte stores of the 64-bit prefixes.  A city frame's 39k chunks take three steps.
-constexpr int kScanThreads = 512;
-constexpr int kScanVec = 8;
-__device__ void chunk_scan(const unsigned *in, unsigned long long *out, long long n, unsigned long long *total) {
-    __shared__ unsigned long long s_w[kScanVec][kScanThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long n4 = (n + 3) / 4;
-    unsigned long long carry = 0;
-    for (long long c0 = 0; c0 < n4; c0 += (long long)kScanVec * kScanThreads) {
-        uint4 v[kScanVec];
+// Exclusive scans of chunk counts over many CTAs in one launch, with no CTA waiting on another:
+// CTA j scans counts [2048 j, 2048 j + 2048) (eight consecutive counts per thread, two 16-byte
+// loads) and finds its base by summing every count before its span itself (16-byte loads, all
+// CTAs in parallel; a city frame's 39k chunks take 20 CTAs, the last reading 39k counts from L2).
+// The CTA holding the last count writes the total.  Counts arrays are 16-byte aligned.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr long long kScanSpan = (long long)kScanThreads * kScanPer;
+__device__ unsigned long long block_sum64(unsigned long long x, unsigned long long *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-        for (int j = 0; j < kScanVec; ++j) {
-            const long long i = c0 + (long long)j * kScanThreads + tid, e = 4 * i;
-            v[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (e + 3 < n) {
-                v[j] = __ldcg(reinterpret_cast<const uint4 *>(in) + i);
-            } else if (e < n) {
-                v[j].x = __ldcg(in + e);
-                if (e + 1 < n) v[j].y = __ldcg(in + e + 1);
-                if (e + 2 < n) v[j].z = __ldcg(in + e + 2);
-            }
-        }
-        unsigned long long incl[kScanVec], sum[kScanVec];
-#pragma unroll
-        for (int j = 0; j < kScanVec; ++j) {
-            sum[j] = (unsigned long long)v[j].x + v[j].y + v[j].z + v[j].w;
-            incl[j] = sum[j];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl[j], o);
-                if (lane >= o) incl[j] += y;
-            }
-            if (lane == 31) s_w[j][warp] = incl[j];
-        }
-        __syncthreads();
-        unsigned long long row_base = carry;
-#pragma unroll
-        for (int j = 0; j < kScanVec; ++j) {
-            unsigned long long wex = 0, tot = 0;
-#pragma unroll 8
-            for (int w2 = 0; w2 < kScanThreads / 32; ++w2) {
-                const unsigned long long y = s_w[j][w2];
-                wex += w2 < warp ? y : 0ull;
-                tot += y;
-            }
-            const long long i = c0 + (long long)j * kScanThreads + tid, e = 4 * i;
-            if (out && e < n) {
-                const unsigned long long o0 = row_base + wex + incl[j] - sum[j], o1 = o0 + v[j].x, o2 = o1 + v[j].y,
-                                         o3 = o2 + v[j].z;
-                if (e + 3 < n) {
-                    reinterpret_cast<ulonglong2 *>(out)[2 * i] = make_ulonglong2(o0, o1);
-                    reinterpret_cast<ulonglong2 *>(out)[2 * i + 1] = make_ulonglong2(o2, o3);
-                } else {
-                    out[e] = o0;
-                    if (e + 1 < n) out[e + 1] = o1;
-                    if (e + 2 < n) out[e + 2] = o2;
-                }
-            }
-            row_base += tot;
-        }
-        carry = row_base;
-        __syncthreads();
-    }
-    if (tid == 0) *total = carry;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_w[warp] = x;
     __syncthreads();
+    unsigned long long t = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) t += s_w[w];
+    __syncthreads();
+    return t;
+}
+__device__ void chunk_scan(const unsigned *in, unsigned long long *out, long long n, unsigned long long *total) {
+    __shared__ unsigned long long s_w[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long j = blockIdx.x, base = j * kScanSpan;
+    const long long jlast = n > 0 ? (n - 1) / kScanSpan : 0;
+    if (j > jlast || (!out && j != jlast)) return;      // uniform over the CTA
+    // sum of the counts before the span (base is a multiple of 4)
+    unsigned long long pre = 0;
+    {
+        const uint4 *in4 = reinterpret_cast<const uint4 *>(in);
+        const long long nb4 = base / 4;
+        long long i = tid;
+        for (; i + 3 * kScanThreads < nb4; i += 4 * kScanThreads) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldcg(in4 + i + u * kScanThreads);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) pre += (unsigned long long)v[u].x + v[u].y + v[u].z + v[u].w;
+        }
+        for (; i < nb4; i += kScanThreads) {
+            const uint4 v = __ldcg(in4 + i);
+            pre += (unsigned long long)v.x + v.y + v.z + v.w;
+        }
+    }
+    pre = block_sum64(pre, s_w);
+    // this thread's eight counts
+    const long long e0 = base + (long long)tid * kScanPer;
+    unsigned c[kScanPer];
+    if (e0 + kScanPer <= n) {
+        const uint4 a = __ldcg(reinterpret_cast<const uint4 *>(in + e0));
+        const uint4 b = __ldcg(reinterpret_cast<const uint4 *>(in + e0) + 1);
+        c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w; c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) c[k] = e0 + k < n ? __ldcg(in + e0 + k) : 0u;
+    }
+    unsigned long long tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) tsum += c[k];
+    // block exclusive scan of the thread sums
+    unsigned long long incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    unsigned long long wex = 0, btot = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        const unsigned long long y = s_w[w];
+        wex += w < warp ? y : 0ull;
+        btot += y;
+    }
+    if (out) {
+        unsigned long long run = pre + wex + incl - tsum;
+        if (e0 + kScanPer <= n) {
+            ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(out + e0);
+#pragma unroll
+            for (int k = 0; k < kScanPer; k += 2) {
+                const unsigned long long o0 = run, o1 = run + c[k];
+                run = o1 + c[k + 1];
+                o2[k / 2] = make_ulonglong2(o0, o1);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanPer; ++k) {
+                if (e0 + k < n) out[e0 + k] = run;
+                run += c[k];
+            }
+        }
+    }
+    if (j == jlast && tid == 0) *total = pre + btot;
 }
 
 // n_items (nullable, device): when given, array a holds counts of ceil(*n_items / kPreBlock) chunks
-// only (at most n), e.g. the rank chunks of the paired Gaussians.
+// only (at most n), e.g. the rank chunks of the paired Gaussians.  Grid: ceil(n / kScanSpan) CTAs.
 __global__ void __launch_bounds__(kScanThreads) k_chunk_scan(const unsigned *in_a, unsigned long long *out_a,
                                                              unsigned long long *tot_a, const unsigned *in_b,
                                                              unsigned long long *out_b, unsigned long long *tot_b,
@@ -803,9 +828,17 @@ __global__ void __launch_bounds__(kScanThreads) k_chunk_scan(const unsigned *in_
         na = c < n ? c : n;
     }
     chunk_scan(in_a, out_a, na, tot_a);
-    if (in_b) chunk_scan(in_b, out_b, n, tot_b);
-    if (threadIdx.x == 0 && status && (long long)*tot_a > pair_cap) atomicOr(status, kStPairOverflow);
+    if (in_b) {
+        __syncthreads();
+        chunk_scan(in_b, out_b, n, tot_b);
+    }
+    const long long jlast = na > 0 ? (na - 1) / kScanSpan : 0;
+    if (status && blockIdx.x == jlast && threadIdx.x == 0) {
+        __threadfence_block();
+        if ((long long)*(volatile unsigned long long *)tot_a > pair_cap) atomicOr(status, kStPairOverflow);
+    }
 }
+static unsigned scan_grid(long long n) { return (unsigned)(n > 0 ? (n + kScanSpan - 1) / kScanSpan : 1); }
 
 // Two-level order, step 1: the paired Gaussians of each chunk, compacted in id order, as
 // (depth bits, id) for the depth sort.
@@ -1176,7 +1209,7 @@ void launch_pre_count(const PreprocessArgs &a, cudaStream_t s) {
 void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted) {
     if (a.n_chunks <= 0) return;
     if (!counted) k_pre_count<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
-    k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, a.chunk_base, &a.ctr->n_pairs, nullptr, nullptr, nullptr,
+    k_chunk_scan<<<scan_grid(a.n_chunks), kScanThreads, 0, s>>>(a.chunk_hits, a.chunk_base, &a.ctr->n_pairs, nullptr, nullptr, nullptr,
                                             a.n_chunks, a.pair_cap, &a.ctr->status, nullptr);
     k_pre_emit<false><<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
 }
@@ -1184,7 +1217,7 @@ void launch_preprocess(const PreprocessArgs &a, cudaStream_t s, bool counted) {
 int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cudaStream_t s, bool counted) {
     if (a.n_chunks <= 0) return 0;
     if (!counted) k_pre_count<<<(unsigned)a.n_chunks, kPreBlock, 0, s>>>(a);
-    k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits, nullptr, &a.ctr->n_pairs, a.chunk_vis, a.vis_base,
+    k_chunk_scan<<<scan_grid(a.n_chunks), kScanThreads, 0, s>>>(a.chunk_hits, nullptr, &a.ctr->n_pairs, a.chunk_vis, a.vis_base,
                                             &a.ctr->n_vis64, a.n_chunks, a.pair_cap, &a.ctr->status, nullptr);
     k_vis_compact<<<(unsigned)min(a.n_chunks, (long long)resident_grid(8)), kPreBlock, 0, s>>>(a);
     // depth sort of the paired Gaussians: 32-bit float bits of z (positive, so bit order = value order)
@@ -1200,7 +1233,7 @@ int launch_preprocess_depth(const PreprocessArgs &a, const SortScratch &scr, cud
     k_emit_sum<<<(unsigned)min(rank_chunks, (long long)resident_grid(8)), kPreBlock, 0, s>>>(a);
     unsigned long long *unused_total = &a.ctr->scratch64;
     // only the rank chunks that hold paired Gaussians: ceil(V / 256) of them
-    k_chunk_scan<<<1, kScanThreads, 0, s>>>(a.chunk_hits2, a.chunk_base2, unused_total, nullptr, nullptr, nullptr,
+    k_chunk_scan<<<scan_grid(rank_chunks), kScanThreads, 0, s>>>(a.chunk_hits2, a.chunk_base2, unused_total, nullptr, nullptr, nullptr,
                                             rank_chunks, 1ll << 62, nullptr, &a.ctr->n_vis64);
     k_pre_emit<true><<<(unsigned)min(rank_chunks, (long long)resident_grid(4)), kPreBlock, 0, s>>>(a);
     k_emit_mid<<<resident_grid(8), kPreBlock, 0, s>>>(a);
