@@ -353,70 +353,46 @@ __global__ void __launch_bounds__(256 / PX) k_blend(const __grid_constant__ Blen
 // longest lists start first and short ones fill the end of the launch -- a long list that starts
 // late would otherwise set the blend's makespan (one 1165-entry tile started at 134 us of a room
 // frame's 209 us median SM finish ran to 250 us).  Within a class any order: tiles are
-// independent, so the images do not depend on it.  One CTA: a class histogram in shared memory,
-// the class bases from the longest class down, then each tile takes the next slot of its class;
-// the lanes of a warp that share a class (most do: few classes hold most tiles) take their slots
-// with one atomic.
-__device__ __forceinline__ unsigned length_class(const unsigned *starts, int t) {
-    return 31u - (unsigned)__clz(starts[t + 1] - starts[t] + 1u);
-}
-
-// Four tiles per thread and step, their loads in flight together (the kernel is one CTA, so the
-// steps are latency-bound).
-__global__ void __launch_bounds__(1024) k_tile_order(const unsigned *starts, int ntiles, unsigned *order) {
-    constexpr int U = 4;
-    __shared__ unsigned s_base[32];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int step = (int)blockDim.x * U;
-    const unsigned FULL = 0xffffffffu;
-    if (tid < 32) s_base[tid] = 0;
+// independent, so the images do not depend on it.  One CTA of 1024 threads, sixteen consecutive
+// tiles per thread (up to 16384 tiles, the limit the caller applies): the seventeen starts a
+// thread needs arrive in one round of loads, the classes stay in registers, a class histogram in
+// shared memory gives the class bases from the longest class down, and each tile takes the next
+// slot of its class by a shared-memory atomic (the order within a class is whatever the atomics
+// give).
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderPer = 16;
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(const unsigned *starts, int ntiles, unsigned *order) {
+    __shared__ unsigned s_cnt[33], s_base[33];
+    const int tid = threadIdx.x;
+    if (tid < 33) s_cnt[tid] = 0;
+    const int t0 = tid * kOrderPer;
+    unsigned st[kOrderPer + 1];
+#pragma unroll
+    for (int k = 0; k <= kOrderPer; ++k) st[k] = t0 + k <= ntiles ? __ldg(starts + t0 + k) : 0u;
+    unsigned cls[kOrderPer];
+#pragma unroll
+    for (int k = 0; k < kOrderPer; ++k)
+        cls[k] = t0 + k < ntiles ? 31u - (unsigned)__clz(st[k + 1] - st[k] + 1u) : 32u;   // 32: past the end
     __syncthreads();
-    for (int b0 = 0; b0 < ntiles; b0 += step) {
-        unsigned c[U];
 #pragma unroll
-        for (int j = 0; j < U; ++j) {
-            const int t = b0 + j * (int)blockDim.x + tid;
-            c[j] = t < ntiles ? length_class(starts, t) : 32u;   // 32: past the end
-        }
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            const unsigned peers = __match_any_sync(FULL, c[j]);
-            if (c[j] < 32u && lane == __ffs(peers) - 1) atomicAdd(&s_base[c[j]], (unsigned)__popc(peers));
-        }
-    }
+    for (int k = 0; k < kOrderPer; ++k)
+        if (cls[k] < 32u) atomicAdd(&s_cnt[cls[k]], 1u);
     __syncthreads();
     if (tid == 0) {
         unsigned base = 0;
-        for (int k = 31; k >= 0; --k) {
-            const unsigned n = s_base[k];
-            s_base[k] = base;
-            base += n;
+        for (int c = 31; c >= 0; --c) {
+            s_base[c] = base;
+            base += s_cnt[c];
         }
     }
     __syncthreads();
-    for (int b0 = 0; b0 < ntiles; b0 += step) {
-        unsigned c[U];
 #pragma unroll
-        for (int j = 0; j < U; ++j) {
-            const int t = b0 + j * (int)blockDim.x + tid;
-            c[j] = t < ntiles ? length_class(starts, t) : 32u;
-        }
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            const unsigned peers = __match_any_sync(FULL, c[j]);
-            if (c[j] < 32u) {
-                const int leader = __ffs(peers) - 1;
-                unsigned slot = 0;
-                if (lane == leader) slot = atomicAdd(&s_base[c[j]], (unsigned)__popc(peers));
-                slot = __shfl_sync(peers, slot, leader) + (unsigned)__popc(peers & ((1u << lane) - 1u));
-                order[slot] = (unsigned)(b0 + j * (int)blockDim.x + tid);
-            }
-        }
-    }
+    for (int k = 0; k < kOrderPer; ++k)
+        if (cls[k] < 32u) order[atomicAdd(&s_base[cls[k]], 1u)] = (unsigned)(t0 + k);
 }
 
 void launch_tile_order(const unsigned *starts, int ntiles, unsigned *order, cudaStream_t s) {
-    if (ntiles > 0) k_tile_order<<<1, 1024, 0, s>>>(starts, ntiles, order);
+    if (ntiles > 0 && ntiles <= kOrderThreads * kOrderPer) k_tile_order<<<1, kOrderThreads, 0, s>>>(starts, ntiles, order);
 }
 
 // Launch shapes (pixels per thread, records per staged batch); the autotuner picks one.

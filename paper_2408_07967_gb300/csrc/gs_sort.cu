@@ -980,10 +980,31 @@ __global__ void __launch_bounds__(256) k_tile_starts(const K *keys, const unsign
     const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     if (n >= ntiles && n <= kScanPairsPerTile * ntiles) {
-        for (long long i = g0; i <= n; i += stride) {
-            const long long prev = i == 0 ? -1 : (long long)(keys[i - 1] >> SHIFT);
-            const long long cur = i == n ? (long long)ntiles : (long long)(keys[i] >> SHIFT);
-            for (long long t = prev + 1; t <= cur; ++t) starts[t] = (unsigned)i;
+        // eight consecutive positions a thread: the keys arrive in 16-byte loads (the key array is
+        // 16-byte aligned), plus the key before them
+        constexpr int V = 8;
+        constexpr int L = V * (int)sizeof(K) / 16;
+        for (long long i0 = g0 * V; i0 <= n; i0 += stride * V) {
+            K k[V];
+            if (i0 + V <= n) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(keys + i0);
+                uint4 raw[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) raw[l] = __ldg(src + l);
+                memcpy(k, raw, sizeof(k));
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) k[v] = i0 + v < n ? keys[i0 + v] : (K)0;
+            }
+            long long prev = i0 == 0 ? -1 : (long long)(keys[i0 - 1] >> SHIFT);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const long long i = i0 + v;
+                if (i > n) break;
+                const long long cur = i == n ? (long long)ntiles : (long long)(k[v] >> SHIFT);
+                for (long long t = prev + 1; t <= cur; ++t) starts[t] = (unsigned)i;
+                prev = cur;
+            }
         }
         return;
     }
