@@ -13,7 +13,9 @@
 //   Each thread takes PX pixels of a row; the nine per-Gaussian sums (u, v, a, b, c, alpha0, r, g,
 //   b) of its pixels are added in the thread, reduced over the warp with shuffles, accumulated
 //   over the CTA in shared memory, then added to global memory once per CTA and entry (warp-level
-//   reduction before atomics, the idea DISTWAR applies to 3DGS).
+//   reduction before atomics, the idea DISTWAR applies to 3DGS).  With two pixels a thread the
+//   pair's states are float2s updated by packed f32x2 operations, and a pixel that does not take
+//   an entry gets alpha = 0 (no branch), which leaves its T and S unchanged and adds nothing.
 // k_gauss_backward: per Gaussian, the chain from those 2D gradients to the parameters: colour ->
 //   SH coefficients and the view direction; alpha0 -> opacity (logit); conic -> Sigma'
 //   (dQ = -Q dSigma' Q) -> Sigma and J W -> scales, quaternion and the camera-space mean; (u, v)
@@ -44,6 +46,36 @@ struct BwdRegion {
     static constexpr int LANES_PER_ROW = RC / PX;
 };
 constexpr int kBwdBatch = 128;
+
+// Warp sums of the nine per-entry terms d, accumulated into s_acc[jj]: d[0..7] by halving
+// exchanges -- across lanes 16 apart each lane keeps four values (its half's) and adds its
+// partner's copy of them, then two, then one; two butterfly steps finish, leaving value
+// 4 b4 + 2 b3 + b2 (bits of the lane) in every lane of a group of four -- 9 shuffles instead of
+// 40; d[8] by a butterfly.
+__device__ __forceinline__ void bwd_warp_sums(const float d[9], int lane, int jj, float (*s_acc)[9]) {
+    const unsigned FULL = 0xffffffffu;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    float k4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = h4 ? d[i] : d[i + 4];
+        k4[i] = (h4 ? d[i + 4] : d[i]) + __shfl_xor_sync(FULL, send, 16);
+    }
+    float k2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = h3 ? k4[i] : k4[i + 2];
+        k2[i] = (h3 ? k4[i + 2] : k4[i]) + __shfl_xor_sync(FULL, send, 8);
+    }
+    float v = (h2 ? k2[1] : k2[0]) + __shfl_xor_sync(FULL, h2 ? k2[0] : k2[1], 4);
+    v += __shfl_xor_sync(FULL, v, 2);
+    v += __shfl_xor_sync(FULL, v, 1);
+    float v8 = d[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(FULL, v8, o);
+    if ((lane & 3) == 0 && v != 0.0f) atomicAdd(&s_acc[jj][lane >> 2], v);
+    if (lane == 0 && v8 != 0.0f) atomicAdd(&s_acc[jj][8], v8);
+}
 
 template <int PX>
 __global__ void __launch_bounds__(256 / PX) k_blend_backward(const __grid_constant__ BwdArgs A) {
@@ -96,6 +128,13 @@ __global__ void __launch_bounds__(256 / PX) k_blend_backward(const __grid_consta
     const float fpy = (float)py + 0.5f;
     const float HALF_LOG2E = 0.72134752044448170f;
     const float amax = A.opt.alpha_max;
+    // two pixels a thread: their states as float2 pairs, updated by packed f32x2 operations
+    float2 fx2 = make_float2(fpx[0], fpx[PX > 1 ? 1 : 0]), T2 = make_float2(T[0], T[PX > 1 ? 1 : 0]);
+    float2 S2 = make_float2(S[0], S[PX > 1 ? 1 : 0]);
+    const float2 G0 = make_float2(g0[0], g0[PX > 1 ? 1 : 0]), G1 = make_float2(g1[0], g1[PX > 1 ? 1 : 0]),
+                 G2 = make_float2(g2[0], g2[PX > 1 ? 1 : 0]);
+    const float2 nhl2 = make_float2(-HALF_LOG2E, -HALF_LOG2E), one2 = make_float2(1.0f, 1.0f),
+                 neg1 = make_float2(-1.0f, -1.0f);
 
     for (int hi = max_last; hi > 0; hi -= kBwdBatch) {
         const int lo = max(0, hi - kBwdBatch);
@@ -109,7 +148,8 @@ __global__ void __launch_bounds__(256 / PX) k_blend_backward(const __grid_consta
                 const Rec rc = A.recs[g];
                 s_r0[e] = rc.r0;
                 s_r1[e] = rc.r1;
-                s_r2[e] = make_float4(rc.r2.x, rc.r2.y, ex2_approx_b(rc.r1.z), 0.f);   // alpha0
+                const float a0v = ex2_approx_b(rc.r1.z);                           // alpha0
+                s_r2[e] = make_float4(rc.r2.x, rc.r2.y, a0v, 1.0f / a0v);
                 s_gid[e] = g;
             }
 #pragma unroll
@@ -140,6 +180,52 @@ __global__ void __launch_bounds__(256 / PX) k_blend_backward(const __grid_consta
                 const float dy = fsub(fpy, r0.y);
                 const float By = fmul(r0.w, dy);
                 const float Cy = fmul(fmul(r1.x, dy), dy);
+                if constexpr (PX == 2) {
+                    // the two pixels in packed steps; a pixel that does not take the entry gets
+                    // alpha = 0, which leaves T and S as they are and adds zero to every sum
+                    const float2 dx2 = __fadd2_rn(fx2, make_float2(-r0.x, -r0.x));
+                    const float2 q2 = __ffma2_rn(__ffma2_rn(make_float2(r0.z, r0.z), dx2, make_float2(By, By)), dx2,
+                                                 make_float2(Cy, Cy));
+                    const bool p0 = j < last[0] && q2.x <= r1.y, p1 = j < last[1] && q2.y <= r1.y;
+                    if (!__any_sync(FULL, p0 || p1)) continue;
+                    const float4 r2 = s_r2[jj];
+                    const float2 e2a = __ffma2_rn(q2, nhl2, make_float2(r1.z, r1.z));
+                    const float e0 = ex2_approx_b(e2a.x), e1 = ex2_approx_b(e2a.y);   // alpha0 e^(-q/2), as forward
+                    const float2 al2 = make_float2(p0 ? fminf(amax, e0) : 0.0f, p1 ? fminf(amax, e1) : 0.0f);
+                    const float2 om2 = __ffma2_rn(al2, neg1, one2);                   // 1 - alpha >= 0.01
+                    const float2 inv2 = make_float2(__fdividef(1.0f, om2.x), __fdividef(1.0f, om2.y));
+                    const float2 Tb2 = __fmul2_rn(T2, inv2);
+                    const float2 gc2 = __ffma2_rn(G0, make_float2(r1.w, r1.w),
+                                                  __ffma2_rn(G1, make_float2(r2.x, r2.x), __fmul2_rn(G2, make_float2(r2.y, r2.y))));
+                    const float2 wgt2 = __fmul2_rn(al2, Tb2);
+                    const float2 si2 = __fmul2_rn(S2, inv2);
+                    const float2 dal2 = __ffma2_rn(Tb2, gc2, make_float2(-si2.x, -si2.y));
+                    S2 = __ffma2_rn(gc2, wgt2, S2);
+                    T2 = Tb2;
+                    // alpha not clamped: the geometry and alpha0 terms, h = alpha dL/dalpha
+                    const float2 h2 = make_float2(p0 && e0 <= amax ? al2.x * dal2.x : 0.0f,
+                                                  p1 && e1 <= amax ? al2.y * dal2.y : 0.0f);
+                    const float2 P0 = __ffma2_rn(make_float2(2.0f * r0.z, 2.0f * r0.z), dx2,
+                                                 make_float2(r0.w * dy, r0.w * dy));
+                    const float2 P1 = __ffma2_rn(make_float2(r0.w, r0.w), dx2,
+                                                 make_float2(2.0f * r1.x * dy, 2.0f * r1.x * dy));
+                    const float2 D0 = __fmul2_rn(h2, P0), D1 = __fmul2_rn(h2, P1);
+                    const float2 D2 = __fmul2_rn(h2, __fmul2_rn(dx2, dx2)), D3 = __fmul2_rn(h2, dx2);
+                    const float2 D6 = __fmul2_rn(wgt2, G0), D7 = __fmul2_rn(wgt2, G1), D8 = __fmul2_rn(wgt2, G2);
+                    const float hs = h2.x + h2.y;
+                    float d[9];
+                    d[0] = 0.5f * (D0.x + D0.y);            // -dq (2 a dx + 2 b dy), dq = -h / 2
+                    d[1] = 0.5f * (D1.x + D1.y);            // -dq (2 b dx + 2 c dy)
+                    d[2] = -0.5f * (D2.x + D2.y);           // dq dx^2
+                    d[3] = -(D3.x + D3.y) * dy;             // dq 2 dx dy
+                    d[4] = -0.5f * hs * dy * dy;            // dq dy^2
+                    d[5] = hs * r2.w;                       // dL/dalpha e^(-q/2) = h / alpha0
+                    d[6] = D6.x + D6.y;
+                    d[7] = D7.x + D7.y;
+                    d[8] = D8.x + D8.y;
+                    bwd_warp_sums(d, lane, jj, s_acc);
+                    continue;
+                }
                 float q[PX], dx[PX];
                 bool pass[PX];
                 bool anyp = false;
@@ -181,31 +267,7 @@ __global__ void __launch_bounds__(256 / PX) k_blend_backward(const __grid_consta
                         d[4] += dq * ddy * ddy;
                     }
                 }
-                // warp sums of d[0..7] by halving exchanges: across lanes 16 apart each lane keeps
-                // four values (its half's) and adds its partner's copy of them, then two, then one;
-                // two butterfly steps finish, leaving value 4 b4 + 2 b3 + b2 (bits of the lane) in
-                // every lane of a group of four -- 9 shuffles instead of 40; d[8] by a butterfly
-                const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
-                float k4[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float send = h4 ? d[i] : d[i + 4];
-                    k4[i] = (h4 ? d[i + 4] : d[i]) + __shfl_xor_sync(FULL, send, 16);
-                }
-                float k2[2];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const float send = h3 ? k4[i] : k4[i + 2];
-                    k2[i] = (h3 ? k4[i + 2] : k4[i]) + __shfl_xor_sync(FULL, send, 8);
-                }
-                float v = (h2 ? k2[1] : k2[0]) + __shfl_xor_sync(FULL, h2 ? k2[0] : k2[1], 4);
-                v += __shfl_xor_sync(FULL, v, 2);
-                v += __shfl_xor_sync(FULL, v, 1);
-                float v8 = d[8];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(FULL, v8, o);
-                if ((lane & 3) == 0 && v != 0.0f) atomicAdd(&s_acc[jj][lane >> 2], v);
-                if (lane == 0 && v8 != 0.0f) atomicAdd(&s_acc[jj][8], v8);
+                bwd_warp_sums(d, lane, jj, s_acc);
             }
         }
         __syncthreads();
