@@ -558,6 +558,15 @@ __global__ void __launch_bounds__(kPreBlock, 8) k_pre_count(const __grid_constan
             S.gl[tid] = log_rn(G.alpha0) * 1.4426950408889634f;     // log2(alpha0)
             S.hxy[tid] = make_float2(G.hx, G.hy);
             units = units_of(w, h);
+            // the colour reads this Gaussian's SH block once the tile tests have run: start
+            // bringing the (at most two) 128-byte lines it spans into L2 now
+            {
+                const long long gid = g0 + S.sl[tid];
+                const size_t bytes = R.scene.sh_half ? kShPlanes * 8 : kShPlanes * 16;
+                const char *sp = (const char *)R.scene.sh + (size_t)gid * bytes;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(sp));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(sp + bytes - 1));
+            }
             items = w >= kWideBox ? h * ((w + kLong - 1) / kLong) : units;
         }
     }
