@@ -2,7 +2,7 @@
 // the per-tile ranges of the sorted pairs.
 //
 // Sort (the stage FlashGS inherits from 3DGS's CUB SortPairs, Section 2.2).  Three forms share
-// one tile body (sort_tile): a CTA loads a tile of 3072 pairs (up to 3584 in the fused form),
+// one tile body (sort_tile): a CTA loads a tile of 3072 pairs (up to 5120 in the fused form),
 // ranks it by digit within each warp (stable: warp-striped load order equals input order; the
 // lanes sharing a digit come from a hardware match when the warp's digits form few runs, else
 // from shared-memory OR masks), places it in (digit, rank) order in shared memory, learns where
@@ -33,12 +33,13 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 12;
 static_assert((kSortThreads * kSortItems * 4) % 16 == 0, "bulk copies of a full tile are whole 16-byte units");
 constexpr int kSortTile = kSortThreads * kSortItems;
-// The fused onesweep sort may take up to 14 items per thread for 64-bit keys, so that a pass of up
-// to 14 x 256 x (resident CTAs) pairs gives every CTA one tile: a second tile in some CTAs would
-// double the pass (tiles are at least kSortTile, so the descriptor area never grows).
+// Items per thread of the per-pass forms' register arrays (they run kSortItems).  The fused sort
+// takes as many items (up to kFusedItems, below) as give every CTA one tile of a pass: a second
+// tile in some CTAs would double the pass (tiles are at least kSortTile, so the descriptor area
+// never grows).
 template <class K>
 constexpr int kMaxItems = sizeof(K) == 8 ? 14 : kSortItems;
-static_assert(32 * kMaxItems<unsigned long long> < 65536, "in-warp ranks fit 16 bits");
+static_assert(32 * 20 < 65536, "in-warp ranks fit 16 bits");
 constexpr unsigned kDescAgg = 1u << 30;
 constexpr unsigned kDescPrefix = 2u << 30;
 constexpr unsigned kDescCount = (1u << 30) - 1;
@@ -171,10 +172,19 @@ __device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned parit
 template <class K>
 constexpr int kBufs = sizeof(K) == 4 ? 2 : 1;
 
+// The fused sort of 64-bit keys runs two CTAs per SM with up to 20 items a thread: one wave of
+// larger tiles per pass (a room frame's 1.4M pairs in about 300 tiles instead of 460) waits less
+// on look-back and barriers than more, smaller tiles (measured: 0.105 vs 0.108 ms; 8 items at 5
+// CTAs per SM 0.160 ms).  The per-pass forms keep kMaxItems.
 template <class K>
+constexpr int kFusedItems = sizeof(K) == 8 ? 20 : kSortItems;
+template <class K>
+constexpr int kFusedCtas = sizeof(K) == 8 ? 2 : 3;
+
+template <class K, int M = kMaxItems<K>>
 struct ScatterSmem {
-    K keys[kBufs<K>][kSortThreads * kMaxItems<K>];   // tile being ranked / next tile in flight
-    unsigned vals[kBufs<K>][kSortThreads * kMaxItems<K>];
+    K keys[kBufs<K>][kSortThreads * M];   // tile being ranked / next tile in flight
+    unsigned vals[kBufs<K>][kSortThreads * M];
     unsigned whist[kSortWarps][256];
     unsigned local_off[256];
     unsigned long long gbase[256];
@@ -226,8 +236,8 @@ __device__ __forceinline__ int look_back(const unsigned long long *base, long lo
 // Starts staging tile t of a pass input into buffer b (one thread): a bulk copy for a full tile of
 // 16-byte-aligned 32-bit-key arrays, completing on the buffer's mbarrier; otherwise nothing (the
 // tile body loads the tile itself).
-template <class K>
-__device__ __forceinline__ void stage_tile(ScatterSmem<K> &S, int b, long long t, int tsize, const K *kin,
+template <class K, int M>
+__device__ __forceinline__ void stage_tile(ScatterSmem<K, M> &S, int b, long long t, int tsize, const K *kin,
                                            const unsigned *vin, long long nfull, int bulk_ok) {
     S.tile[b] = t;
     const bool bulk = kBufs<K> == 2 && bulk_ok && t < nfull;
@@ -241,7 +251,7 @@ __device__ __forceinline__ void stage_tile(ScatterSmem<K> &S, int b, long long t
     }
 }
 
-// One tile of `items` x 256 pairs (kSortItems <= items <= kMaxItems, uniform over the CTA) of a
+// One tile of `items` x 256 pairs (kSortItems <= items <= M, uniform over the CTA) of a
 // scatter pass, run by the whole CTA once the per-warp digit counters are zero and the tile's
 // staging (stage_tile into buffer b) has been started: load, stable ranking, `publish(cnt)` of
 // the tile's count of valid items of digit tid, placement in (digit, rank) order in shared
@@ -249,8 +259,8 @@ __device__ __forceinline__ void stage_tile(ScatterSmem<K> &S, int b, long long t
 // then the global writes in runs of consecutive addresses.  The onesweep and the
 // reduce-then-scan passes differ only in the hooks.  Returns false when the staged copy did not
 // arrive (status flagged; uniform over the CTA).
-template <class K, class Publish, class Resolve, class Next>
-__device__ __forceinline__ bool sort_tile(ScatterSmem<K> &S, int b, long long tile, const K *__restrict__ kin,
+template <class K, int M, class Publish, class Resolve, class Next>
+__device__ __forceinline__ bool sort_tile(ScatterSmem<K, M> &S, int b, long long tile, const K *__restrict__ kin,
                                           const unsigned *__restrict__ vin, K *__restrict__ kout,
                                           unsigned *__restrict__ vout, long long n, int items, int shift,
                                           unsigned dmask, FrameCounters *ctr, unsigned &phases, Publish publish,
@@ -259,7 +269,6 @@ __device__ __forceinline__ bool sort_tile(ScatterSmem<K> &S, int b, long long ti
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << lane) - 1u;
-    constexpr int M = kMaxItems<K>;
     const int tsize = kSortThreads * items;
     const int db = kBufs<K> == 2 ? b : 0;      // data buffer of this tile
     const long long tbase = tile * tsize;
@@ -423,8 +432,8 @@ __device__ __forceinline__ unsigned long long onesweep_resolve(unsigned long lon
 
 // A failed wait leaves copies possibly in flight: give them a bounded chance to land (the phase
 // of a buffer is advanced only by a successful wait, so it names the pending one).
-template <class K>
-__device__ __forceinline__ void drain_staging(ScatterSmem<K> &S, unsigned phases) {
+template <class K, int M>
+__device__ __forceinline__ void drain_staging(ScatterSmem<K, M> &S, unsigned phases) {
     if (threadIdx.x == 0)
         for (int q = 0; q < 2; ++q)
             if (S.bulk[q]) bar_wait(&S.bar[q], (phases >> q) & 1u);
@@ -542,7 +551,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned ncta, Fra
 
 template <class K>
 struct FusedSmem {
-    ScatterSmem<K> s;
+    ScatterSmem<K, kFusedItems<K>> s;
     unsigned offs[8][256];         // exclusive digit offsets of every pass
 };
 
@@ -557,7 +566,7 @@ struct FusedSmem {
 // clear); the epoch used for this sort's tags is published for the next one once every CTA has
 // read the previous value.  bars: nine counters, zero at the start (barriers 0..7, exits).
 template <class K>
-__global__ void __launch_bounds__(kSortThreads, 3) k_sort_fused(K *k0, unsigned *v0, K *k1, unsigned *v1,
+__global__ void __launch_bounds__(kSortThreads, kFusedCtas<K>) k_sort_fused(K *k0, unsigned *v0, K *k1, unsigned *v1,
                                                              const unsigned long long *n_dev, long long n_host,
                                                              long long cap, int passes, unsigned *hist,
                                                              unsigned long long *desc, unsigned long long *bdesc,
@@ -565,14 +574,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_fused(K *k0, unsigned 
                                                              unsigned limit, unsigned top_mask) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FusedSmem<K> &F = *reinterpret_cast<FusedSmem<K> *>(smem_raw);
-    ScatterSmem<K> &S = F.s;
+    ScatterSmem<K, kFusedItems<K>> &S = F.s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // an earlier sort of the frame gave up waiting: its output (this sort's input) is incomplete
     if (__syncthreads_or(tid == 0 && upstream_timed_out(ctr))) return;
     const long long n = pair_count(n_dev, n_host, cap);
     // items per thread: the fewest (>= kSortItems) that give every CTA at most one tile, if any do
     int items = kSortItems;
-    while (items < kMaxItems<K> && n > (long long)gridDim.x * kSortThreads * items) ++items;
+    while (items < kFusedItems<K> && n > (long long)gridDim.x * kSortThreads * items) ++items;
     const int tsize = kSortThreads * items;
     const long long ntiles = (n + tsize - 1) / tsize;
     const long long nfull = n / tsize;
