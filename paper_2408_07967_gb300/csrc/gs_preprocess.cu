@@ -852,28 +852,38 @@ __global__ void __launch_bounds__(kScanThreads) k_chunk_scan(const unsigned *in_
 static unsigned scan_grid(long long n) { return (unsigned)(n > 0 ? (n + kScanSpan - 1) / kScanSpan : 1); }
 
 // Two-level order, step 1: the paired Gaussians of each chunk, compacted in id order, as
-// (depth bits, id) for the depth sort.
+// (depth bits, id) for the depth sort.  One warp a chunk (no block-wide step): its eight count
+// loads go out together, then eight ballots place the paired ones after the chunk's base; a
+// resident grid's warps walk the chunks, skipping those without paired Gaussians.
 __global__ void __launch_bounds__(kPreBlock) k_vis_compact(const __grid_constant__ PreprocessArgs A) {
-    __shared__ unsigned s_w[kPreBlock / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // a resident grid walks the chunks; chunks without paired Gaussians are skipped whole
-    for (long long chunk = blockIdx.x; chunk < A.n_chunks; chunk += gridDim.x) {
-        if (A.chunk_vis[chunk] == 0) continue;
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long chunk = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; chunk < A.n_chunks;
+         chunk += nwarps) {
+        if (A.chunk_vis[chunk] == 0) continue;            // uniform over the warp
         const ReqDesc &R = A.B.r[req_of_chunk(A.B, chunk)];
-        const long long gid = (chunk - R.chunk0) * kPreBlock + threadIdx.x;
-        const long long rec = R.rec0 + gid;
-        const bool vis = gid < R.scene.P && A.counts[rec] != 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, vis);
-        if (lane == 0) s_w[warp] = __popc(bal);
-        __syncthreads();
-        unsigned pre = 0;
-        for (int w2 = 0; w2 < warp; ++w2) pre += s_w[w2];
-        if (vis) {
-            const unsigned long long pos = A.vis_base[chunk] + pre + __popc(bal & ((1u << lane) - 1u));
-            A.dkey[pos] = __float_as_uint(A.geo1[rec].z);
-            A.dval[pos] = (unsigned)rec;
+        const long long g0 = (chunk - R.chunk0) * kPreBlock;
+        constexpr int K = kPreBlock / 32;
+        unsigned c[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const long long gid = g0 + 32 * k + lane;
+            c[k] = gid < R.scene.P ? A.counts[R.rec0 + gid] : 0u;
         }
-        __syncthreads();
+        unsigned long long base = A.vis_base[chunk];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool vis = c[k] != 0u;
+            const unsigned bal = __ballot_sync(FULL, vis);
+            if (vis) {
+                const long long rec = R.rec0 + g0 + 32 * k + lane;
+                const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+                A.dkey[pos] = __float_as_uint(A.geo1[rec].z);
+                A.dval[pos] = (unsigned)rec;
+            }
+            base += __popc(bal);
+        }
     }
 }
 
