@@ -1080,8 +1080,10 @@ __global__ void __launch_bounds__(kPreBlock, DEPTH ? 4 : 8) k_pre_emit(const __g
 // units tested 32 at a time, hits staged per warp and written as coalesced runs from the
 // Gaussian's base.
 __global__ void __launch_bounds__(kPreBlock) k_emit_mid(const __grid_constant__ PreprocessArgs A) {
+    // four consecutive units a lane and step (128 units): a 4096-tile Gaussian takes four steps
+    constexpr int U = 4;
     constexpr int kWarps = kPreBlock / 32;
-    __shared__ unsigned s_tile[kWarps][32 * kSeg];
+    __shared__ unsigned s_tile[kWarps][32 * kSeg * U];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned FULL = 0xffffffffu;
     const unsigned nmid = *(volatile unsigned *)&A.ctr->n_mid;
@@ -1100,20 +1102,28 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_mid(const __grid_constant__ 
         const unsigned mo = __float_as_uint(g1.w);
         const int segs = (g2.z + kSeg - 1) / kSeg;
         const int nunits = segs * g2.w;
-        for (int base = 0; base < nunits; base += 32) {
-            const int k = base + lane;
-            unsigned m = 0;
-            int tx = 0, ty = 0;
-            if (k < nunits) {
-                const int dy = k / segs, seg = k - dy * segs;
-                tx = g2.x + seg * kSeg;
-                ty = g2.y + dy;
-                const int nrun = min(kSeg, g2.z - seg * kSeg);
-                m = mo != kNoMasks       ? (unsigned)A.masks[(unsigned long long)mo + (unsigned)k]
-                    : R.opt.intersect == 1 ? (1u << nrun) - 1u
-                                           : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, nrun, ty);
+        for (int base = 0; base < nunits; base += 32 * U) {
+            unsigned m[U];
+            int tx[U], ty[U];
+            unsigned c = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = base + lane * U + u;
+                m[u] = 0;
+                tx[u] = ty[u] = 0;
+                if (k < nunits) {
+                    const int dy = k / segs, seg = k - dy * segs;
+                    tx[u] = g2.x + seg * kSeg;
+                    ty[u] = g2.y + dy;
+                    const int nrun = min(kSeg, g2.z - seg * kSeg);
+                    m[u] = mo != kNoMasks       ? (unsigned)A.masks[(unsigned long long)mo + (unsigned)k]
+                           : R.opt.intersect == 1 ? (1u << nrun) - 1u
+                                                  : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y,
+                                                             tx[u], nrun, ty[u]);
+                }
             }
-            const unsigned c = (unsigned)__popc(m);
+#pragma unroll
+            for (int u = 0; u < U; ++u) c += (unsigned)__popc(m[u]);
             unsigned incl = c;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -1122,8 +1132,11 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_mid(const __grid_constant__ 
             }
             const unsigned tot = __shfl_sync(FULL, incl, 31);
             unsigned i = incl - c;
-            const unsigned trow = (unsigned)(R.tile0 + ty * R.cam.tiles_x);
-            for (unsigned mm = m; mm; mm &= mm - 1, ++i) s_tile[warp][i] = trow + (unsigned)(tx + __ffs(mm) - 1);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const unsigned trow = (unsigned)(R.tile0 + ty[u] * R.cam.tiles_x);
+                for (unsigned mm = m[u]; mm; mm &= mm - 1, ++i) s_tile[warp][i] = trow + (unsigned)(tx[u] + __ffs(mm) - 1);
+            }
             __syncwarp();
             for (unsigned j = lane; j < tot; j += 32) {
                 const unsigned long long pos = run + j;
@@ -1141,8 +1154,11 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_mid(const __grid_constant__ 
 // Depth order, large Gaussians: one CTA per Gaussian (persistent grid, ticketed), its candidate
 // tiles tested 256 at a time, hits written in row-major order from the Gaussian's base.
 __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ PreprocessArgs A) {
+    // four consecutive units a thread and step (1024 units, 8192 candidate tiles): a Gaussian
+    // that covers the whole image takes four steps, each with its loads in flight together
+    constexpr int U = 4;
     __shared__ unsigned s_item, s_w[kPreBlock / 32];
-    __shared__ unsigned s_tile[kPreBlock * kSeg];
+    __shared__ unsigned s_tile[kPreBlock * kSeg * U];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned FULL = 0xffffffffu;
     const unsigned nbig = *(volatile unsigned *)&A.ctr->n_big;
@@ -1163,21 +1179,29 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
         const unsigned mo = __float_as_uint(g1.w);
         const int segs = (g2.z + kSeg - 1) / kSeg;
         const int nunits = segs * g2.w;
-        for (int base = 0; base < nunits; base += kPreBlock) {
-            const int k = base + tid;
-            unsigned m = 0;
-            int tx = 0, ty = 0;
-            if (k < nunits) {
-                const int dy = k / segs, seg = k - dy * segs;
-                tx = g2.x + seg * kSeg;
-                ty = g2.y + dy;
-                const int nrun = min(kSeg, g2.z - seg * kSeg);
-                m = mo != kNoMasks       ? (unsigned)A.masks[(unsigned long long)mo + (unsigned)k]
-                    : R.opt.intersect == 1 ? (1u << nrun) - 1u
-                                           : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, tx, nrun, ty);
+        for (int base = 0; base < nunits; base += kPreBlock * U) {
+            unsigned m[U];
+            int tx[U], ty[U];
+            unsigned c = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = base + tid * U + u;
+                m[u] = 0;
+                tx[u] = ty[u] = 0;
+                if (k < nunits) {
+                    const int dy = k / segs, seg = k - dy * segs;
+                    tx[u] = g2.x + seg * kSeg;
+                    ty[u] = g2.y + dy;
+                    const int nrun = min(kSeg, g2.z - seg * kSeg);
+                    m[u] = mo != kNoMasks       ? (unsigned)A.masks[(unsigned long long)mo + (unsigned)k]
+                           : R.opt.intersect == 1 ? (1u << nrun) - 1u
+                                                  : run_hits(R.cam.W, R.cam.H, g0.x, g0.y, g0.z, g0.w, g1.x, g1.y,
+                                                             tx[u], nrun, ty[u]);
+                }
             }
-            // block exclusive scan of the hit counts
-            const unsigned c = (unsigned)__popc(m);
+#pragma unroll
+            for (int u = 0; u < U; ++u) c += (unsigned)__popc(m[u]);
+            // block exclusive scan of the hit counts (thread order = unit order)
             unsigned incl = c;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -1194,8 +1218,11 @@ __global__ void __launch_bounds__(kPreBlock) k_emit_big(const __grid_constant__ 
                 tot += x;
             }
             unsigned i = wpre + incl - c;
-            const unsigned trow = (unsigned)(R.tile0 + ty * R.cam.tiles_x);
-            for (unsigned mm = m; mm; mm &= mm - 1, ++i) s_tile[i] = trow + (unsigned)(tx + __ffs(mm) - 1);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const unsigned trow = (unsigned)(R.tile0 + ty[u] * R.cam.tiles_x);
+                for (unsigned mm = m[u]; mm; mm &= mm - 1, ++i) s_tile[i] = trow + (unsigned)(tx[u] + __ffs(mm) - 1);
+            }
             __syncthreads();
             for (unsigned j = tid; j < tot; j += kPreBlock) {
                 const unsigned long long pos = run + j;
