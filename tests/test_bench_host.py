@@ -60,3 +60,17 @@ def test_committed_traffic_matches_the_sources():
 def test_numpy_float16_is_round_to_nearest_even(x, expect):
     with np.errstate(over="ignore"):
         assert float(np.float32(x).astype(np.float16)) == expect
+
+
+def test_clock_summary_counts_only_samples_inside_the_timed_region():
+    """Samples taken before the timed region (the idle GPU while nvidia-smi starts) are left out;
+    throttle reasons are reported when active in any counted sample; bad lines are skipped."""
+    idle = "0, 120, 2070, 120.5, 0x1, Not Active, Not Active, Not Active, Not Active"
+    load = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active"
+    lines = [(0.0, idle), (0.5, idle), (1.0, load), (1.1, "garbage"), (1.2, load), (1.3, capped)]
+    r = bench.summarize_clock_lines(lines, 1.0)
+    assert r["samples"] == 3 and r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"]
+    r = bench.summarize_clock_lines(lines, 2.0)      # nothing inside the region
+    assert r["samples"] == 0 and r["sm_mhz"] is None
